@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these re-runs the oracle's own formula: each compares with a library
+special case (scipy / numpy), a value printed in the paper (tests/golden), a
+closed form or identity, a group action, or brute force on a tiny input.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+from oracle import fb, special
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for ln in open(os.path.join(GOLDEN, name)):
+        if ln.strip() and not ln.startswith("#"):
+            key, val = ln.split()
+            out[key] = float(val)
+    return out
+
+
+def _masked_noise(L, R, n, seed):
+    rng = np.random.default_rng(seed)
+    I = rng.standard_normal((n, L, L))
+    idx = np.arange(L) - L // 2
+    r2 = idx[:, None] ** 2 + idx[None, :] ** 2
+    I[:, r2 >= R * R] = 0.0
+    return I
+
+
+# --- special functions ------------------------------------------------------
+@pytest.mark.parametrize("k", [0, 1, 2, 7, 50, 183, 379])
+def test_besselj_matches_scipy(k):
+    x = np.linspace(0.0, 410.0, 1500)
+    assert np.max(np.abs(special.besselj(k, x) - sp.jv(k, x))) < 5e-14
+
+
+def test_besselj_identities():
+    """Three-term recurrence J_{k-1} + J_{k+1} = (2k/x) J_k and Neumann's
+    addition identity J_0^2 + 2 sum_k J_k^2 = 1 (no library involved)."""
+    for x in (0.7, 33.3, 151.0, 395.5):
+        ks = np.arange(0, 700)
+        J = special.besselj(ks, np.full(ks.shape, x))
+        rec = J[:-2] + J[2:] - 2 * ks[1:-1] / x * J[1:-1]
+        assert np.max(np.abs(rec)) < 1e-13 * max(1.0, 400.0 / x)
+        assert abs(J[0] ** 2 + 2 * np.sum(J[1:] ** 2) - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("k", [0, 1, 10, 120])
+def test_bessel_zeros_match_scipy(k):
+    z = special.bessel_zeros(k, 410.0)
+    ref = sp.jn_zeros(k, z.size)
+    assert np.all(ref[-1] <= 410.0) and sp.jn_zeros(k, z.size + 1)[-1] > 410.0
+    assert np.max(np.abs(z - ref) / ref) < 1e-14
+
+
+@pytest.mark.parametrize("n", [16, 64, 128, 256])
+def test_gauss_legendre(n):
+    x, w = special.gauss_legendre(n)
+    xl, wl = np.polynomial.legendre.leggauss(n)
+    assert np.max(np.abs(x - xl)) < 1e-14
+    assert np.max(np.abs(w - wl) / wl) < 1e-10       # numpy's own weights carry ~1e-11
+    c = 0.5
+    xc, wc = special.gauss_legendre(n, 0.0, c)
+    for m in (0, 1, 7, n, 2 * n - 2, 2 * n - 1):   # exact for degree <= 2n-1
+        exact = c ** (m + 1) / (m + 1)
+        assert abs(np.sum(wc * xc ** m) - exact) <= 5e-14 * exact
+
+
+# --- plan: sampling criterion and sizes (Sec. II-A, Alg. 1 step 1) ----------
+def test_plan_sizes_golden():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "sizes.txt")) if not ln.startswith("#")]
+    for row in rows:
+        L = int(row[0])
+        if L > 64:
+            continue                      # larger plans are exercised in GPU tests
+        p = fb.make_plan(L, 0.5, L / 2)
+        assert (p.k_max, p.P, int(p.p[0] + 2 * p.p[1:].sum()), int(np.sum(p.p ** 2)),
+                p.n_xi, p.n_theta) == tuple(int(float(v)) for v in row[2:])
+
+
+@pytest.mark.parametrize("L", [32, 64])
+def test_breen_bounds(L):
+    """Eqs. kmaxbs and the total-count bounds 8(cR)^2 <= p <= 4 pi (cR)^2;
+    per-k bounds of Eq. pkbs hold to +-1 (the derivation uses '~')."""
+    c, R = 0.5, L / 2
+    p = fb.make_plan(L, c, R)
+    assert 4 * c * R - 3.517 < p.k_max < 2 * math.pi * c * R - 2.042
+    tot = int(p.p[0] + 2 * p.p[1:].sum())
+    assert 8 * (c * R) ** 2 <= tot <= 4 * math.pi * (c * R) ** 2
+    for k, pk in enumerate(p.p):
+        assert 2 * c * R - k / 2 - 3.035 / 4 - 1 < pk < 2 * c * R - k / math.pi + 1.4 / 4 + 1
+
+
+def test_criterion_variants_differ_by_one_zero_per_k():
+    lit = fb.make_plan(32, 0.5, 16.0, "literal")
+    inc = fb.make_plan(32, 0.5, 16.0, "inclusive")
+    assert inc.k_max >= lit.k_max
+    assert np.all(inc.p[:lit.k_max + 1] == lit.p + 1)
+
+
+def _gram_errors(p):
+    """|2 pi sum_j N J_k(R_q xi_j/c) N J_k(R_q' xi_j/c) xi_j w_j - delta_qq'|
+    per k (the exact integral of Eq. gint gives delta after normalisation)."""
+    out = []
+    for k in range(p.k_max + 1):
+        NJ = p.B[k] / (p.xi * p.w)[None, :]
+        G = 2 * math.pi * (NJ * (p.xi * p.w)[None, :]) @ NJ.T
+        out.append(np.abs(G - np.eye(G.shape[0])))
+    return out
+
+
+def test_gram_identity():
+    """Sec. II-B / Fig. 2a: the largest radial quadrature error is at
+    k = 0, q1 = q2 = p_0, and it falls steeply with n_xi; at n_xi =
+    ceil(4cR) it is at rounding level once R is large (R = 64 here), while a
+    few extra nodes bring a small R (R = 32) to rounding level too."""
+    p = fb.make_plan(64, 0.5, 32.0)
+    E = _gram_errors(p)
+    worst = max(e.max() for e in E)
+    assert E[0][-1, -1] == worst                 # G(0, p_0, p_0) is the worst
+    assert worst < 1e-7
+    p_more = fb.make_plan(64, 0.5, 32.0, n_xi=p.n_xi + 12)
+    assert max(e.max() for e in _gram_errors(p_more)) < 1e-13
+    assert max(e.max() for e in _gram_errors(fb.make_plan(128, 0.5, 64.0))) < 1e-12
+
+
+def test_worked_example_psi_1_5():
+    """Sec. II-B: F f = psi^{1,5}, c = 0.5, R = 30 gives a_{1,5} = 1, all
+    others 0, to RMSE 1.2e-16 and max error 2.7e-15 (golden values)."""
+    g = _golden("worked_example_psi_1_5.txt")
+    L = int(2 * g["R"])
+    p = fb.make_plan(L, g["c"], g["R"])
+    k, qi = int(g["k"]), int(g["q"]) - 1
+    x1, x2 = p.polar_points()
+    th = np.arctan2(x2, x1)
+    radial = 1.0 / (p.c * math.sqrt(math.pi) * abs(sp.jv(k + 1, p.zeros[k][qi]))) \
+        * sp.jv(k, p.zeros[k][qi] * p.xi / p.c)
+    F = (radial[:, None] * np.exp(1j * k * th))[None]
+    a = fb.coefficients_from_polar(p, F)[0]
+    target = np.zeros(p.P, complex)
+    target[p.offset[k] + qi] = 1.0
+    err = np.abs(a - target)
+    assert math.sqrt(np.mean(err ** 2)) <= 2 * g["rmse"]
+    assert err.max() <= 2 * g["max_abs_err"]
+
+
+# --- polar Fourier transform (Eq. nufft) -------------------------------------
+def test_ndft_brute_force():
+    """Direct evaluation of the double sum of Eq. nufft with explicit loops."""
+    p = fb.make_plan(6, 0.5, 3.0)
+    rng = np.random.default_rng(3)
+    I = rng.standard_normal((2, 6, 6))
+    F = fb.ndft_polar(p, I)
+    x1, x2 = p.polar_points()
+    idx = p.pixel_index()
+    for (j, l) in [(0, 0), (1, 5), (p.n_xi - 1, p.n_theta - 1), (2, 7)]:
+        for i in range(2):
+            s = 0j
+            for a in range(6):
+                for b in range(6):
+                    s += I[i, a, b] * complex(math.cos(-2 * math.pi * (x1[j, l] * idx[a] + x2[j, l] * idx[b])),
+                                              math.sin(-2 * math.pi * (x1[j, l] * idx[a] + x2[j, l] * idx[b])))
+            assert abs(F[i, j, l] - s) < 1e-13
+
+
+def test_ndft_hermitian_half_ring():
+    """Real images: F(xi, theta + pi) = conj F(xi, theta)."""
+    p = fb.make_plan(16, 0.5, 8.0)
+    F = fb.ndft_polar(p, _masked_noise(16, 8, 2, 4))
+    h = p.n_theta // 2
+    assert np.max(np.abs(F[:, :, h:] - F[:, :, :h].conj())) < 1e-12
+
+
+# --- whole forward map T* ----------------------------------------------------
+def _rotate90(I):
+    """I'(i1, i2) = I(i2, -i1): counter-clockwise rotation by pi/2."""
+    n, L, _ = I.shape
+    o = L // 2
+    out = np.zeros_like(I)
+    for a1 in range(L):
+        for a2 in range(L):
+            s1, s2 = (a2 - o), -(a1 - o)
+            if -o <= s1 < L - o and -o <= s2 < L - o:
+                out[:, a1, a2] = I[:, s1 + o, s2 + o]
+    return out
+
+
+def _reflect(I):
+    """I'(i1, i2) = I(-i1, i2)."""
+    n, L, _ = I.shape
+    o = L // 2
+    out = np.zeros_like(I)
+    for a1 in range(L):
+        s1 = -(a1 - o)
+        if -o <= s1 < L - o:
+            out[:, a1, :] = I[:, s1 + o, :]
+    return out
+
+
+def test_rotation_and_reflection():
+    """Eqs. rot / refl: rotation by pi/2 multiplies a_{k,q} by e^{-i k pi/2};
+    reflection x -> -x conjugates.  Exact on the grid when n_theta = 0 mod 4
+    and the image vanishes for r >= R."""
+    p = fb.make_plan(16, 0.5, 8.0)
+    I = _masked_noise(16, 8, 3, 5)
+    a = fb.expand(p, I)
+    ar = fb.expand(p, _rotate90(I))
+    af = fb.expand(p, _reflect(I))
+    scale = np.max(np.abs(a))
+    assert np.max(np.abs(ar - a * np.exp(-1j * p.k_of * math.pi / 2))) < 1e-13 * scale
+    assert np.max(np.abs(af - a.conj())) < 1e-13 * scale
+
+
+def _real_operator(p):
+    """Q (p x L^2): T* with the k > 0 coefficients split into sqrt(2) Re and
+    sqrt(2) Im, so that |Q x|^2 = |a|_W^2 (both +-k terms counted)."""
+    L = p.L
+    A = fb.expand(p, np.eye(L * L).reshape(L * L, L, L))
+    p0 = p.p[0]
+    return np.concatenate([A[:, :p0].real, math.sqrt(2) * A[:, p0:].real,
+                           math.sqrt(2) * A[:, p0:].imag], axis=1).T, A
+
+
+def test_near_unitary_spectrum():
+    """Fig. 3: eigenvalues of T*T are mostly 1, none above 1 beyond the
+    quadrature error, the smallest still close to 1."""
+    p = fb.make_plan(24, 0.5, 12.0)
+    Q, _ = _real_operator(p)
+    ev = np.linalg.eigvalsh(Q @ Q.T)
+    assert ev.max() < 1.0 + 1e-3
+    assert abs(np.median(ev) - 1.0) < 1e-4
+    assert np.mean(ev > 0.99) > 0.75
+    assert ev.min() > 0.85
+
+
+def test_bessel_inequality():
+    p = fb.make_plan(16, 0.5, 8.0)
+    I = np.random.default_rng(6).standard_normal((4, 16, 16))
+    a = fb.expand(p, I)
+    normW = np.sum(np.abs(a) ** 2 * p.weights_W()[None, :], axis=1)
+    assert np.all(normW <= (1 + 1e-3) * np.sum(I ** 2, axis=(1, 2)))
+
+
+# --- adjoint and synthesis ---------------------------------------------------
+def test_adjoint_is_transpose_of_brute_force_matrix():
+    p = fb.make_plan(12, 0.5, 6.0)
+    _, A = _real_operator(p)                 # A[i, :] = T* e_i
+    rng = np.random.default_rng(7)
+    y = rng.standard_normal((2, p.P)) + 1j * rng.standard_normal((2, p.P))
+    ref = (A.conj() @ y.T).real.T.reshape(2, 12, 12)   # Re(M^H y)
+    assert np.max(np.abs(fb.adjoint(p, y) - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_adjoint_dot_product():
+    p = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((3, 16, 16))
+    y = rng.standard_normal((3, p.P)) + 1j * rng.standard_normal((3, p.P))
+    lhs = np.sum((fb.expand(p, x).conj() * y).real, axis=1)
+    rhs = np.sum(x * fb.adjoint(p, y), axis=(1, 2))
+    assert np.max(np.abs(lhs - rhs) / np.abs(lhs)) < 1e-12
+
+
+def test_synthesis_matches_analytic_inverse_transform():
+    """S a = T(W a) is the polar quadrature of sum_k,q a_{k,q} F^{-1}(psi^{k,q});
+    Eq. IFT_FB gives the same sum in closed form.  With the phase i^k that the
+    inverse transform of Eq. IPFT produces they agree to the quadrature error;
+    the phase printed in Eq. IFT_FB (i^-k) gives a different image."""
+    p = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal((2, p.P)) + 1j * rng.standard_normal((2, p.P))
+    a[:, :p.p[0]] = a[:, :p.p[0]].real
+    s_quad = fb.synthesize(p, a)
+    idx = p.pixel_index()
+    inner = (idx[:, None] ** 2 + idx[None, :] ** 2) < (p.R / 2) ** 2
+    scale = np.max(np.abs(s_quad))
+    d_der = np.max(np.abs((s_quad - fb.synthesize_analytic(p, a, "derived"))[:, inner]))
+    d_pr = np.max(np.abs((s_quad - fb.synthesize_analytic(p, a, "printed"))[:, inner]))
+    assert d_der < 1e-3 * scale
+    assert d_pr > 0.1 * scale
+
+
+# --- steerable covariance and PCA (Sec. III, Alg. 2) -------------------------
+def test_covariance_against_rotation_average_definition():
+    """Eq. cov: C_{(k,q),(k',q')} = (1/4 pi n) sum_i int_0^{2pi}
+    (a_{k,q} conj a_{k',q'} + a_{-k,q} conj a_{-k',q'}) e^{-i(k-k')alpha} d alpha,
+    evaluated by brute force over the full +-k coefficient vector with an
+    exact trapezoid rule in alpha; it must be block diagonal with the blocks
+    of Eqs. ck / ck_0 (after the k = 0 mean is removed, Alg. 2 step 1)."""
+    p = fb.make_plan(12, 0.5, 6.0)
+    rng = np.random.default_rng(10)
+    I = rng.standard_normal((7, 12, 12)) + 0.5
+    a = fb.expand(p, I)
+    n = a.shape[0]
+    mean0, blocks = fb.covariance(p, a)
+    ac = a.copy()
+    ac[:, :p.p[0]] -= mean0[None, :]
+    # full vector over k = -kmax..kmax: a_{-k,q} = conj(a_{k,q})
+    ks, cols = [], []
+    for k in range(-p.k_max, p.k_max + 1):
+        o, pk = p.offset[abs(k)], p.p[abs(k)]
+        for qi in range(pk):
+            ks.append(k)
+            cols.append(ac[:, o + qi] if k >= 0 else ac[:, o + qi].conj())
+    ks = np.array(ks)
+    Afull = np.stack(cols, axis=1)                       # (n, p)
+    # index of (-k, q) for each (k, q)
+    start = {k: int(np.argmax(ks == k)) for k in range(-p.k_max, p.k_max + 1)}
+    neg = np.array([start[-k] + (i - start[k]) for i, k in enumerate(ks)])
+    nalpha = 4 * p.k_max + 4
+    alphas = 2 * math.pi * np.arange(nalpha) / nalpha
+    C = np.zeros((ks.size, ks.size), dtype=complex)
+    for al in alphas:
+        ph = np.exp(-1j * (ks[:, None] - ks[None, :]) * al)
+        M1 = Afull.T @ Afull.conj()
+        M2 = Afull[:, neg].T @ Afull[:, neg].conj()
+        C += (M1 + M2) * ph
+    C *= (2 * math.pi / nalpha) / (4 * math.pi * n)
+    for k in range(0, p.k_max + 1):
+        sel = np.nonzero(ks == k)[0]
+        assert np.max(np.abs(C[np.ix_(sel, sel)] - blocks[k])) < 1e-12
+        other = np.nonzero(ks != k)[0]
+        assert np.max(np.abs(C[np.ix_(sel, other)])) < 1e-12
+
+
+def test_eigendecomposition_definition():
+    p = fb.make_plan(16, 0.5, 8.0)
+    a = fb.expand(p, np.random.default_rng(11).standard_normal((40, 16, 16)))
+    _, blocks = fb.covariance(p, a)
+    lams, vecs = fb.eig_blocks(blocks)
+    for C, lam, U in zip(blocks, lams, vecs):
+        assert np.all(np.diff(lam) <= 1e-15)
+        assert np.max(np.abs(C @ U - U * lam[None, :])) < 1e-12 * max(1.0, np.abs(lam).max())
+        assert np.max(np.abs(U.T @ U - np.eye(U.shape[1]))) < 1e-12
+        piv = np.argmax(np.abs(U), axis=0)
+        assert np.all(U[piv, np.arange(U.shape[1])] > 0)
+
+
+def test_white_noise_marchenko_pastur():
+    """Sec. V: for pure white noise every eigenvalue of C^(k) lies in
+    sigma^2 (1 +- sqrt(gamma_k))^2 (gamma_0 = p_0/n, gamma_k = p_k/2n), up to
+    finite-n fluctuation and the spread of T*T below 1."""
+    p = fb.make_plan(24, 0.5, 12.0)
+    n, sigma2 = 1500, 2.0
+    I = math.sqrt(sigma2) * np.random.default_rng(12).standard_normal((n, 24, 24))
+    _, blocks = fb.covariance(p, fb.expand(p, I))
+    lams, _ = fb.eig_blocks(blocks)
+    for k, lam in enumerate(lams):
+        g = p.p[k] / n if k == 0 else p.p[k] / (2 * n)
+        assert lam.max() < 1.05 * sigma2 * (1 + math.sqrt(g)) ** 2
+        assert lam.min() > 0.85 * sigma2 * (1 - math.sqrt(g)) ** 2
+
+
+def test_planted_component_recovered():
+    """A rank-one signal s_i u planted in the k = 3 block of white coefficient
+    noise is the top eigenvector of C^(3), eigenvalue ~ var(s) + sigma^2."""
+    p = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(13)
+    n = 4000
+    a = (rng.standard_normal((n, p.P)) + 1j * rng.standard_normal((n, p.P))) / math.sqrt(2)
+    a[:, :p.p[0]] = a[:, :p.p[0]].real * math.sqrt(2)
+    o, pk = p.offset[3], p.p[3]
+    u = rng.standard_normal(pk)
+    u /= np.linalg.norm(u)
+    s = 3.0 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2)
+    a[:, o:o + pk] += s[:, None] * u[None, :]
+    _, blocks = fb.covariance(p, a)
+    lams, vecs = fb.eig_blocks(blocks)
+    assert abs(abs(vecs[3][:, 0] @ u) - 1.0) < 1e-2
+    assert abs(lams[3][0] - (9.0 + 1.0)) < 0.6
+
+
+def test_topk_and_mp_selection():
+    p = fb.make_plan(16, 0.5, 8.0)
+    lams = [np.sort(np.random.default_rng(k).uniform(0, 10, pk))[::-1] for k, pk in enumerate(p.p)]
+    hs = fb.select_filter(p, lams, "topk", K=7)
+    kept = sorted([(-lams[k][l], k, l) for k in range(len(lams)) for l in range(lams[k].size)])[:7]
+    assert sum(int(h.sum()) for h in hs) == 7
+    for _, k, l in kept:
+        assert hs[k][l] == 1.0
+    hs = fb.select_filter(p, lams, "mp_wiener", sigma2=4.0, n=100)
+    for k, (lam, h) in enumerate(zip(lams, hs)):
+        g = p.p[k] / 100 if k == 0 else p.p[k] / 200
+        thr = 4.0 * (1 + math.sqrt(g)) ** 2
+        assert np.all((h > 0) == (lam > thr))
+        assert np.allclose(h[lam > thr], 1 - 4.0 / lam[lam > thr])
+
+
+def test_denoise_all_components_is_projection():
+    """With every component kept (h = 1) the filter is the identity on the
+    coefficients (mean removed then added back), so denoise = S T*."""
+    p = fb.make_plan(16, 0.5, 8.0)
+    I = _masked_noise(16, 8, 30, 14) + 1.0
+    out = fb.denoise(p, I, "all")
+    ref = fb.synthesize(p, fb.expand(p, I))
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
