@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput of the FB expansion + steerable covariance hot path (Alg. 1 steps
+3-4 and Alg. 2 steps 1-4 accumulation) at L = 128 on GB300.
+
+One step = ffb_expand + ffb_covariance(reset) over the whole stack of
+n = 100000 synthetic Gaussian-blob images (L = 128, R = 64, c = 1/2,
+SNR = 1/10; 6.55 GB, larger than L2, resident in HBM before timing).
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead (a bounded sample per step).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "images/sec FB expansion+covariance at L=128 (compensated TC vs FP32), % roofline"
+UNIT = "images/s"
+L_, C_, R_, EPS = 128, 0.5, 64.0, 1e-6
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", help="fp32|bf16|bf16x3|tf32|tf32x3|auto")
+    ap.add_argument("--n", type=int, default=0, help="override images per GPU (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per image (flops) of each kernel class, and its roofline
+# ---------------------------------------------------------------------------
+def algorithmic_flops(plan):
+    n_xi, nth, w, N, L = plan.n_xi, plan.n_theta, plan.w, plan.N, plan.L
+    pts = n_xi * (nth // 2)
+    sum_p2_sym = sum(pk * (pk + 1) // 2 for pk in plan.p)
+    return {
+        "rows_fft": (L / 2) * 5 * N * math.log2(N),
+        "cols_fft": (N / 2 + 1) * 5 * N * math.log2(N),
+        # w^2 taps x (2 FMA = 4 flop) per node + ring FFT of length n_theta per ring
+        "interp_ring": pts * w * w * 4 + n_xi * 5 * nth * math.log2(nth),
+        "bessel": 4.0 * plan.P * n_xi,
+        "covariance": 4.0 * sum_p2_sym,
+    }
+
+
+def fp32_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_rate(budget_s=15.0, max_images=64):
+    """FP64 oracle (direct NDFT, plain ring DFT, quadrature, two-pass
+    covariance) on a bounded sample of the L = 128 workload, images/s."""
+    import numpy as np
+    from oracle import fb
+    from paper_1412_0781_gb300 import data
+    op = fb.make_plan(L_, C_, R_)           # precomputation, untimed
+    imgs, _, _ = data.blob_stack(data.PRECISION_L128, n=max_images)
+    x = imgs.double().numpy()
+    fb.expand(op, x[:1])                    # warm the cached NDFT factors
+    t0 = time.perf_counter()
+    done = 0
+    while done < max_images and (time.perf_counter() - t0) < budget_s:
+        a = fb.expand(op, x[done:done + 4])
+        fb.covariance(op, a)
+        done += a.shape[0]
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(budget_s=2.0, max_images=4)
+    total_imgs, total_t = 0, 0.0
+    for _ in range(args.steps):
+        r, m, dt = oracle_rate(budget_s=max(2.0, 60.0 / max(1, args.steps)), max_images=16)
+        rates.append(r)
+        total_imgs += m
+        total_t += dt
+    value = total_imgs / total_t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "precision stack L=128 R=64 c=0.5 SNR=1/10 (n=100000)", "L": L_,
+                       "n": 100000, "oracle_sample_images": total_imgs},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d images of the n=100000 L=128 stack per run, direct NDFT" % total_imgs},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1412_0781_gb300 import Plan, data
+
+    spec = data.PRECISION_L128
+    n = args.n or spec.n
+    images, _, _ = data.blob_stack(data.StackSpec(n, spec.L, spec.R, spec.n_blobs, spec.width, spec.snr,
+                                                  spec.seed + 7919 * rank), device=dev)
+    precisions = ["fp32"] if args.precision == "auto" else [args.precision]
+    results = {}
+    for prec in precisions:
+        plan = Plan(L_, C_, R_, eps=EPS, precision=prec)
+        coef = torch.empty((n, plan.P, 2), device=dev, dtype=torch.float32)
+
+        def step():
+            plan.expand(images, out=coef)
+            plan.covariance(coef, reset=True)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        plan.sync()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = plan.launch_count()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        plan.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        prof = plan.profile_read()
+        plan.profile(False)
+        plan.sync()
+        launches = plan.launch_count() - l0
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        results[prec] = {"plan": plan, "coef": coef, "ms": ms, "prof": prof, "clocks": clocks,
+                         "launches": launches}
+    head = precisions[0]
+    r = results[head]
+    plan = r["plan"]
+    ms_step = r["ms"] / args.steps
+    value = world * n / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    flops = algorithmic_flops(plan)
+    prof = r["prof"]
+    dom = max(prof, key=lambda c: prof[c][0])
+    dom_ms, dom_calls = prof[dom]
+    sm_mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
+    share = {c: round(v[0] / sum(x[0] for x in prof.values()), 4) for c, v in prof.items()}
+    imgs_per_launch = (n * args.steps) / dom_calls if dom_calls else 0
+    achieved = flops.get(dom, 0.0) * imgs_per_launch / (dom_ms / dom_calls / 1e3) / 1e12 if dom_calls else 0.0
+    peak = fp32_peak_tflops(2070.0)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": "FP32 FFMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, max clock)",
+                "kernel_ms_per_launch": dom_ms / dom_calls, "images_per_launch": imgs_per_launch,
+                "share": share}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        hbuf = torch.empty(images.shape, dtype=torch.float32, pin_memory=True)
+        hbuf.copy_(images)
+        del images
+        torch.cuda.empty_cache()
+        dbuf = torch.empty(hbuf.shape, dtype=torch.float32, device=dev)
+        out_mean = torch.empty(plan.p[0], dtype=torch.float64, pin_memory=True)
+        out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            dbuf.copy_(hbuf, non_blocking=True)
+            plan.expand(dbuf, out=r["coef"])
+            plan.covariance(r["coef"], reset=True)
+            m, C = plan.cov_get()
+            out_mean.copy_(m)
+            out_C.copy_(C)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = max(3, args.steps // 4)
+        for _ in range(k):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
+               "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        rate, m, dt = oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d images of the n=100000 L=128 stack (%.1f s), FP64 direct NDFT + ring DFT + "
+                         "quadrature + covariance; numpy BLAS threads" % (m, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head == "fp32" else head,
+                "data": "synthetic",
+                "config": {"workload": "precision stack: n=100000 Gaussian-blob images L=128 R=64 c=0.5 "
+                                       "SNR=1/10, eps=1e-6", "L": L_, "n_per_gpu": n, "precision": head,
+                           "l2": "inputs (6.55 GB) larger than L2, no flush"},
+                "precisions": {p: {"images_per_s": world * n / (v["ms"] / args.steps / 1e3)}
+                               for p, v in results.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
+                "clocks": r["clocks"]}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

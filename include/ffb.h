@@ -1,0 +1,192 @@
+/*
+ * ffb.h -- C ABI of the GB300 fast Fourier-Bessel steerable PCA library.
+ *
+ * Method: Zhao, Shkolnisky & Singer, "Fast Steerable Principal Component
+ * Analysis" (Alg. 1 "Fast Fourier-Bessel Expansion", Alg. 2 "Steerable PCA").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are float32, row-major [n][L][L].  The first array index is the
+ *   pixel coordinate i1 (x), the second is i2 (y); both run over
+ *   i = -ceil((L-1)/2) .. floor((L-1)/2) (Sec. II), so array position a holds
+ *   i = a - L/2 (integer division).
+ * - Fourier transform sign convention: F(f)(xi) = int f(x) e^{-2 pi i x.xi}
+ *   (Sec. II).  The polar samples are F(I)(xi) = sum_i I(i) e^{-2 pi i xi.i};
+ *   the 1/(2R)^2 factor printed in Eq. nufft is not applied, so the map from
+ *   images to coefficients is close to unitary (Fig. 3).
+ * - Coefficients a_{k,q} for k = 0..k_max only (a_{-k,q} = conj a_{k,q}, Sec.
+ *   II-B), stored as interleaved complex float32 [n][P][2] (re, im) with the
+ *   index of (k, q) equal to offset[k] + (q-1): k ascending, q ascending.
+ *   Im a_{0,q} is written as exactly 0.
+ * - Pointers named d_* are DEVICE pointers owned by the caller; pointers named
+ *   h_* are HOST pointers owned by the caller.  The plan owns its tables, its
+ *   scratch memory and the covariance accumulator.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Compute calls are asynchronous on that stream; argument errors
+ *   are returned immediately, device-side errors (non-finite input, a
+ *   bounded wait that timed out, Jacobi not converged) are latched in the plan
+ *   and returned by the next call that synchronises (ffb_cov_get, ffb_eig,
+ *   ffb_sync).  No entry point aborts the process.
+ * - Every entry point returns an ffb_status; ffb_strerror() names it.
+ */
+#ifndef FFB_H
+#define FFB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffb_plan_s *ffb_plan_t;
+
+typedef enum {
+    FFB_OK = 0,
+    FFB_ERR_ARG = -1,            /* invalid argument (size, range, NULL)        */
+    FFB_ERR_CUDA = -2,           /* a CUDA runtime call failed                  */
+    FFB_ERR_OOM = -3,            /* device allocation failed                    */
+    FFB_ERR_NONFINITE = -4,      /* NaN/Inf met in an input image               */
+    FFB_ERR_NOT_CONVERGED = -5,  /* Jacobi sweep limit reached                  */
+    FFB_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up          */
+    FFB_ERR_STATE = -7,          /* call out of order (e.g. eig before cov)     */
+    FFB_ERR_UNSUPPORTED = -8     /* size/precision not supported by this build */
+} ffb_status;
+
+/* Arithmetic of the two dense contractions (radial quadrature, covariance). */
+typedef enum {
+    FFB_FP32 = 0,     /* CUDA-core FFMA, float32                              */
+    FFB_BF16 = 1,     /* tensor cores, bf16 operands, fp32 accumulation       */
+    FFB_BF16X3 = 2,   /* bf16 hi/lo split, 3 products (hh + hl + lh)          */
+    FFB_TF32 = 3,     /* tensor cores, tf32 operands, fp32 accumulation       */
+    FFB_TF32X3 = 4    /* tf32 hi/lo split, 3 products                         */
+} ffb_precision;
+
+/* Denoising modes of ffb_denoise (Sec. V). */
+typedef enum {
+    FFB_DENOISE_TOPK = 0,       /* keep the K (k,l) pairs of largest eigenvalue, gain 1 */
+    FFB_DENOISE_MP_WIENER = 1,  /* keep lambda > sigma2 (1+sqrt(gamma_k))^2 (Eq. compselect),
+                                   gain (lambda - sigma2)/lambda                          */
+    FFB_DENOISE_ALL = 2         /* every component, gain 1 (projection onto the span)    */
+} ffb_denoise_mode;
+
+/* ffb_plan -- Alg. 1 steps 1-2 (precomputation), Sec. II-A and II-B.
+ * Selects (k, q) by the sampling criterion R_{k,q+1} <= 2 pi c R (Eq.
+ * criterion1), fixes n_xi = ceil(4cR), n_theta = ceil(16cR), computes on the
+ * GPU in float64 the Bessel zeros R_{k,q}, the Gauss-Legendre rule on [0, c]
+ * and the radial table B^(k)_{q,j} = N_{k,q} J_k(R_{k,q} xi_j/c) xi_j w_j of
+ * Eq. a, and builds the type-2 NUFFT used for Eq. nufft (exponential-of-
+ * semicircle kernel, oversampling 2, width ceil(log10(1/eps)) + 2).
+ *   L in [8, 512], c in (0, 1/2], R in (0, L/2], eps in [1e-7, 1e-2],
+ *   precision an ffb_precision.  2L and n_theta must factor into 2, 3, 5.
+ * On success *out owns device memory until ffb_plan_destroy.  Synchronous. */
+int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
+             int precision, void *stream);
+
+/* Releases everything the plan owns.  NULL is accepted. */
+int ffb_plan_destroy(ffb_plan_t plan);
+
+/* Sizes of the plan, written to h_info[0..9]:
+ *   0 L, 1 k_max, 2 P (= sum_{k>=0} p_k), 3 n_xi, 4 n_theta,
+ *   5 N (oversampled grid), 6 kernel width w, 7 precision,
+ *   8 max_k p_k, 9 images per internal chunk. */
+int ffb_plan_info(ffb_plan_t plan, int *h_info);
+
+/* p_k and offset[k] (k = 0..k_max), host arrays of k_max+1 ints. */
+int ffb_plan_sizes(ffb_plan_t plan, int *h_p, int *h_offset);
+
+/* Copies the float64 setup tables to host arrays (any may be NULL):
+ * h_zeros[P] = R_{k,q}; h_xi[n_xi], h_w[n_xi] = Gauss-Legendre rule on [0,c];
+ * h_B[P*n_xi] = B^(k)_{q,j} row-major (coefficient index, j). */
+int ffb_plan_tables(ffb_plan_t plan, double *h_zeros, double *h_xi, double *h_w,
+                    double *h_B);
+
+/* Changes the arithmetic of the dense contractions (ffb_precision). */
+int ffb_set_precision(ffb_plan_t plan, int precision);
+
+/* ffb_polar -- Eq. nufft at the polar nodes with theta_l in [0, pi):
+ * d_F[n][n_xi][n_theta/2][2] (interleaved complex, float32); the other half
+ * of every ring is the complex conjugate (real images).  Exposes steps
+ * a1-a3 of the path (precorrect, oversampled FFT, interpolation). */
+int ffb_polar(ffb_plan_t plan, const float *d_images, int64_t n, float *d_F,
+              void *stream);
+
+/* ffb_expand -- Alg. 1 steps 3-4: a = T* I for n images.
+ * d_images [n][L][L] float32 -> d_coef [n][P][2] float32 (layout above).
+ * Eq. nufft by NUFFT, Eq. 1DFFT by FFT on each ring, Eq. a as a grouped
+ * contraction over k in the plan's precision.  n >= 0 (n = 0 is a no-op). */
+int ffb_expand(ffb_plan_t plan, const float *d_images, int64_t n, float *d_coef,
+               void *stream);
+
+/* ffb_expand_adjoint -- the exact adjoint T y = Re(M^H y) of ffb_expand for
+ * the inner products Re sum conj(u) v (coefficients) and sum x y (images):
+ * transposed radial quadrature, conjugate ring DFT, type-1 NUFFT, real part.
+ * d_coef [n][P][2] -> d_images [n][L][L].  The synthesis of a real image from
+ * its coefficients is ffb_expand_adjoint applied to W a with W = 1 (k = 0),
+ * 2 (k > 0). */
+int ffb_expand_adjoint(ffb_plan_t plan, const float *d_coef, int64_t n,
+                       float *d_images, void *stream);
+
+/* ffb_covariance -- Alg. 2 steps 1-4 (accumulation part): adds n coefficient
+ * vectors to the plan's float64 accumulator of the k = 0 mean (Eq. mean2) and
+ * of the blocks sum_i Re{a_k a_k^*} (Eqs. ck, ck_0).  reset != 0 clears it
+ * first.  Streaming over several calls gives the same result as one call. */
+int ffb_covariance(ffb_plan_t plan, const float *d_coef, int64_t n, int reset,
+                   void *stream);
+
+/* ffb_cov_get -- finalises the accumulator: d_mean0[p_0] = (1/n) sum a_{0,q},
+ * d_C = packed blocks C^(k) (k ascending, each p_k x p_k row-major float64),
+ * C^(k) = (1/n) Re{A A^*} with the k = 0 block centred (Eqs. ck, ck_0).
+ * Either pointer may be NULL.  Synchronises the stream; returns latched
+ * device errors. */
+int ffb_cov_get(ffb_plan_t plan, double *d_mean0, double *d_C, void *stream);
+
+/* ffb_eig -- Alg. 2 step 4: eigenpairs of every block C^(k) by a batched
+ * float64 cyclic Jacobi solver on the GPU (one CTA per block).
+ * d_evals[P]: per block descending; d_evecs packed p_k x p_k row-major,
+ * column l = u^(k)_l, each signed so its largest-magnitude entry (first on
+ * ties) is positive.  Either pointer may be NULL.  Synchronises the stream. */
+int ffb_eig(ffb_plan_t plan, double *d_evals, double *d_evecs, void *stream);
+
+/* ffb_eig_blocks -- the same batched float64 Jacobi solver applied to caller
+ * supplied symmetric blocks: d_C packed like ffb_cov_get's output (k
+ * ascending, p_k x p_k row-major).  Outputs as ffb_eig.  Synchronises. */
+int ffb_eig_blocks(ffb_plan_t plan, const double *d_C, double *d_evals, double *d_evecs,
+                   void *stream);
+
+/* ffb_denoise -- expansion, steerable covariance, eigendecomposition,
+ * selection (ffb_denoise_mode; K pairs for TOPK, sigma2 the noise variance
+ * for MP_WIENER), filtering of c_{k,l} = sum_q a_{k,q} u_l(q) (Eq. sPCAcoeff)
+ * and synthesis back to images through the adjoint with weights W.
+ * d_images [n][L][L] -> d_out [n][L][L].  Uses and overwrites the plan's
+ * covariance accumulator.  Synchronises the stream. */
+int ffb_denoise(ffb_plan_t plan, const float *d_images, int64_t n, int mode,
+                int K, double sigma2, float *d_out, void *stream);
+
+/* ffb_sync -- waits for the stream and returns the first latched device error
+ * (then clears it). */
+int ffb_sync(ffb_plan_t plan, void *stream);
+
+/* ffb_profile -- enable (1) or disable (0) per-launch timing: every kernel
+ * the plan launches is bracketed by two CUDA events on its stream.  Enabling
+ * discards earlier records. */
+int ffb_profile(ffb_plan_t plan, int enable);
+
+/* ffb_profile_read -- sums the recorded launch durations per kernel class
+ * into h_ms[16] (milliseconds) and h_calls[16] (launches), then discards the
+ * records.  Classes: 0 rows FFT, 1 column FFT, 2 interpolation + ring DFT,
+ * 3 radial quadrature, 4 covariance, 5 covariance shift/finalise, 6 Jacobi,
+ * 7 transposed quadrature, 8 inverse ring DFT + spreading, 9 inverse column
+ * FFT, 10 inverse row FFT + deconvolution, 11 steerable filter, 12 setup.
+ * Synchronises on the recorded events. */
+int ffb_profile_read(ffb_plan_t plan, double *h_ms, int64_t *h_calls);
+
+/* Number of kernel launches issued by this plan since creation (for
+ * accounting of GPU work). */
+int64_t ffb_launch_count(ffb_plan_t plan);
+
+const char *ffb_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFB_H */

@@ -1,0 +1,244 @@
+// ffb_gemm.cu -- the dense contractions of the hot path on CUDA cores (FP32):
+//   a5  radial quadrature (Eq. a):  a^(k)_{i,q} = sum_j Fhat^(k)_{i,j} B^(k)_{q,j}
+//   a6  k = 0 mean (Alg. 2 step 1, Eq. mean2)
+//   a7  covariance blocks (Eqs. ck, ck_0): sum_i Re(a_{i,q} conj a_{i,q'})
+// plus the finalisation C^(k) = acc/n (k = 0 centred).
+#include "ffb_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// a5, FP32: one CTA per (k, 32 images).  Rows of the A operand are the 64
+// (image, re/im) rows of Fhat[k] (contiguous in memory), columns of B are
+// the p_k rows of B^(k); K = n_xi.  Each thread owns 2 images x 4 q.
+// ---------------------------------------------------------------------------
+#define BES_IMG 32
+__global__ void __launch_bounds__(256)
+k_bessel_fp32(const float *__restrict__ Fhat, const float *__restrict__ Bf, const int *__restrict__ pk_,
+              const int *__restrict__ off_, int n_xi, int chunk, int nimg, int P, float2 *__restrict__ coef) {
+    extern __shared__ float sm[];
+    const int k = blockIdx.y;
+    const int pk = pk_[k], o = off_[k];
+    const int i0 = blockIdx.x * BES_IMG;
+    const int ld = n_xi + 1;
+    float *As = sm;                  // [64][ld]
+    float *Bs = sm + 64 * ld;        // [64][ld]
+    const float *Ak = Fhat + ((size_t)k * chunk + i0) * 2 * n_xi;
+    const int rows = min(BES_IMG, nimg - i0) * 2;
+    for (int t = threadIdx.x; t < 64 * n_xi; t += 256) {
+        int r = t / n_xi, j = t - r * n_xi;
+        As[r * ld + j] = (r < rows) ? __ldg(&Ak[(size_t)r * n_xi + j]) : 0.f;
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty: image pair, tx: q lane
+    for (int q0 = 0; q0 < pk; q0 += 64) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * n_xi; t += 256) {
+            int q = t / n_xi, j = t - q * n_xi;
+            Bs[q * ld + j] = (q0 + q < pk) ? __ldg(&Bf[(size_t)(o + q0 + q) * n_xi + j]) : 0.f;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+        for (int j = 0; j < n_xi; ++j) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[(ty * 4 + r) * ld + j];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[(tx + 16 * c) * ld + j];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+            const int img = i0 + ty * 2 + ii;
+            if (img >= nimg) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int q = q0 + tx + 16 * c;
+                if (q < pk) {
+                    float2 v = make_float2(acc[2 * ii][c], (k == 0) ? 0.f : acc[2 * ii + 1][c]);
+                    coef[(size_t)img * P + o + q] = v;
+                }
+            }
+        }
+    }
+}
+
+int ffb_launch_bessel_fp32(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
+    size_t smem = sizeof(float) * 2 * 64 * (size_t)(p->n_xi + 1);
+    static int attr = 0;
+    if (smem > 48 * 1024 && attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_bessel_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    dim3 g((nimg + BES_IMG - 1) / BES_IMG, p->k_max + 1);
+    ProfScope ps(p, FFB_KC_BESSEL, s);
+    k_bessel_fp32<<<g, 256, smem, s>>>(p->d_Fhat, p->d_Bf, p->d_p, p->d_off, p->n_xi, p->chunk, nimg, p->P,
+                                       (float2 *)d_coef_chunk);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_bessel(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
+    // tensor-core variants are dispatched here once available for the precision
+    return ffb_launch_bessel_fp32(p, nimg, d_coef_chunk, s);
+}
+
+// ---------------------------------------------------------------------------
+// a6/a7: covariance accumulation.  Work item (k, q0, q1) is the 64 x 64 tile
+// of block k at rows q0.., columns q1..; blockIdx.y splits the images.  Each
+// thread owns a 4 x 4 sub-tile, sums 128 images in float32 and folds the
+// partial sums into float64 registers; the CTA result is added to the
+// float64 accumulator with atomics (both the tile and, off the diagonal, its
+// transpose).  For k = 0 the values are shifted by `shift` (a pilot mean):
+// sum (a - s)(a - s)^T, finalised as C = acc/n - d d^T with d = sum(a - s)/n.
+// ---------------------------------------------------------------------------
+#define COV_TI 32
+__global__ void __launch_bounds__(256)
+k_cov_fp32(const float2 *__restrict__ coef, int64_t n, int P, const int *__restrict__ pk_,
+           const int *__restrict__ off_, const int *__restrict__ cov_off, const int4 *__restrict__ work,
+           const float *__restrict__ shift, int64_t per, double *__restrict__ acc, double *__restrict__ sum0) {
+    __shared__ float2 Xa[COV_TI][64];
+    __shared__ float2 Xb[COV_TI][64];
+    const int4 wk = work[blockIdx.x];
+    const int k = wk.x, q0 = wk.y, q1 = wk.z;
+    const int pk = pk_[k], o = off_[k];
+    const int64_t ib = (int64_t)blockIdx.y * per;
+    const int64_t ie = min(n, ib + per);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const bool do_sum = (k == 0 && q0 == q1);  // diagonal tiles of block 0 carry the mean
+    float accf[4][4];
+    double accd[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            accf[r][c] = 0.f;
+            accd[r][c] = 0.0;
+        }
+    float sf = 0.f;
+    double sd = 0.0;
+    int tiles = 0;
+    for (int64_t i = ib; i < ie; i += COV_TI) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < COV_TI * 64; t += 256) {
+            int ii = t >> 6, qq = t & 63;
+            int64_t img = i + ii;
+            float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+            if (img < ie) {
+                if (q0 + qq < pk) va = __ldg(&coef[img * P + o + q0 + qq]);
+                if (q1 + qq < pk) vb = __ldg(&coef[img * P + o + q1 + qq]);
+                if (k == 0) {
+                    va = make_float2(q0 + qq < pk ? va.x - shift[q0 + qq] : 0.f, 0.f);
+                    vb = make_float2(q1 + qq < pk ? vb.x - shift[q1 + qq] : 0.f, 0.f);
+                }
+            }
+            Xa[ii][qq] = va;
+            Xb[ii][qq] = vb;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int ii = 0; ii < COV_TI; ++ii) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = Xa[ii][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Xb[ii][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
+        }
+        if (do_sum && threadIdx.x < 64) {
+            for (int ii = 0; ii < COV_TI; ++ii) sf += Xa[ii][threadIdx.x].x;
+        }
+        if (++tiles == 4) {
+            tiles = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    accd[r][c] += (double)accf[r][c];
+                    accf[r][c] = 0.f;
+                }
+            sd += (double)sf;
+            sf = 0.f;
+        }
+    }
+    double *blk = acc + cov_off[k];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int qa = q0 + ty * 4 + r, qb = q1 + tx * 4 + c;
+            if (qa < pk && qb < pk) {
+                double v = accd[r][c] + (double)accf[r][c];
+                atomicAdd(&blk[(size_t)qa * pk + qb], v);
+                if (q0 != q1) atomicAdd(&blk[(size_t)qb * pk + qa], v);
+            }
+        }
+    if (do_sum && threadIdx.x < 64 && q0 + (int)threadIdx.x < pk)
+        atomicAdd(&sum0[q0 + threadIdx.x], sd + (double)sf);
+}
+
+// pilot shift for the k = 0 block: mean of a_0 over the first min(n, 4096)
+// images of the first batch after a reset
+__global__ void k_cov_shift(const float2 *__restrict__ coef, int64_t n, int P, int p0, float *shift) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= p0) return;
+    int64_t m = min(n, (int64_t)4096);
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += (double)coef[i * P + q].x;
+    shift[q] = (float)(s / (double)m);
+}
+
+// C^(k) = acc^(k)/n; for k = 0: C = acc/n - d d^T, mean = shift + d, d = sum0/n
+__global__ void k_cov_final(const double *__restrict__ acc, const double *__restrict__ sum0,
+                            const float *__restrict__ shift, double n, const int *__restrict__ pk_,
+                            const int *__restrict__ cov_off, double *__restrict__ Cfin, double *__restrict__ mean) {
+    const int k = blockIdx.y;
+    const int pk = pk_[k];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= pk * pk) return;
+    const int qa = e / pk, qb = e % pk;
+    double v = acc[cov_off[k] + e] / n;
+    if (k == 0) {
+        double da = sum0[qa] / n, db = sum0[qb] / n;
+        v -= da * db;
+        if (qb == 0) mean[qa] = (double)shift[qa] + da;
+    }
+    Cfin[cov_off[k] + e] = v;
+}
+
+int ffb_launch_cov_shift(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
+    ProfScope ps(p, FFB_KC_COVAUX, s);
+    k_cov_shift<<<(p->p[0] + 63) / 64, 64, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0], p->d_shift);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_cov(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
+    const int64_t per = 2048;
+    int64_t ns = (n + per - 1) / per;
+    if (ns > 65535) return FFB_ERR_ARG;
+    dim3 g(p->n_cov_work, (unsigned)ns);
+    ProfScope ps(p, FFB_KC_COV, s);
+    k_cov_fp32<<<g, 256, 0, s>>>((const float2 *)d_coef, n, p->P, p->d_p, p->d_off, p->d_cov_off, p->d_cov_work,
+                                 p->d_shift, per, p->d_acc, p->d_sum0);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_cov_final(ffb_plan_t p, cudaStream_t s) {
+    if (p->n_acc <= 0) return FFB_ERR_STATE;
+    dim3 g((p->pmax * p->pmax + 255) / 256, p->k_max + 1);
+    ProfScope ps(p, FFB_KC_COVAUX, s);
+    k_cov_final<<<g, 256, 0, s>>>(p->d_acc, p->d_sum0, p->d_shift, (double)p->n_acc, p->d_p, p->d_cov_off,
+                                  p->d_Cfin, p->d_mean);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}

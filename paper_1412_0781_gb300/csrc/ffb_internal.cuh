@@ -1,0 +1,256 @@
+// ffb_internal.cuh -- plan layout and device helpers shared by the CUDA
+// translation units of the library (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/ffb.h"
+
+#define FFB_MAX_RADIX_STAGES 16
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct FftPlanDev {
+    int n;                          // transform length
+    int nst;                        // number of Stockham stages
+    int rad[FFB_MAX_RADIX_STAGES];  // radix of each stage (4, 2, 3, 5)
+};
+
+// kernel classes for the optional per-launch event timing (ffb_profile)
+enum { FFB_KC_ROWS = 0, FFB_KC_COLS = 1, FFB_KC_INTERP = 2, FFB_KC_BESSEL = 3, FFB_KC_COV = 4,
+       FFB_KC_COVAUX = 5, FFB_KC_EIG = 6, FFB_KC_ADJ_BESSEL = 7, FFB_KC_ADJ_RING = 8,
+       FFB_KC_ADJ_COLS = 9, FFB_KC_ADJ_ROWS = 10, FFB_KC_FILTER = 11, FFB_KC_SETUP = 12,
+       FFB_NKC = 16 };
+
+struct ProfEv {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+struct ffb_plan_s {
+    // problem
+    int L, off;          // image size, pixel index offset (i = a - off)
+    double c, R, eps;
+    int precision;
+    // basis
+    int k_max, P, n_xi, n_theta, pmax;
+    std::vector<int> p, offset;   // host, k_max+1
+    std::vector<int> cov_off;     // host, k_max+2: offsets of blocks in packed C
+    int cov_total;                // sum p_k^2
+    // NUFFT
+    int N, w, h, Mh;     // fine grid size, kernel width, halo, rows of the half grid
+    double beta;         // ES kernel shape
+    FftPlanDev fftN, fftT;
+    int chunk;           // images per internal chunk
+    // device tables (float64 setup results)
+    double *d_zeros = nullptr;   // [P]
+    double *d_xi = nullptr;      // [n_xi]
+    double *d_wq = nullptr;      // [n_xi]
+    double *d_B64 = nullptr;     // [P][n_xi]
+    // device tables used by the hot path
+    float *d_Bf = nullptr;       // [P][n_xi]   fp32 copy of B
+    int *d_p = nullptr;          // [k_max+1]
+    int *d_off = nullptr;        // [k_max+1]
+    int *d_cov_off = nullptr;    // [k_max+2]
+    float *d_corr = nullptr;     // [L] 1/Psi((a-off)/N)
+    float2 *d_twN = nullptr;     // [N] e^{-2 pi i e/N}
+    float2 *d_twT = nullptr;     // [n_theta]
+    float2 *d_rad = nullptr;     // [n_xi] N xi_j as (hi, lo)
+    float4 *d_ang = nullptr;     // [n_theta/2] (cos hi, cos lo, sin hi, sin lo)
+    int4 *d_cov_work = nullptr;  // covariance work items (k, q0, q0', 0)
+    int n_cov_work = 0;
+    // scratch (chunk-sized)
+    float2 *d_H = nullptr;       // [chunk][N/2+1][L]
+    float2 *d_G = nullptr;       // [chunk][Mh][N]
+    float *d_Fhat = nullptr;     // [k_max+1][chunk][2][n_xi]
+    // covariance state
+    double *d_acc = nullptr;     // [cov_total] sum Re(a a^*), k = 0 shifted
+    double *d_sum0 = nullptr;    // [p0] sum (a0 - shift)
+    float *d_shift = nullptr;    // [p0]
+    int64_t n_acc = 0;
+    int shift_set = 0;
+    // eig results
+    double *d_Cfin = nullptr;    // [cov_total]
+    double *d_mean = nullptr;    // [p0]
+    double *d_evals = nullptr;   // [P]
+    double *d_evecs = nullptr;   // [cov_total]
+    // status word written by kernels (first nonzero error wins)
+    int *d_status = nullptr;
+    int64_t launches = 0;
+    // optional per-launch timing
+    int prof_on = 0;
+    size_t prof_used = 0;
+    std::vector<ProfEv> prof;
+};
+
+// Brackets one launch with events when profiling is on (host side).
+struct ProfScope {
+    ffb_plan_s *p;
+    cudaStream_t s;
+    int idx;
+    ProfScope(ffb_plan_s *p_, int cls, cudaStream_t s_) : p(p_), s(s_), idx(-1) {
+        if (!p->prof_on) return;
+        if (p->prof_used == p->prof.size()) {
+            ProfEv e;
+            if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
+            p->prof.push_back(e);
+        }
+        idx = (int)p->prof_used++;
+        p->prof[idx].cls = cls;
+        cudaEventRecord(p->prof[idx].a, s);
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(p->prof[idx].b, s);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ffb_flag(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Small DFTs: V[m] = sum_r v[r] e^{-+2 pi i r m / R}.
+template <bool INV>
+__device__ __forceinline__ void dft2(float2 *v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 *v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+}
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 *v) {
+    const float s = 0.86602540378443864676f;  // sin(2 pi / 3)
+    float2 t = cadd(v[1], v[2]);
+    float2 u = csub(v[1], v[2]);
+    float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    float2 r = mul_mi<INV>(cscale(u, s));   // -i s u (forward)
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+}
+template <bool INV>
+__device__ __forceinline__ void dft5(float2 *v) {
+    const float c1 = 0.30901699437494742410f;   // cos(2 pi/5)
+    const float c2 = -0.80901699437494742410f;  // cos(4 pi/5)
+    const float s1 = 0.95105651629515357212f;   // sin(2 pi/5)
+    const float s2 = 0.58778525229247312917f;   // sin(4 pi/5)
+    float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    float2 x0 = v[0];
+    float2 p1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+    float2 p2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+    float2 q1 = mul_mi<INV>(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    float2 q2 = mul_mi<INV>(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+    v[1] = cadd(p1, q1);
+    v[4] = csub(p1, q1);
+    v[2] = cadd(p2, q2);
+    v[3] = csub(p2, q2);
+}
+
+// One Stockham autosort pass sequence (decimation in time) executed by a
+// group of `nthr` threads (thread index `t` within the group) on a length-n
+// sequence in shared memory.  a: input, b: scratch; returns the buffer
+// holding the result.  The caller synchronises the group between passes via
+// `sync` (a functor) -- for a single warp this is __syncwarp().
+// Stage s with radix R and Ns = product of earlier radices maps butterfly j
+// (0 <= j < n/R) from a[j + r n/R] (twiddled by W_n^{r (j mod Ns) n/(Ns R)})
+// to b[(j/Ns) Ns R + (j mod Ns) + r Ns].
+template <bool INV, class Sync>
+__device__ __forceinline__ float2 *smem_fft(float2 *a, float2 *b, const FftPlanDev &fp,
+                                            const float2 *__restrict__ tw, int t, int nthr,
+                                            Sync sync) {
+    const int n = fp.n;
+    int Ns = 1;
+    for (int s = 0; s < fp.nst; ++s) {
+        const int R = fp.rad[s];
+        const int nb = n / R;
+        const int tstep = n / (Ns * R);
+        for (int j = t; j < nb; j += nthr) {
+            const int k = j % Ns;
+            float2 v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) v[r] = a[j + r * nb];
+#pragma unroll
+            for (int r = 1; r < 5; ++r) {
+                if (r < R) {
+                    int e = (r * k * tstep) % n;
+                    float2 wv = __ldg(&tw[e]);
+                    if (INV) wv.y = -wv.y;
+                    v[r] = cmul(v[r], wv);
+                }
+            }
+            if (R == 4) dft4<INV>(v);
+            else if (R == 2) dft2<INV>(v);
+            else if (R == 3) dft3<INV>(v);
+            else dft5<INV>(v);
+            const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) b[base + r * Ns] = v[r];
+        }
+        sync();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
+        Ns *= R;
+    }
+    return a;
+}
+
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// Exponential-of-semicircle kernel psi(x) = exp(beta (sqrt(1 - (2x/w)^2) - 1)),
+// |x| < w/2, in fine-grid units.
+__device__ __forceinline__ float es_kernel(float x, float two_over_w, float beta) {
+    float t = x * two_over_w;
+    float u = fmaxf(1.0f - t * t, 0.0f);
+    return (u > 0.0f) ? __expf(beta * (sqrtf(u) - 1.0f)) : 0.0f;
+}
+
+// Host helpers (implemented in ffb_plan.cu).
+int ffb_check_cuda(cudaError_t e);
+int ffb_ensure_scratch(ffb_plan_t plan);
+
+// Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
+int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);
+int ffb_launch_polar(ffb_plan_t plan, int nimg, float *d_F, cudaStream_t s);
+int ffb_launch_interp_ring(ffb_plan_t plan, int nimg, cudaStream_t s);
+int ffb_launch_bessel(ffb_plan_t plan, int nimg, float *d_coef_chunk, cudaStream_t s);
+int ffb_launch_cov(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
+int ffb_launch_cov_shift(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
+int ffb_launch_cov_final(ffb_plan_t plan, cudaStream_t s);
+int ffb_launch_eig(ffb_plan_t plan, cudaStream_t s);
+int ffb_launch_adjoint(ffb_plan_t plan, const float *d_coef, int64_t n, float *d_images,
+                       cudaStream_t s);
+int ffb_launch_filter(ffb_plan_t plan, const float *d_coef_in, int64_t n, const double *d_gain,
+                      float *d_coef_out, cudaStream_t s);

@@ -1,0 +1,243 @@
+"""ctypes binding of ``libffb.so`` (declared in ``include/ffb.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors must be contiguous CUDA tensors of the stated dtype; the
+binding passes their device pointers and the current torch stream.  There is
+no CPU path: if the library cannot be loaded an ``ImportError`` is raised.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffb.so")
+
+FFB_OK = 0
+STATUS = {0: "FFB_OK", -1: "FFB_ERR_ARG", -2: "FFB_ERR_CUDA", -3: "FFB_ERR_OOM",
+          -4: "FFB_ERR_NONFINITE", -5: "FFB_ERR_NOT_CONVERGED", -6: "FFB_ERR_TIMEOUT",
+          -7: "FFB_ERR_STATE", -8: "FFB_ERR_UNSUPPORTED"}
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
+DENOISE = {"topk": 0, "mp_wiener": 1, "all": 2}
+
+# every symbol declared in include/ffb.h, with (restype, argtypes)
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_pi = ctypes.POINTER(ctypes.c_int)
+_pd = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "ffb_plan": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _d, _i, _vp]),
+    "ffb_plan_destroy": (_i, [_vp]),
+    "ffb_plan_info": (_i, [_vp, _pi]),
+    "ffb_plan_sizes": (_i, [_vp, _pi, _pi]),
+    "ffb_plan_tables": (_i, [_vp, _pd, _pd, _pd, _pd]),
+    "ffb_set_precision": (_i, [_vp, _i]),
+    "ffb_polar": (_i, [_vp, _vp, _i64, _vp, _vp]),
+    "ffb_expand": (_i, [_vp, _vp, _i64, _vp, _vp]),
+    "ffb_expand_adjoint": (_i, [_vp, _vp, _i64, _vp, _vp]),
+    "ffb_covariance": (_i, [_vp, _vp, _i64, _i, _vp]),
+    "ffb_cov_get": (_i, [_vp, _vp, _vp, _vp]),
+    "ffb_eig": (_i, [_vp, _vp, _vp, _vp]),
+    "ffb_eig_blocks": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ffb_denoise": (_i, [_vp, _vp, _i64, _i, _i, _d, _vp, _vp]),
+    "ffb_sync": (_i, [_vp, _vp]),
+    "ffb_profile": (_i, [_vp, _i]),
+    "ffb_profile_read": (_i, [_vp, _pd, ctypes.POINTER(ctypes.c_int64)]),
+    "ffb_launch_count": (_i64, [_vp]),
+    "ffb_strerror": (ctypes.c_char_p, [_i]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libffb.so once and declare its signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libffb.so not built (run __graft_entry__.build()): " + path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class FFBError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status),
+                                          load().ffb_strerror(status).decode()))
+
+
+def _check(status, where):
+    if status != FFB_OK:
+        raise FFBError(status, where)
+
+
+def _ptr(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns an ffb plan (device tables, scratch, covariance accumulator)."""
+
+    def __init__(self, L, c=0.5, R=None, eps=1e-6, precision="fp32", stream=None):
+        lib = load()
+        R = L / 2.0 if R is None else float(R)
+        h = ctypes.c_void_p()
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.ffb_plan(ctypes.byref(h), int(L), float(c), R, float(eps), prec, _stream(stream)),
+               "ffb_plan")
+        self._h = h
+        info = (ctypes.c_int * 10)()
+        _check(lib.ffb_plan_info(h, info), "ffb_plan_info")
+        (self.L, self.k_max, self.P, self.n_xi, self.n_theta, self.N, self.w,
+         self.precision, self.pmax, self.chunk) = list(info)
+        self.c, self.R, self.eps = float(c), R, float(eps)
+        pk = (ctypes.c_int * (self.k_max + 1))()
+        off = (ctypes.c_int * (self.k_max + 1))()
+        _check(lib.ffb_plan_sizes(h, pk, off), "ffb_plan_sizes")
+        self.p = list(pk)
+        self.offset = list(off)
+        self.cov_total = sum(v * v for v in self.p)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ffb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- host-side accessors ------------------------------------------------
+    def tables(self):
+        """float64 setup tables: (zeros[P], xi[n_xi], w[n_xi], B[P, n_xi])."""
+        import numpy as np
+        z = np.zeros(self.P)
+        xi = np.zeros(self.n_xi)
+        w = np.zeros(self.n_xi)
+        B = np.zeros((self.P, self.n_xi))
+        f = lambda a: a.ctypes.data_as(_pd)
+        _check(load().ffb_plan_tables(self._h, f(z), f(xi), f(w), f(B)), "ffb_plan_tables")
+        return z, xi, w, B
+
+    def set_precision(self, precision):
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(load().ffb_set_precision(self._h, prec), "ffb_set_precision")
+        self.precision = prec
+
+    KERNEL_CLASSES = ["rows_fft", "cols_fft", "interp_ring", "bessel", "covariance", "cov_aux", "jacobi",
+                      "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup"]
+
+    def profile(self, enable=True):
+        _check(load().ffb_profile(self._h, int(bool(enable))), "ffb_profile")
+
+    def profile_read(self):
+        """{class: (total_ms, launches)} of the launches recorded since profile(True)."""
+        ms = (ctypes.c_double * 16)()
+        calls = (ctypes.c_int64 * 16)()
+        _check(load().ffb_profile_read(self._h, ms, calls), "ffb_profile_read")
+        return {name: (ms[i], int(calls[i])) for i, name in enumerate(self.KERNEL_CLASSES) if calls[i]}
+
+    def launch_count(self):
+        return int(load().ffb_launch_count(self._h))
+
+    # -- compute (all asynchronous on the current stream unless noted) ------
+    def polar(self, images, out=None, stream=None):
+        n = images.shape[0]
+        if out is None:
+            out = torch.empty((n, self.n_xi, self.n_theta // 2, 2), device=images.device, dtype=torch.float32)
+        _check(load().ffb_polar(self._h, _ptr(images, torch.float32, "images"), n,
+                                _ptr(out, torch.float32, "out"), _stream(stream)), "ffb_polar")
+        return out
+
+    def expand(self, images, out=None, stream=None):
+        """images float32 (n, L, L) -> coefficients float32 (n, P, 2)."""
+        n = images.shape[0]
+        if out is None:
+            out = torch.empty((n, self.P, 2), device=images.device, dtype=torch.float32)
+        _check(load().ffb_expand(self._h, _ptr(images, torch.float32, "images"), n,
+                                 _ptr(out, torch.float32, "out"), _stream(stream)), "ffb_expand")
+        return out
+
+    def expand_adjoint(self, coef, out=None, stream=None):
+        """coefficients float32 (n, P, 2) -> images float32 (n, L, L)."""
+        n = coef.shape[0]
+        if out is None:
+            out = torch.empty((n, self.L, self.L), device=coef.device, dtype=torch.float32)
+        _check(load().ffb_expand_adjoint(self._h, _ptr(coef, torch.float32, "coef"), n,
+                                         _ptr(out, torch.float32, "out"), _stream(stream)),
+               "ffb_expand_adjoint")
+        return out
+
+    def covariance(self, coef, reset=True, stream=None):
+        n = coef.shape[0]
+        _check(load().ffb_covariance(self._h, _ptr(coef, torch.float32, "coef"), n, int(bool(reset)),
+                                     _stream(stream)), "ffb_covariance")
+
+    def cov_get(self, device="cuda", stream=None):
+        """Synchronising: (mean0 float64 (p_0,), packed C float64 (sum p_k^2,))."""
+        mean = torch.empty(self.p[0], device=device, dtype=torch.float64)
+        C = torch.empty(self.cov_total, device=device, dtype=torch.float64)
+        _check(load().ffb_cov_get(self._h, _ptr(mean, torch.float64, "mean"), _ptr(C, torch.float64, "C"),
+                                  _stream(stream)), "ffb_cov_get")
+        return mean, C
+
+    def eig(self, device="cuda", stream=None):
+        """Synchronising: (evals float64 (P,), packed evecs float64 (sum p_k^2,))."""
+        ev = torch.empty(self.P, device=device, dtype=torch.float64)
+        U = torch.empty(self.cov_total, device=device, dtype=torch.float64)
+        _check(load().ffb_eig(self._h, _ptr(ev, torch.float64, "evals"), _ptr(U, torch.float64, "evecs"),
+                              _stream(stream)), "ffb_eig")
+        return ev, U
+
+    def eig_blocks(self, C, stream=None):
+        """Synchronising: Jacobi eigenpairs of caller-supplied packed blocks."""
+        ev = torch.empty(self.P, device=C.device, dtype=torch.float64)
+        U = torch.empty(self.cov_total, device=C.device, dtype=torch.float64)
+        _check(load().ffb_eig_blocks(self._h, _ptr(C, torch.float64, "C"), _ptr(ev, torch.float64, "evals"),
+                                     _ptr(U, torch.float64, "evecs"), _stream(stream)), "ffb_eig_blocks")
+        return ev, U
+
+    def denoise(self, images, mode="topk", K=0, sigma2=0.0, out=None, stream=None):
+        n = images.shape[0]
+        if out is None:
+            out = torch.empty_like(images)
+        m = DENOISE[mode] if isinstance(mode, str) else int(mode)
+        _check(load().ffb_denoise(self._h, _ptr(images, torch.float32, "images"), n, m, int(K),
+                                  float(sigma2), _ptr(out, torch.float32, "out"), _stream(stream)),
+               "ffb_denoise")
+        return out
+
+    def sync(self, stream=None):
+        _check(load().ffb_sync(self._h, _stream(stream)), "ffb_sync")
+
+    # -- helpers for packed outputs ----------------------------------------
+    def unpack_blocks(self, packed):
+        """Packed (sum p_k^2,) -> list of (p_k, p_k) views."""
+        out, o = [], 0
+        for pk in self.p:
+            out.append(packed[o:o + pk * pk].view(pk, pk))
+            o += pk * pk
+        return out
