@@ -121,7 +121,7 @@ def fp32_peak_tflops(sm_mhz):
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_rate(budget_s=15.0, max_images=64):
+def oracle_rate(budget_s=15.0, max_images=1024):
     """FP64 oracle (direct NDFT, plain ring DFT, quadrature, two-pass
     covariance) on a bounded sample of the L = 128 workload, images/s."""
     import numpy as np

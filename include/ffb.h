@@ -153,6 +153,33 @@ int ffb_eig(ffb_plan_t plan, double *d_evals, double *d_evecs, void *stream);
 int ffb_eig_blocks(ffb_plan_t plan, const double *d_C, double *d_evals, double *d_evecs,
                    void *stream);
 
+/* ffb_select -- Sec. V component selection from the eigenpairs of the last
+ * ffb_eig/ffb_denoise call: gains h^(k)_l per ffb_denoise_mode (K pairs for
+ * TOPK, noise variance sigma2 and image count n for MP_WIENER), stored in the
+ * plan together with the filter matrices M^(k) = U^(k) diag(h^(k)) U^(k)T
+ * used by ffb_filter.  Optionally copies the gains to h_gain[P] (host, may be
+ * NULL).  Synchronises. */
+int ffb_select(ffb_plan_t plan, int mode, int K, double sigma2, int64_t n, double *h_gain,
+               void *stream);
+
+/* ffb_filter -- applies the selected steerable filter to coefficients:
+ * a_out^(k) = M^(k) (a^(k) - m) + m with m the k = 0 mean (Alg. 2 step 1),
+ * i.e. the projection / shrinkage of c_{k,l} = sum_q a_{k,q} u_l(q)
+ * (Eq. sPCAcoeff) mapped back to the Fourier-Bessel basis.
+ * flags bit 0 (FFB_FILTER_LINEAR): drop the mean terms (the linear part,
+ * which is also the map's own transpose); bit 1 (FFB_FILTER_WEIGHT): multiply
+ * the result by W (1 for k = 0, 2 for k > 0).  In place allowed.  Requires a
+ * prior ffb_select. */
+int ffb_filter(ffb_plan_t plan, const float *d_coef_in, int64_t n, float *d_coef_out, int flags,
+               void *stream);
+#define FFB_FILTER_LINEAR 1
+#define FFB_FILTER_WEIGHT 2
+
+/* ffb_weight -- d_out = W a (W = 1 on k = 0 coefficients, 2 on k > 0), the
+ * weights that turn the adjoint into the synthesis of a real image from its
+ * k >= 0 coefficients.  In place allowed. */
+int ffb_weight(ffb_plan_t plan, const float *d_coef_in, int64_t n, float *d_coef_out, void *stream);
+
 /* ffb_denoise -- expansion, steerable covariance, eigendecomposition,
  * selection (ffb_denoise_mode; K pairs for TOPK, sigma2 the noise variance
  * for MP_WIENER), filtering of c_{k,l} = sum_q a_{k,q} u_l(q) (Eq. sPCAcoeff)

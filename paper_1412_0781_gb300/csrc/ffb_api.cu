@@ -1,5 +1,7 @@
 // ffb_api.cu -- C ABI entry points of the hot path (see include/ffb.h).
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "ffb_internal.cuh"
 
@@ -139,13 +141,95 @@ extern "C" int ffb_expand_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, 
     return ffb_launch_adjoint(p, d_coef, n, d_images, (cudaStream_t)stream);
 }
 
-extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int mode, int K, double sigma2,
-                           float *d_out, void *stream) {
-    (void)p; (void)d_images; (void)n; (void)mode; (void)K; (void)sigma2; (void)d_out; (void)stream;
-    return FFB_ERR_UNSUPPORTED;
+// Selection of the steerable components (Sec. V), host side: gains h for
+// every (k, l) from the per-block descending eigenvalues.
+static void select_gains(ffb_plan_t p, const std::vector<double> &ev, int mode, int K, double sigma2, int64_t n,
+                         std::vector<double> &h) {
+    h.assign(p->P, 0.0);
+    if (mode == FFB_DENOISE_ALL) {
+        h.assign(p->P, 1.0);
+        return;
+    }
+    if (mode == FFB_DENOISE_TOPK) {
+        // rank pairs (k, l) by eigenvalue, ties by smaller k then smaller l
+        std::vector<int> idx(p->P);
+        std::vector<int> kof(p->P);
+        for (int k = 0; k <= p->k_max; ++k)
+            for (int l = 0; l < p->p[k]; ++l) kof[p->offset[k] + l] = k;
+        for (int i = 0; i < p->P; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            if (ev[a] != ev[b]) return ev[a] > ev[b];
+            if (kof[a] != kof[b]) return kof[a] < kof[b];
+            return a < b;
+        });
+        for (int i = 0; i < K && i < p->P; ++i) h[idx[i]] = 1.0;
+        return;
+    }
+    // Marchenko-Pastur edge (Eq. compselect) with the Wiener gain (lambda - sigma2)/lambda
+    for (int k = 0; k <= p->k_max; ++k) {
+        double gamma = (k == 0) ? (double)p->p[k] / (double)n : (double)p->p[k] / (2.0 * (double)n);
+        double thr = sigma2 * (1.0 + std::sqrt(gamma)) * (1.0 + std::sqrt(gamma));
+        for (int l = 0; l < p->p[k]; ++l) {
+            double lam = ev[p->offset[k] + l];
+            if (lam > thr) h[p->offset[k] + l] = (lam - sigma2) / lam;
+        }
+    }
 }
 
-int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_images, cudaStream_t s) {
-    (void)p; (void)d_coef; (void)n; (void)d_images; (void)s;
-    return FFB_ERR_UNSUPPORTED;
+extern "C" int ffb_select(ffb_plan_t p, int mode, int K, double sigma2, int64_t n, double *h_gain, void *stream) {
+    if (!p) return FFB_ERR_ARG;
+    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_ALL) return FFB_ERR_ARG;
+    if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
+    if (mode == FFB_DENOISE_MP_WIENER && (!(sigma2 >= 0.0) || n <= 0)) return FFB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->d_gain) CK(ffb_check_cuda(cudaMalloc(&p->d_gain, sizeof(double) * p->P)));
+    if (!p->d_M) CK(ffb_check_cuda(cudaMalloc(&p->d_M, sizeof(float) * p->cov_total)));
+    std::vector<double> ev(p->P);
+    CK(ffb_check_cuda(cudaMemcpyAsync(ev.data(), p->d_evals, sizeof(double) * p->P, cudaMemcpyDeviceToHost, s)));
+    CK(read_status(p, s));
+    std::vector<double> h;
+    select_gains(p, ev, mode, K, sigma2, n, h);
+    if (h_gain) std::copy(h.begin(), h.end(), h_gain);
+    CK(ffb_check_cuda(cudaMemcpyAsync(p->d_gain, h.data(), sizeof(double) * p->P, cudaMemcpyHostToDevice, s)));
+    CK(ffb_launch_filter_matrix(p, s));
+    p->selected = 1;
+    return read_status(p, s);
+}
+
+extern "C" int ffb_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, int flags, void *stream) {
+    if (!p || n < 0 || (n > 0 && (!d_coef_in || !d_coef_out)) || (flags & ~3)) return FFB_ERR_ARG;
+    if (!p->selected) return FFB_ERR_STATE;
+    if (n == 0) return FFB_OK;
+    return ffb_launch_filter(p, d_coef_in, n, d_coef_out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int ffb_weight(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, void *stream) {
+    if (!p || n < 0 || (n > 0 && (!d_coef_in || !d_coef_out))) return FFB_ERR_ARG;
+    if (n == 0) return FFB_OK;
+    return ffb_launch_weight(p, d_coef_in, n, d_coef_out, (cudaStream_t)stream);
+}
+
+extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int mode, int K, double sigma2,
+                           float *d_out, void *stream) {
+    if (!p || n <= 0 || !d_images || !d_out) return FFB_ERR_ARG;
+    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_ALL) return FFB_ERR_ARG;
+    if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
+    if (mode == FFB_DENOISE_MP_WIENER && !(sigma2 >= 0.0)) return FFB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->den_cap < n) {
+        if (p->d_coef_den) cudaFree(p->d_coef_den);
+        p->d_coef_den = nullptr;
+        p->den_cap = 0;
+        CK(ffb_check_cuda(cudaMalloc(&p->d_coef_den, sizeof(float2) * (size_t)n * p->P)));
+        p->den_cap = n;
+    }
+    float *coef = (float *)p->d_coef_den;
+    CK(ffb_expand(p, d_images, n, coef, stream));
+    CK(ffb_covariance(p, coef, n, 1, stream));
+    CK(ffb_launch_cov_final(p, s));
+    CK(ffb_launch_eig(p, s));
+    CK(ffb_select(p, mode, K, sigma2, n, nullptr, stream));
+    CK(ffb_launch_filter(p, coef, n, coef, FFB_FILTER_WEIGHT, s));
+    CK(ffb_launch_adjoint(p, coef, n, d_out, s));
+    return read_status(p, s);
 }

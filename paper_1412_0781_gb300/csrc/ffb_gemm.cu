@@ -242,3 +242,106 @@ int ffb_launch_cov_final(ffb_plan_t p, cudaStream_t s) {
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// a9: steerable filter.  M^(k) = U^(k) diag(h^(k)) U^(k)T (one CTA per k), then
+// a_out = W_k (M^(k) (a - m) + m) with m the k = 0 mean (zero for k > 0) and
+// W_k = 1 (k = 0), 2 (k > 0), i.e. the coefficients of the filtered image
+// ready for the synthesis S = T W (Eq. sPCAcoeff filtered and recombined).
+// ---------------------------------------------------------------------------
+__global__ void k_filter_matrix(const double *__restrict__ U, const double *__restrict__ gain,
+                                const int *__restrict__ pk_, const int *__restrict__ off_,
+                                const int *__restrict__ cov_off, float *__restrict__ M) {
+    const int k = blockIdx.x;
+    const int pk = pk_[k], o = off_[k];
+    const double *Uk = U + cov_off[k];
+    for (int e = threadIdx.x; e < pk * pk; e += blockDim.x) {
+        const int a = e / pk, b = e % pk;
+        double s = 0.0;
+        for (int l = 0; l < pk; ++l) s += Uk[a * pk + l] * gain[o + l] * Uk[b * pk + l];
+        M[cov_off[k] + e] = (float)s;
+    }
+}
+
+#define FIL_IMG 32
+__global__ void __launch_bounds__(256)
+k_filter(const float2 *__restrict__ cin, float2 *__restrict__ cout, int64_t n, int P, const float *__restrict__ M,
+         const double *__restrict__ mean, const int *__restrict__ pk_, const int *__restrict__ off_,
+         const int *__restrict__ cov_off, int flags) {
+    extern __shared__ float smf[];
+    const int k = blockIdx.y;
+    const int pk = pk_[k], o = off_[k];
+    const int64_t i0 = (int64_t)blockIdx.x * FIL_IMG;
+    const bool affine = !(flags & 1) && k == 0;
+    float *Ms = smf;                          // [pk][pk]
+    float2 *X = (float2 *)(smf + pk * pk);    // [FIL_IMG][pk]
+    for (int e = threadIdx.x; e < pk * pk; e += blockDim.x) Ms[e] = M[cov_off[k] + e];
+    for (int t = threadIdx.x; t < FIL_IMG * pk; t += blockDim.x) {
+        const int ii = t / pk, q = t - ii * pk;
+        float2 v = make_float2(0.f, 0.f);
+        if (i0 + ii < n) {
+            v = cin[(i0 + ii) * P + o + q];
+            if (k == 0) v.y = 0.f;
+            if (affine) v.x -= (float)mean[q];
+        }
+        X[t] = v;
+    }
+    __syncthreads();
+    const float wk = ((flags & 2) && k > 0) ? 2.f : 1.f;
+    for (int t = threadIdx.x; t < FIL_IMG * pk; t += blockDim.x) {
+        const int ii = t / pk, a = t - ii * pk;
+        if (i0 + ii >= n) continue;
+        float sx = 0.f, sy = 0.f;
+        for (int b = 0; b < pk; ++b) {
+            const float m = Ms[a * pk + b];
+            const float2 x = X[ii * pk + b];
+            sx = fmaf(m, x.x, sx);
+            sy = fmaf(m, x.y, sy);
+        }
+        if (affine) sx += (float)mean[a];
+        cout[(i0 + ii) * P + o + a] = make_float2(wk * sx, wk * sy);
+    }
+}
+
+__global__ void k_weight(const float2 *__restrict__ cin, float2 *__restrict__ cout, int64_t total, int P, int p0) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int q = (int)(t % P);
+    float2 v = cin[t];
+    if (q < p0) v.y = 0.f;
+    const float wk = (q < p0) ? 1.f : 2.f;
+    cout[t] = make_float2(wk * v.x, wk * v.y);
+}
+
+int ffb_launch_filter_matrix(ffb_plan_t p, cudaStream_t s) {
+    ProfScope ps(p, FFB_KC_FILTER, s);
+    k_filter_matrix<<<p->k_max + 1, 256, 0, s>>>(p->d_evecs, p->d_gain, p->d_p, p->d_off, p->d_cov_off, p->d_M);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, int flags,
+                      cudaStream_t s) {
+    const size_t smem = sizeof(float) * (size_t)p->pmax * p->pmax + sizeof(float2) * FIL_IMG * (size_t)p->pmax;
+    static int attr = 0;
+    if (smem > 48 * 1024 && attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    dim3 g((unsigned)((n + FIL_IMG - 1) / FIL_IMG), p->k_max + 1);
+    ProfScope ps(p, FFB_KC_FILTER, s);
+    k_filter<<<g, 256, smem, s>>>((const float2 *)d_coef_in, (float2 *)d_coef_out, n, p->P, p->d_M, p->d_mean,
+                                  p->d_p, p->d_off, p->d_cov_off, flags);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_weight(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, cudaStream_t s) {
+    const int64_t total = n * (int64_t)p->P;
+    ProfScope ps(p, FFB_KC_FILTER, s);
+    k_weight<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const float2 *)d_coef_in, (float2 *)d_coef_out, total,
+                                                           p->P, p->p[0]);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}

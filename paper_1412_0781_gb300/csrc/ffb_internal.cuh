@@ -77,6 +77,12 @@ struct ffb_plan_s {
     double *d_mean = nullptr;    // [p0]
     double *d_evals = nullptr;   // [P]
     double *d_evecs = nullptr;   // [cov_total]
+    // denoising
+    float2 *d_coef_den = nullptr;  // [den_cap][P]
+    int64_t den_cap = 0;
+    double *d_gain = nullptr;      // [P]
+    float *d_M = nullptr;          // [cov_total] U diag(h) U^T per block
+    int selected = 0;              // filter matrices valid
     // status word written by kernels (first nonzero error wins)
     int *d_status = nullptr;
     int64_t launches = 0;
@@ -252,5 +258,7 @@ int ffb_launch_cov_final(ffb_plan_t plan, cudaStream_t s);
 int ffb_launch_eig(ffb_plan_t plan, cudaStream_t s);
 int ffb_launch_adjoint(ffb_plan_t plan, const float *d_coef, int64_t n, float *d_images,
                        cudaStream_t s);
-int ffb_launch_filter(ffb_plan_t plan, const float *d_coef_in, int64_t n, const double *d_gain,
-                      float *d_coef_out, cudaStream_t s);
+int ffb_launch_filter_matrix(ffb_plan_t plan, cudaStream_t s);
+int ffb_launch_filter(ffb_plan_t plan, const float *d_coef_in, int64_t n, float *d_coef_out, int flags,
+                      cudaStream_t s);
+int ffb_launch_weight(ffb_plan_t plan, const float *d_coef_in, int64_t n, float *d_coef_out, cudaStream_t s);

@@ -38,6 +38,9 @@ SIGNATURES = {
     "ffb_cov_get": (_i, [_vp, _vp, _vp, _vp]),
     "ffb_eig": (_i, [_vp, _vp, _vp, _vp]),
     "ffb_eig_blocks": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ffb_select": (_i, [_vp, _i, _i, _d, _i64, _pd, _vp]),
+    "ffb_filter": (_i, [_vp, _vp, _i64, _vp, _i, _vp]),
+    "ffb_weight": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_denoise": (_i, [_vp, _vp, _i64, _i, _i, _d, _vp, _vp]),
     "ffb_sync": (_i, [_vp, _vp]),
     "ffb_profile": (_i, [_vp, _i]),
@@ -219,6 +222,37 @@ class Plan:
         _check(load().ffb_eig_blocks(self._h, _ptr(C, torch.float64, "C"), _ptr(ev, torch.float64, "evals"),
                                      _ptr(U, torch.float64, "evecs"), _stream(stream)), "ffb_eig_blocks")
         return ev, U
+
+    def select(self, mode="topk", K=0, sigma2=0.0, n=0, stream=None):
+        """Synchronising: gains h (numpy, P) of the selected components; stores
+        the filter matrices in the plan."""
+        import numpy as np
+        m = DENOISE[mode] if isinstance(mode, str) else int(mode)
+        h = np.zeros(self.P)
+        _check(load().ffb_select(self._h, m, int(K), float(sigma2), int(n), h.ctypes.data_as(_pd),
+                                 _stream(stream)), "ffb_select")
+        return h
+
+    def filter(self, coef, linear=False, weight=False, out=None, stream=None):
+        n = coef.shape[0]
+        if out is None:
+            out = torch.empty_like(coef)
+        flags = (1 if linear else 0) | (2 if weight else 0)
+        _check(load().ffb_filter(self._h, _ptr(coef, torch.float32, "coef"), n, _ptr(out, torch.float32, "out"),
+                                 flags, _stream(stream)), "ffb_filter")
+        return out
+
+    def weight(self, coef, out=None, stream=None):
+        n = coef.shape[0]
+        if out is None:
+            out = torch.empty_like(coef)
+        _check(load().ffb_weight(self._h, _ptr(coef, torch.float32, "coef"), n, _ptr(out, torch.float32, "out"),
+                                 _stream(stream)), "ffb_weight")
+        return out
+
+    def synthesize(self, coef, out=None, stream=None):
+        """Real images of the truncated expansion: adjoint(W a)."""
+        return self.expand_adjoint(self.weight(coef, stream=stream), out=out, stream=stream)
 
     def denoise(self, images, mode="topk", K=0, sigma2=0.0, out=None, stream=None):
         n = images.shape[0]
