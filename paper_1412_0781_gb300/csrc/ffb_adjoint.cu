@@ -264,6 +264,7 @@ static int set_smem(const void *fn, size_t bytes, int *cache) {
 int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_images, cudaStream_t s) {
     int e = ffb_ensure_scratch(p);
     if (e) return e;
+    if ((e = ffb_ensure_scratch_grid(p))) return e;
     const int N = p->N, L = p->L, Nh = N / 2 + 1;
     static int a_bes = 0, a_ring = 0, a_cols = 0, a_rows = 0;
     const size_t sm_bes = sizeof(float) * 2 * 64 * (size_t)(p->pmax + 1);

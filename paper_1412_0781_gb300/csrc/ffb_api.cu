@@ -59,8 +59,12 @@ extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *
     const size_t per = (size_t)p->n_xi * (p->n_theta / 2) * 2;
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, n - i0);
-        CK(ffb_launch_grid(p, d_images, i0, m, s));
-        CK(ffb_launch_polar(p, m, d_F + (size_t)i0 * per, s));
+        if (p->fused) {
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, (float2 *)(d_F + (size_t)i0 * per), s));
+        } else {
+            CK(ffb_launch_grid(p, d_images, i0, m, s));
+            CK(ffb_launch_polar(p, m, d_F + (size_t)i0 * per, s));
+        }
     }
     return FFB_OK;
 }
@@ -72,8 +76,13 @@ extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float 
     CK(ffb_ensure_scratch(p));
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, n - i0);
-        CK(ffb_launch_grid(p, d_images, i0, m, s));
-        CK(ffb_launch_interp_ring(p, m, s));
+        if (p->fused) {
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s));
+            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, s));
+        } else {
+            CK(ffb_launch_grid(p, d_images, i0, m, s));
+            CK(ffb_launch_interp_ring(p, m, s));
+        }
         CK(ffb_launch_bessel(p, m, d_coef + (size_t)i0 * p->P * 2, s));
     }
     return FFB_OK;

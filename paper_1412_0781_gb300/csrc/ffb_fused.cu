@@ -1,0 +1,333 @@
+// ffb_fused.cu -- steps a1-a4 with the oversampled grid held in shared memory.
+//
+// One CTA per (image, half).  Half 0 owns the polar nodes with xi1 >= 0
+// (theta in [0, pi/2]), half 1 those with xi1 < 0 (theta in (pi/2, pi)); all
+// have xi2 >= 0.  The grid values a half needs are G[m1][m2] for
+// m2 in [-h, N/2 + h] and m1 in [-h, N/2 + h] (half 0) or [-N/2 - h, h]
+// (half 1): a (N/2 + 1 + 2h)^2 block that fits in one SM's shared memory
+// for N <= 256 (137 x 137 complex = 150 KB at N = 256, w = 8).
+//
+// Phase 1  rows: for pixel rows a1 (two per complex FFT), the length-N DFT
+//          over i2 of I(i) corr(i1) corr(i2) placed at i2 mod N; the outputs
+//          m2 in [-h, N/2 + h] are stored in column a1 of S[m2 + h][.].
+// Phase 2  columns: for each m2 row of S, the length-N DFT over i1 (entries
+//          placed at i1 mod N); the half's m1 range overwrites the row in
+//          place (the row is read completely before it is written).
+// Phase 3  interpolation of the half's nodes from S (w x w taps of the ES
+//          kernel, node coordinates in double-float as in ffb_nufft.cu), the
+//          result written to the polar buffer F[img][j][l], l < n_theta/2.
+//
+// A second kernel completes every half ring with F(theta + pi) = conj F(theta)
+// and takes the length-n_theta FFT of Eq. 1DFFT.
+//
+// Both halves compute the same row transforms (phase 1); the columns and the
+// nodes are split.
+#include "ffb_internal.cuh"
+
+#define FUS_WARPS 16
+#define FUS_NT (32 * FUS_WARPS)
+#define RFFT_RB 8
+
+// ---------------------------------------------------------------------------
+// Stockham FFT of compile-time power-of-two length by one warp (radix 4,
+// then one radix-2 stage when log2(N) is odd).  Same pass structure as
+// smem_fft, with every division and modulo by a power of two.
+// ---------------------------------------------------------------------------
+template <int N, bool INV>
+__device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const float2 *__restrict__ tw, int lane) {
+    constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9 : (N == 1024) ? 10 : -1;
+    static_assert(LOG > 0, "power-of-two length 64..1024");
+    constexpr int N4 = LOG / 2;           // radix-4 stages
+    constexpr bool TAIL2 = (LOG & 1);     // one radix-2 stage
+#pragma unroll
+    for (int s = 0; s < N4; ++s) {
+        const int Ns = 1 << (2 * s);
+        constexpr int nb = N / 4;
+        const int tshift = LOG - 2 * s - 2;   // tstep = N / (Ns * 4)
+#pragma unroll
+        for (int jj = 0; jj < nb / 32; ++jj) {
+            const int j = lane + 32 * jj;
+            const int k = j & (Ns - 1);
+            float2 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r] = a[j + r * nb];
+#pragma unroll
+            for (int r = 1; r < 4; ++r) {
+                float2 wv = __ldg(&tw[((r * k) << tshift) & (N - 1)]);
+                if (INV) wv.y = -wv.y;
+                v[r] = cmul(v[r], wv);
+            }
+            dft4<INV>(v);
+            const int base = ((j >> (2 * s)) << (2 * s + 2)) + k;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[base + r * Ns] = v[r];
+        }
+        __syncwarp();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    if (TAIL2) {
+        constexpr int Ns = 1 << (2 * N4);
+        constexpr int nb = N / 2;
+#pragma unroll
+        for (int jj = 0; jj < nb / 32; ++jj) {
+            const int j = lane + 32 * jj;
+            const int k = j & (Ns - 1);
+            float2 v[2];
+            v[0] = a[j];
+            v[1] = a[j + nb];
+            float2 wv = __ldg(&tw[k & (N - 1)]);  // tstep = 1
+            if (INV) wv.y = -wv.y;
+            v[1] = cmul(v[1], wv);
+            dft2<INV>(v);
+            const int base = ((j / Ns) * Ns * 2) + k;
+            b[base] = v[0];
+            b[base + Ns] = v[1];
+        }
+        __syncwarp();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// true when warp_fft_pow2<N> leaves its result in the second buffer
+template <int N>
+__host__ __device__ constexpr bool fft_pow2_result_in_b() {
+    return (((N == 64) ? 3 : (N == 128) ? 4 : (N == 256) ? 4 : (N == 512) ? 5 : 5) & 1) != 0;
+}
+
+template <int N, int W>
+__global__ void __launch_bounds__(FUS_NT, 1)
+k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
+                   const float2 *__restrict__ tw, float beta, const float2 *__restrict__ rad,
+                   const float4 *__restrict__ ang, int n_xi, int n_theta, int nq0, float2 *__restrict__ Fpol,
+                   int *status) {
+    constexpr int L = N / 2;
+    constexpr int H = (W + 1) / 2;
+    constexpr int MH = N / 2 + 1 + 2 * H;         // rows of S (m2 + h)
+    constexpr int SLD = (MH > L) ? MH : L;        // row length of S
+    extern __shared__ float2 smz[];
+    float2 *S = smz;                               // [MH][SLD]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *bufA = smz + MH * SLD + warp * 2 * N;
+    float2 *bufB = bufA + N;
+    const int half = blockIdx.x;
+    const int img = blockIdx.y;
+    const float *im = images + (size_t)img * L * L;
+
+    // ---- phase 1: row transforms (two pixel rows per complex FFT) --------
+    bool bad = false;
+    for (int rp = warp; rp < L / 2; rp += FUS_WARPS) {
+        const int a1 = 2 * rp;
+        float x[L / 32], y[L / 32];
+#pragma unroll
+        for (int q = 0; q < L / 32; ++q) {
+            x[q] = __ldg(&im[(size_t)a1 * L + lane + 32 * q]);
+            y[q] = __ldg(&im[(size_t)(a1 + 1) * L + lane + 32 * q]);
+        }
+#pragma unroll
+        for (int q = 0; q < N / 32; ++q) bufA[lane + 32 * q] = make_float2(0.f, 0.f);
+        __syncwarp();
+        const float c1 = corr[a1], c2 = corr[a1 + 1];
+#pragma unroll
+        for (int q = 0; q < L / 32; ++q) {
+            const int a2 = lane + 32 * q;
+            bad |= !(isfinite(x[q]) && isfinite(y[q]));
+            const float ca = corr[a2];
+            bufA[(a2 - off) & (N - 1)] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
+        }
+        __syncwarp();
+        const float2 *X = warp_fft_pow2<N, false>(bufA, bufB, tw, lane);
+        for (int e = lane; e < MH; e += 32) {
+            const int m = (e - H) & (N - 1);
+            const float2 Z = X[m];
+            const float2 Zc = cconj(X[(N - m) & (N - 1)]);
+            const float2 D = csub(Z, Zc);
+            S[e * SLD + a1] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+            S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
+        }
+        __syncwarp();
+    }
+    if (bad) ffb_flag(status, FFB_ERR_NONFINITE);
+    __syncthreads();
+
+    // ---- phase 2: column transforms, in place per row of S ---------------
+    const int m1lo = (half == 0) ? -H : -(N / 2) - H;
+    for (int e = warp; e < MH; e += FUS_WARPS) {
+        float2 *row = S + e * SLD;
+#pragma unroll
+        for (int q = 0; q < N / 32; ++q) bufA[lane + 32 * q] = make_float2(0.f, 0.f);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < L / 32; ++q) {
+            const int a1 = lane + 32 * q;
+            bufA[(a1 - off) & (N - 1)] = row[a1];
+        }
+        __syncwarp();
+        const float2 *X = warp_fft_pow2<N, false>(bufA, bufB, tw, lane);
+        for (int c = lane; c < MH; c += 32) row[c] = X[(c + m1lo) & (N - 1)];
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- phase 3: interpolation of this half's nodes -----------------------
+    const int nh = n_theta / 2;
+    const int lbeg = (half == 0) ? 0 : nq0;
+    const int nl = (half == 0) ? nq0 : nh - nq0;
+    const int npts = n_xi * nl;
+    constexpr float halfw = 0.5f * W;
+    constexpr float two_over_w = 2.0f / W;
+    float2 *Fout = Fpol + (size_t)img * n_xi * nh;
+    for (int t = threadIdx.x; t < npts; t += FUS_NT) {
+        const int j = t / nl;
+        const int l = lbeg + (t - j * nl);
+        const float2 r = __ldg(&rad[j]);
+        const float4 a = __ldg(&ang[l]);
+        const float p1 = r.x * a.x;
+        const float e1 = fmaf(r.x, a.x, -p1) + fmaf(r.x, a.y, r.y * a.x);
+        const float p2 = r.x * a.z;
+        const float e2 = fmaf(r.x, a.z, -p2) + fmaf(r.x, a.w, r.y * a.z);
+        const float m1f = ceilf(p1 - halfw), m2f = ceilf(p2 - halfw);
+        const float f1 = (p1 - m1f) + e1, f2 = (p2 - m2f) + e2;
+        const int c0 = (int)m1f - m1lo;     // column of the first tap in S
+        const int r0 = (int)m2f + H;        // row of the first tap in S
+        float2 acc = make_float2(0.f, 0.f);
+        if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) {
+            ffb_flag(status, FFB_ERR_ARG);
+        } else {
+            float wx[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) wx[q] = es_kernel(f1 - (float)q, two_over_w, beta);
+            const float2 *base = S + r0 * SLD + c0;
+#pragma unroll
+            for (int bq = 0; bq < W; ++bq) {
+                const float wy = es_kernel(f2 - (float)bq, two_over_w, beta);
+                const float2 *row = base + bq * SLD;
+                float sx = 0.f, sy = 0.f;
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    const float2 g = row[q];
+                    sx = fmaf(wx[q], g.x, sx);
+                    sy = fmaf(wx[q], g.y, sy);
+                }
+                acc.x = fmaf(wy, sx, acc.x);
+                acc.y = fmaf(wy, sy, acc.y);
+            }
+        }
+        Fout[(size_t)j * nh + l] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ring FFT: F[img][j][l] (l < n_theta/2) -> Fhat[k][img][c][j], k <= k_max,
+// with the conjugate completion of the ring and the 2 pi / n_theta weight.
+// grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads (one warp per ring)
+// ---------------------------------------------------------------------------
+template <int NTH>
+__global__ void __launch_bounds__(32 * RFFT_RB)
+k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
+           float *__restrict__ Fhat) {
+    constexpr int NH = NTH / 2;
+    extern __shared__ float2 smr[];
+    float2 *ringA = smr;                    // [RFFT_RB][NTH]
+    float2 *ringB = smr + RFFT_RB * NTH;    // [RFFT_RB][NTH]
+    const int img = blockIdx.y;
+    const int j0 = blockIdx.x * RFFT_RB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float2 *src = Fpol + ((size_t)img * n_xi + j0) * NH;
+    const int nrings = min(RFFT_RB, n_xi - j0);
+    for (int t = threadIdx.x; t < nrings * NH; t += 32 * RFFT_RB) {
+        const int jj = t / NH, l = t - jj * NH;
+        const float2 v = src[(size_t)jj * NH + l];
+        ringA[jj * NTH + l] = v;
+        ringA[jj * NTH + l + NH] = cconj(v);
+    }
+    __syncthreads();
+    if (warp < nrings) warp_fft_pow2<NTH, false>(ringA + warp * NTH, ringB + warp * NTH, twT, lane);
+    __syncthreads();
+    const float2 *res = fft_pow2_result_in_b<NTH>() ? ringB : ringA;
+    const float scale = 6.283185307179586f / (float)NTH;
+    for (int t = threadIdx.x; t < (kmax + 1) * 2 * RFFT_RB; t += 32 * RFFT_RB) {
+        const int jj = t % RFFT_RB, cc = (t / RFFT_RB) & 1, k = t / (2 * RFFT_RB);
+        if (jj < nrings) {
+            const float2 v = res[jj * NTH + k];
+            Fhat[(((size_t)k * chunk + img) * 2 + cc) * n_xi + j0 + jj] = scale * (cc ? v.y : v.x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+template <int N, int W>
+static size_t fused_smem() {
+    constexpr int L = N / 2, H = (W + 1) / 2, MH = N / 2 + 1 + 2 * H, SLD = (MH > L) ? MH : L;
+    return sizeof(float2) * ((size_t)MH * SLD + (size_t)FUS_WARPS * 2 * N);
+}
+
+template <int N, int W>
+static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {
+    static int attr = 0;
+    const size_t smem = fused_smem<N, W>();
+    if (attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_grid_interp_half<N, W>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    dim3 g(2, m);
+    ProfScope ps(p, FFB_KC_GRID_INTERP, s);
+    k_grid_interp_half<N, W><<<g, FUS_NT, smem, s>>>(d_images + (size_t)i0 * p->L * p->L, p->off, p->d_corr,
+                                                     p->d_twN, (float)p->beta, p->d_rad, p->d_ang, p->n_xi,
+                                                     p->n_theta, p->nq0, Fpol, p->d_status);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+bool ffb_fused_supported(ffb_plan_t p) {
+    if (p->L * 2 != p->N || p->w != 8) return false;
+    if (!(p->N == 128 || p->N == 256)) return false;
+    if (!(p->n_theta == 128 || p->n_theta == 256 || p->n_theta == 512 || p->n_theta == 1024)) return false;
+    if (p->L % 32) return false;
+    const size_t smem = (p->N == 256) ? fused_smem<256, 8>() : fused_smem<128, 8>();
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return smem <= (size_t)optin;
+}
+
+int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {
+    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s);
+    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s);
+    return FFB_ERR_UNSUPPORTED;
+}
+
+template <int NTH>
+static int launch_ring(ffb_plan_t p, int m, const float2 *Fpol, cudaStream_t s) {
+    static int attr = 0;
+    const size_t smem = sizeof(float2) * 2 * RFFT_RB * (size_t)NTH;
+    if (smem > 48 * 1024 && attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_fft<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
+    ProfScope ps(p, FFB_KC_RING_FFT, s);
+    k_ring_fft<NTH><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, p->chunk, p->d_twT, p->d_Fhat);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, cudaStream_t s) {
+    switch (p->n_theta) {
+        case 128: return launch_ring<128>(p, m, Fpol, s);
+        case 256: return launch_ring<256>(p, m, Fpol, s);
+        case 512: return launch_ring<512>(p, m, Fpol, s);
+        case 1024: return launch_ring<1024>(p, m, Fpol, s);
+        default: return FFB_ERR_UNSUPPORTED;
+    }
+}

@@ -273,8 +273,9 @@ k_filter(const float2 *__restrict__ cin, float2 *__restrict__ cout, int64_t n, i
     const int pk = pk_[k], o = off_[k];
     const int64_t i0 = (int64_t)blockIdx.x * FIL_IMG;
     const bool affine = !(flags & 1) && k == 0;
-    float *Ms = smf;                          // [pk][pk]
-    float2 *X = (float2 *)(smf + pk * pk);    // [FIL_IMG][pk]
+    // float2 tile first: it needs 8-byte alignment (pk * pk floats may be odd)
+    float2 *X = (float2 *)smf;                    // [FIL_IMG][pk]
+    float *Ms = smf + 2 * FIL_IMG * pk;           // [pk][pk]
     for (int e = threadIdx.x; e < pk * pk; e += blockDim.x) Ms[e] = M[cov_off[k] + e];
     for (int t = threadIdx.x; t < FIL_IMG * pk; t += blockDim.x) {
         const int ii = t / pk, q = t - ii * pk;

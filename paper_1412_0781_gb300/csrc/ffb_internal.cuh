@@ -23,7 +23,7 @@ struct FftPlanDev {
 enum { FFB_KC_ROWS = 0, FFB_KC_COLS = 1, FFB_KC_INTERP = 2, FFB_KC_BESSEL = 3, FFB_KC_COV = 4,
        FFB_KC_COVAUX = 5, FFB_KC_EIG = 6, FFB_KC_ADJ_BESSEL = 7, FFB_KC_ADJ_RING = 8,
        FFB_KC_ADJ_COLS = 9, FFB_KC_ADJ_ROWS = 10, FFB_KC_FILTER = 11, FFB_KC_SETUP = 12,
-       FFB_NKC = 16 };
+       FFB_KC_GRID_INTERP = 13, FFB_KC_RING_FFT = 14, FFB_NKC = 16 };
 
 struct ProfEv {
     cudaEvent_t a, b;
@@ -45,6 +45,8 @@ struct ffb_plan_s {
     double beta;         // ES kernel shape
     FftPlanDev fftN, fftT;
     int chunk;           // images per internal chunk
+    int nq0;             // half-ring angles with cos(theta) >= 0 (fused path split)
+    int fused;           // 1: grid held in shared memory (ffb_fused.cu)
     // device tables (float64 setup results)
     double *d_zeros = nullptr;   // [P]
     double *d_xi = nullptr;      // [n_xi]
@@ -66,6 +68,7 @@ struct ffb_plan_s {
     float2 *d_H = nullptr;       // [chunk][N/2+1][L]
     float2 *d_G = nullptr;       // [chunk][Mh][N]
     float *d_Fhat = nullptr;     // [k_max+1][chunk][2][n_xi]
+    float2 *d_Fpol = nullptr;    // [chunk][n_xi][n_theta/2] (fused path)
     // covariance state
     double *d_acc = nullptr;     // [cov_total] sum Re(a a^*), k = 0 shifted
     double *d_sum0 = nullptr;    // [p0] sum (a0 - shift)
@@ -77,6 +80,7 @@ struct ffb_plan_s {
     double *d_mean = nullptr;    // [p0]
     double *d_evals = nullptr;   // [P]
     double *d_evecs = nullptr;   // [cov_total]
+    double *d_eig_work = nullptr;  // Jacobi eigenvector workspace for large blocks
     // denoising
     float2 *d_coef_den = nullptr;  // [den_cap][P]
     int64_t den_cap = 0;
@@ -246,6 +250,11 @@ __device__ __forceinline__ float es_kernel(float x, float two_over_w, float beta
 // Host helpers (implemented in ffb_plan.cu).
 int ffb_check_cuda(cudaError_t e);
 int ffb_ensure_scratch(ffb_plan_t plan);
+int ffb_ensure_scratch_grid(ffb_plan_t plan);
+bool ffb_fused_supported(ffb_plan_t plan);
+int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
+                           cudaStream_t s);
+int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, cudaStream_t s);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);

@@ -275,3 +275,4 @@ int ffb_launch_interp_ring(ffb_plan_t p, int nimg, cudaStream_t s) {
 int ffb_launch_polar(ffb_plan_t p, int nimg, float *d_F, cudaStream_t s) {
     return launch_interp<true>(p, nimg, (float2 *)d_F, s);
 }
+

@@ -211,7 +211,7 @@ static void free_plan(ffb_plan_t p) {
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
                     p->d_cov_work, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
-                    p->d_coef_den, p->d_gain, p->d_M};
+                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (ProfEv &e : p->prof) {
@@ -387,12 +387,22 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     return hstatus;
 }
 
-int ffb_ensure_scratch(ffb_plan_t p) {
+// row spectra and half grid of a chunk (separate-kernel NUFFT and adjoint)
+int ffb_ensure_scratch_grid(ffb_plan_t p) {
     if (p->d_H) return FFB_OK;
     CK(dalloc(&p->d_H, (size_t)p->chunk * (p->N / 2 + 1) * p->L));
     CK(dalloc(&p->d_G, (size_t)p->chunk * p->Mh * p->N));
-    CK(dalloc(&p->d_Fhat, (size_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi));
     return FFB_OK;
+}
+
+// ring spectra of a chunk, plus the polar samples (fused path) or the grid
+int ffb_ensure_scratch(ffb_plan_t p) {
+    if (!p->d_Fhat) CK(dalloc(&p->d_Fhat, (size_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi));
+    if (p->fused) {
+        if (!p->d_Fpol) CK(dalloc(&p->d_Fpol, (size_t)p->chunk * p->n_xi * (p->n_theta / 2)));
+        return FFB_OK;
+    }
+    return ffb_ensure_scratch_grid(p);
 }
 
 extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, int precision,
@@ -421,6 +431,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     p->h = (p->w + 1) / 2;
     p->Mh = p->N / 2 + 1 + 2 * p->h;
     p->chunk = 256;
+    p->nq0 = p->n_theta / 4 + 1;   // l <= n_theta/4  <=>  cos(theta_l) >= 0
     if (!factor_235(p->N, &p->fftN) || !factor_235(p->n_theta, &p->fftT) || p->n_xi < 2) {
         delete p;
         return FFB_ERR_UNSUPPORTED;
@@ -429,6 +440,10 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     int st = ffb_check_cuda(cudaMalloc(&p->d_status, sizeof(int)));
     if (st == FFB_OK) st = ffb_check_cuda(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     if (st == FFB_OK) st = build_plan(p, s);
+    if (st == FFB_OK && false && ffb_fused_supported(p)) {
+        p->fused = 1;
+        p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
+    }
     if (st != FFB_OK) {
         cudaStreamSynchronize(s);
         free_plan(p);

@@ -48,7 +48,11 @@ def pixel_index(L, device="cpu", dtype=torch.float64):
 
 
 def blob_stack(spec, n=None, device="cpu", chunk=2048):
-    """Return (images float32 (n, L, L), clean float32 (n, L, L), sigma2 float)."""
+    """Return (images float32 (n, L, L), clean float32 (n, L, L), sigma2 float).
+
+    ``chunk`` fixes how the noise is drawn (part of the seeded recipe); the
+    blob rendering is split independently so that its float64 temporaries
+    stay near 256 MB."""
     n = spec.n if n is None else n
     L, R = spec.L, float(spec.R)
     g = torch.Generator(device=device)
@@ -70,8 +74,9 @@ def blob_stack(spec, n=None, device="cpu", chunk=2048):
     inside = (X1 * X1 + X2 * X2) < R * R
     clean = torch.empty((n, L, L), device=device, dtype=torch.float32)
     power = torch.zeros((), device=device, dtype=f64)
-    for s0 in range(0, n, chunk):
-        s1 = min(n, s0 + chunk)
+    rchunk = max(1, (1 << 25) // (spec.n_blobs * L * L))
+    for s0 in range(0, n, rchunk):
+        s1 = min(n, s0 + rchunk)
         dx = X1[None, None] - x0[s0:s1, :, None, None]
         dy = X2[None, None] - y0[s0:s1, :, None, None]
         ss = s[s0:s1, :, None, None]

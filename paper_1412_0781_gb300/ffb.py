@@ -151,7 +151,8 @@ class Plan:
         self.precision = prec
 
     KERNEL_CLASSES = ["rows_fft", "cols_fft", "interp_ring", "bessel", "covariance", "cov_aux", "jacobi",
-                      "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup"]
+                      "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup",
+                      "grid_interp", "ring_fft"]
 
     def profile(self, enable=True):
         _check(load().ffb_profile(self._h, int(bool(enable))), "ffb_profile")
