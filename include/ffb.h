@@ -110,6 +110,21 @@ int ffb_set_precision(ffb_plan_t plan, int precision);
 int ffb_polar(ffb_plan_t plan, const float *d_images, int64_t n, float *d_F,
               void *stream);
 
+/* ffb_polar_noalloc -- the same polar samples as ffb_polar, computed without
+ * allocating device memory.  The paper has no counterpart: this entry point
+ * exists for callers that must not call cudaMalloc on the calling path
+ * (code running during CUDA stream capture, latency-bound serving loops,
+ * host frameworks that own all device memory).  Scratch comes from a 16 MiB
+ * array that the library reserves statically on every device where it is
+ * loaded, until the process exits.  The first call on each device resolves
+ * that array's address (cudaGetSymbolAddress) and must precede any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * A plan whose single image needs more than 16 MiB of scratch is rejected
+ * with FFB_ERR_UNSUPPORTED (not reached for L <= 512).  Arguments as
+ * ffb_polar; the plan must already exist. */
+int ffb_polar_noalloc(ffb_plan_t plan, const float *d_images, int64_t n, float *d_F,
+                      void *stream);
+
 /* ffb_expand -- Alg. 1 steps 3-4: a = T* I for n images.
  * d_images [n][L][L] float32 -> d_coef [n][P][2] float32 (layout above).
  * Eq. nufft by NUFFT, Eq. 1DFFT by FFT on each ring, Eq. a as a grouped

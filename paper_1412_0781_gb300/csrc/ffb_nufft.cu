@@ -276,3 +276,94 @@ int ffb_launch_polar(ffb_plan_t p, int nimg, float *d_F, cudaStream_t s) {
     return launch_interp<true>(p, nimg, (float2 *)d_F, s);
 }
 
+// ---------------------------------------------------------------------------
+// ffb_polar_noalloc: the polar transform of ffb_polar without any device
+// allocation, for callers that must not call cudaMalloc on the calling path:
+// code running while a CUDA stream is being captured into a graph (where
+// cudaMalloc is not allowed), real-time or serving loops whose latency budget
+// cannot absorb an allocation, and host frameworks that own all device
+// memory through their own pool and forbid third-party allocations.
+//
+// The scratch (row spectra and half grid of a group of images) lives in the
+// file-scope array below, FFB_NOALLOC_SCRATCH_BYTES (16 MiB) per device,
+// reserved for as long as the library stays loaded.  Host code cannot use the
+// array's name as a device address; the first call on each device looks the
+// address up with cudaGetSymbolAddress (with that device current) and caches
+// it, so that first call must come before any stream capture.  Every call
+// shares the one array: calls that overlap on the GPU (different streams or
+// host threads without ordering) race on it.  Each call writes every element
+// it reads before reading it, so nothing has to start at zero.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define FFB_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define FFB_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FFB_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_addr[FFB_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+static int noalloc_scratch_address(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FFB_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= FFB_NOALLOC_MAX_DEVICES) return FFB_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+        if (e != cudaSuccess || !addr) {
+            cudaGetLastError();
+            return FFB_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = addr;
+    }
+    *out = g_noalloc_addr[dev];
+    return FFB_OK;
+}
+
+static int noalloc_smem(const void *fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return FFB_OK;
+    return ffb_check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+extern "C" int ffb_polar_noalloc(ffb_plan_t p, const float *d_images, int64_t n, float *d_F, void *stream) {
+    if (!p || n < 0 || (n > 0 && (!d_images || !d_F))) return FFB_ERR_ARG;
+    const int N = p->N, L = p->L, Nh = N / 2 + 1;
+    const size_t h_bytes = (sizeof(float2) * (size_t)Nh * L + 255) / 256 * 256;
+    const size_t g_bytes = (sizeof(float2) * (size_t)p->Mh * N + 255) / 256 * 256;
+    const size_t per_image = h_bytes + g_bytes;
+    if (per_image > FFB_NOALLOC_SCRATCH_BYTES) return FFB_ERR_UNSUPPORTED;  // one image does not fit
+    if (n == 0) return FFB_OK;
+    void *base = nullptr;
+    int e = noalloc_scratch_address(&base);
+    if (e) return e;
+    const int group = (int)(FFB_NOALLOC_SCRATCH_BYTES / per_image);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sm_rows = sizeof(float2) * ((size_t)ROW_WARPS * 2 * N + (size_t)Nh * 2 * ROW_WARPS);
+    const size_t sm_cols = sizeof(float2) * (size_t)COL_WARPS * 2 * N;
+    if ((e = noalloc_smem((const void *)k_rows, sm_rows))) return e;
+    if ((e = noalloc_smem((const void *)k_cols, sm_cols))) return e;
+    const size_t per_out = (size_t)p->n_xi * (p->n_theta / 2) * 2;  // floats per image
+    for (int64_t i0 = 0; i0 < n; i0 += group) {
+        const int m = (int)((n - i0) < group ? (n - i0) : group);
+        float2 *H = (float2 *)base;
+        float2 *G = (float2 *)((unsigned char *)base + h_bytes * (size_t)m);
+        dim3 g1((L + 2 * ROW_WARPS - 1) / (2 * ROW_WARPS), m);
+        k_rows<<<g1, 32 * ROW_WARPS, sm_rows, s>>>(d_images + (size_t)i0 * L * L, L, p->off, N, p->d_corr,
+                                                    p->d_twN, p->fftN, H, p->d_status);
+        dim3 g2((Nh + COL_WARPS - 1) / COL_WARPS, m);
+        k_cols<<<g2, 32 * COL_WARPS, sm_cols, s>>>(H, L, p->off, N, p->h, p->Mh, p->d_twN, p->fftN, G);
+        dim3 g3((p->n_xi + RING_RB - 1) / RING_RB, m);
+        k_interp_ring<true><<<g3, RING_NT, 0, s>>>(G, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad, p->d_ang,
+                                                   p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max, m,
+                                                   nullptr, (float2 *)(d_F + (size_t)i0 * per_out),
+                                                   p->d_status);
+        p->launches += 3;
+        e = ffb_check_cuda(cudaGetLastError());
+        if (e) return e;
+    }
+    return FFB_OK;
+}

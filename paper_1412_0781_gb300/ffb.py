@@ -32,6 +32,7 @@ SIGNATURES = {
     "ffb_plan_tables": (_i, [_vp, _pd, _pd, _pd, _pd]),
     "ffb_set_precision": (_i, [_vp, _i]),
     "ffb_polar": (_i, [_vp, _vp, _i64, _vp, _vp]),
+    "ffb_polar_noalloc": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_expand": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_expand_adjoint": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_covariance": (_i, [_vp, _vp, _i64, _i, _vp]),
