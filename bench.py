@@ -100,14 +100,22 @@ class ClockSampler:
 # algorithmic work per image (flops) of each kernel class, and its roofline
 # ---------------------------------------------------------------------------
 def algorithmic_flops(plan):
+    """Algorithmic flops per image of each kernel class (5 n log2 n per
+    complex FFT of length n; 2 flop per real multiply-add)."""
     n_xi, nth, w, N, L = plan.n_xi, plan.n_theta, plan.w, plan.N, plan.L
     pts = n_xi * (nth // 2)
+    fftN = 5 * N * math.log2(N)
+    ring = n_xi * 5 * nth * math.log2(nth)
+    interp = pts * w * w * 4
+    rows = (L / 2) * fftN
+    cols = (N / 2 + 1) * fftN
     sum_p2_sym = sum(pk * (pk + 1) // 2 for pk in plan.p)
     return {
-        "rows_fft": (L / 2) * 5 * N * math.log2(N),
-        "cols_fft": (N / 2 + 1) * 5 * N * math.log2(N),
-        # w^2 taps x (2 FMA = 4 flop) per node + ring FFT of length n_theta per ring
-        "interp_ring": pts * w * w * 4 + n_xi * 5 * nth * math.log2(nth),
+        "rows_fft": rows,
+        "cols_fft": cols,
+        "interp_ring": interp + ring,          # separate-kernel path
+        "grid_interp": rows + cols + interp,   # shared-memory grid path
+        "ring_fft": ring,
         "bessel": 4.0 * plan.P * n_xi,
         "covariance": 4.0 * sum_p2_sym,
     }

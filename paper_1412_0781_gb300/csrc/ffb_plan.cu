@@ -207,6 +207,7 @@ static cudaError_t dalloc(T **p, size_t count) {
 }
 
 static void free_plan(ffb_plan_t p) {
+    ffb_tc_release(p);
     void *ptrs[] = {p->d_zeros, p->d_xi, p->d_wq, p->d_B64, p->d_Bf, p->d_p, p->d_off,
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
                     p->d_cov_work, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
@@ -440,7 +441,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     int st = ffb_check_cuda(cudaMalloc(&p->d_status, sizeof(int)));
     if (st == FFB_OK) st = ffb_check_cuda(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     if (st == FFB_OK) st = build_plan(p, s);
-    if (st == FFB_OK && false && ffb_fused_supported(p)) {
+    if (st == FFB_OK && ffb_fused_supported(p)) {
         p->fused = 1;
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
     }
