@@ -84,7 +84,7 @@ int ffb_launch_bessel_fp32(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStre
 }
 
 int ffb_launch_bessel(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    // tensor-core variants are dispatched here once available for the precision
+    if (p->precision != FFB_FP32 && ffb_tc_supported(p)) return ffb_launch_bessel_tc(p, nimg, d_coef_chunk, s);
     return ffb_launch_bessel_fp32(p, nimg, d_coef_chunk, s);
 }
 

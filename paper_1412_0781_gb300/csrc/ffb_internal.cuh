@@ -90,6 +90,8 @@ struct ffb_plan_s {
     // status word written by kernels (first nonzero error wins)
     int *d_status = nullptr;
     int64_t launches = 0;
+    // tensor-core operand tables and TMA descriptors (ffb_tc.cu)
+    void *tc = nullptr;
     // optional per-launch timing
     int prof_on = 0;
     size_t prof_used = 0;
@@ -261,6 +263,9 @@ int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg
 int ffb_launch_polar(ffb_plan_t plan, int nimg, float *d_F, cudaStream_t s);
 int ffb_launch_interp_ring(ffb_plan_t plan, int nimg, cudaStream_t s);
 int ffb_launch_bessel(ffb_plan_t plan, int nimg, float *d_coef_chunk, cudaStream_t s);
+int ffb_launch_bessel_tc(ffb_plan_t plan, int nimg, float *d_coef_chunk, cudaStream_t s);
+bool ffb_tc_supported(ffb_plan_t plan);
+void ffb_tc_release(ffb_plan_t plan);
 int ffb_launch_cov(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
 int ffb_launch_cov_shift(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
 int ffb_launch_cov_final(ffb_plan_t plan, cudaStream_t s);
