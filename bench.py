@@ -299,10 +299,21 @@ def run_ours(args):
         out_mean = torch.empty(plan.p[0], dtype=torch.float64, pin_memory=True)
         out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
 
+        copy_stream = torch.cuda.Stream(device=dev)
+        nparts = 8
+        bounds = [(n * c // nparts, n * (c + 1) // nparts) for c in range(nparts)]
+        events = [torch.cuda.Event() for _ in range(nparts)]
+
         def e2e_step():
-            dbuf.copy_(hbuf, non_blocking=True)
-            plan.expand(dbuf, out=r["coef"])
-            plan.covariance(r["coef"], reset=True)
+            # host->device copy of part c+1 overlaps the expansion of part c
+            with torch.cuda.stream(copy_stream):
+                for c, (a, b) in enumerate(bounds):
+                    dbuf[a:b].copy_(hbuf[a:b], non_blocking=True)
+                    events[c].record(copy_stream)
+            for c, (a, b) in enumerate(bounds):
+                torch.cuda.current_stream().wait_event(events[c])
+                plan.expand(dbuf[a:b], out=r["coef"][a:b])
+                plan.covariance(r["coef"][a:b], reset=(c == 0))
             m, C = plan.cov_get()
             out_mean.copy_(m)
             out_C.copy_(C)

@@ -155,6 +155,20 @@ int ffb_covariance(ffb_plan_t plan, const float *d_coef, int64_t n, int reset,
  * device errors. */
 int ffb_cov_get(ffb_plan_t plan, double *d_mean0, double *d_C, void *stream);
 
+/* Covariance statistics of disjoint image sets (e.g. one per GPU; Sec. IV
+ * splits the images over workers).  A state is the float64 host vector
+ * [n, mean0 (p_0 values), C^(0..k_max) packed as in ffb_cov_get]
+ * (length 1 + p_0 + sum p_k^2).
+ * ffb_cov_export: finalises the plan's accumulator into h_state (synchronises).
+ * ffb_cov_merge:  host-only; pools nstates consecutive states of the plan
+ *   sizes (k_max, h_p[k_max+1]) into h_out: n = sum n_r, m = sum n_r m_r / n,
+ *   C^(0) = sum n_r (C0_r + (m_r - m)(m_r - m)^T)/n, C^(k) = sum n_r C^(k)_r/n.
+ * ffb_cov_import: replaces the plan's accumulator by a (pooled) state, so that
+ *   ffb_cov_get / ffb_eig return the pooled covariance (synchronises). */
+int ffb_cov_export(ffb_plan_t plan, double *h_state, void *stream);
+int ffb_cov_merge(int k_max, const int *h_p, int nstates, const double *h_states, double *h_out);
+int ffb_cov_import(ffb_plan_t plan, const double *h_state, void *stream);
+
 /* ffb_eig -- Alg. 2 step 4: eigenpairs of every block C^(k) by a batched
  * float64 cyclic Jacobi solver on the GPU (one CTA per block).
  * d_evals[P]: per block descending; d_evecs packed p_k x p_k row-major,

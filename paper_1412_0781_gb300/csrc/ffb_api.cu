@@ -74,16 +74,18 @@ extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float 
     if (n == 0) return FFB_OK;
     cudaStream_t s = (cudaStream_t)stream;
     CK(ffb_ensure_scratch(p));
+    RingOut ring{FFB_FMT_F32, p->d_Fhat, nullptr, p->n_xi};
+    if (p->precision != FFB_FP32) CK(ffb_tc_prepare(p, s, &ring));
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, n - i0);
         if (p->fused) {
             CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s));
-            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, s));
+            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, ring, s));
         } else {
             CK(ffb_launch_grid(p, d_images, i0, m, s));
             CK(ffb_launch_interp_ring(p, m, s));
         }
-        CK(ffb_launch_bessel(p, m, d_coef + (size_t)i0 * p->P * 2, s));
+        CK(ffb_launch_bessel(p, m, d_coef + (size_t)i0 * p->P * 2, p->fused != 0, s));
     }
     return FFB_OK;
 }
@@ -241,4 +243,91 @@ extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int m
     CK(ffb_launch_filter(p, coef, n, coef, FFB_FILTER_WEIGHT, s));
     CK(ffb_launch_adjoint(p, coef, n, d_out, s));
     return read_status(p, s);
+}
+
+// ---------------------------------------------------------------------------
+// Covariance statistics across processes (images split over GPUs, Sec. IV):
+// state = [n, mean0 (p_0), C^(0..k_max) packed], float64, host memory.
+// ---------------------------------------------------------------------------
+static int64_t state_len(const std::vector<int> &p) {
+    int64_t len = 1 + p[0];
+    for (int v : p) len += (int64_t)v * v;
+    return len;
+}
+
+extern "C" int ffb_cov_export(ffb_plan_t p, double *h_state, void *stream) {
+    if (!p || !h_state) return FFB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->n_acc <= 0) return FFB_ERR_STATE;
+    CK(ffb_launch_cov_final(p, s));
+    h_state[0] = (double)p->n_acc;
+    CK(ffb_check_cuda(cudaMemcpyAsync(h_state + 1, p->d_mean, sizeof(double) * p->p[0], cudaMemcpyDeviceToHost, s)));
+    CK(ffb_check_cuda(cudaMemcpyAsync(h_state + 1 + p->p[0], p->d_Cfin, sizeof(double) * p->cov_total,
+                                      cudaMemcpyDeviceToHost, s)));
+    return read_status(p, s);
+}
+
+// Pooled statistics of nstates disjoint image sets (Chan et al.'s pairwise
+// update generalised): n = sum n_r, m = sum n_r m_r / n,
+// C^(0) = sum n_r (C0_r + (m_r - m)(m_r - m)^T) / n, C^(k>0) = sum n_r C^(k)_r / n.
+extern "C" int ffb_cov_merge(int k_max, const int *h_p, int nstates, const double *h_states, double *h_out) {
+    if (k_max < 0 || !h_p || nstates < 1 || !h_states || !h_out) return FFB_ERR_ARG;
+    std::vector<int> p(h_p, h_p + k_max + 1);
+    for (int v : p)
+        if (v <= 0) return FFB_ERR_ARG;
+    const int64_t len = state_len(p);
+    const int p0 = p[0];
+    double n = 0.0;
+    for (int r = 0; r < nstates; ++r) {
+        const double nr = h_states[(size_t)r * len];
+        if (!(nr > 0.0)) return FFB_ERR_ARG;
+        n += nr;
+    }
+    std::vector<double> out((size_t)len, 0.0);
+    out[0] = n;
+    for (int r = 0; r < nstates; ++r) {
+        const double *st = h_states + (size_t)r * len;
+        for (int q = 0; q < p0; ++q) out[1 + q] += st[0] * st[1 + q] / n;
+    }
+    for (int r = 0; r < nstates; ++r) {
+        const double *st = h_states + (size_t)r * len;
+        const double w = st[0] / n;
+        const double *mr = st + 1;
+        // k = 0 block with the between-set term
+        for (int a = 0; a < p0; ++a)
+            for (int b = 0; b < p0; ++b) {
+                const double da = mr[a] - out[1 + a], db = mr[b] - out[1 + b];
+                out[1 + p0 + (size_t)a * p0 + b] += w * (st[1 + p0 + (size_t)a * p0 + b] + da * db);
+            }
+        for (int64_t e = 1 + p0 + (int64_t)p0 * p0; e < len; ++e) out[(size_t)e] += w * st[e];
+    }
+    std::copy(out.begin(), out.end(), h_out);
+    return FFB_OK;
+}
+
+// Loads pooled statistics into the plan's accumulator (shift = rounded mean),
+// after which ffb_cov_get / ffb_eig see the pooled covariance.
+extern "C" int ffb_cov_import(ffb_plan_t p, const double *h_state, void *stream) {
+    if (!p || !h_state || !(h_state[0] >= 1.0)) return FFB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int p0 = p->p[0];
+    const double n = h_state[0];
+    std::vector<float> shift(p0);
+    std::vector<double> sum0(p0), acc(p->cov_total);
+    for (int q = 0; q < p0; ++q) {
+        shift[q] = (float)h_state[1 + q];
+        sum0[q] = n * (h_state[1 + q] - (double)shift[q]);
+    }
+    const double *C = h_state + 1 + p0;
+    for (int a = 0; a < p0; ++a)
+        for (int b = 0; b < p0; ++b)
+            acc[(size_t)a * p0 + b] = n * (C[(size_t)a * p0 + b] + (sum0[a] / n) * (sum0[b] / n));
+    for (int e = p0 * p0; e < p->cov_total; ++e) acc[e] = n * C[e];
+    CK(ffb_check_cuda(cudaMemcpyAsync(p->d_shift, shift.data(), sizeof(float) * p0, cudaMemcpyHostToDevice, s)));
+    CK(ffb_check_cuda(cudaMemcpyAsync(p->d_sum0, sum0.data(), sizeof(double) * p0, cudaMemcpyHostToDevice, s)));
+    CK(ffb_check_cuda(cudaMemcpyAsync(p->d_acc, acc.data(), sizeof(double) * p->cov_total, cudaMemcpyHostToDevice, s)));
+    CK(ffb_check_cuda(cudaStreamSynchronize(s)));
+    p->n_acc = (int64_t)(n + 0.5);
+    p->shift_set = 1;
+    return FFB_OK;
 }

@@ -83,8 +83,8 @@ int ffb_launch_bessel_fp32(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStre
     return ffb_check_cuda(cudaGetLastError());
 }
 
-int ffb_launch_bessel(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    if (p->precision != FFB_FP32 && ffb_tc_supported(p)) return ffb_launch_bessel_tc(p, nimg, d_coef_chunk, s);
+int ffb_launch_bessel(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s) {
+    if (p->precision != FFB_FP32) return ffb_launch_bessel_tc(p, nimg, d_coef_chunk, planes_ready, s);
     return ffb_launch_bessel_fp32(p, nimg, d_coef_chunk, s);
 }
 
@@ -205,7 +205,8 @@ __global__ void k_cov_final(const double *__restrict__ acc, const double *__rest
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= pk * pk) return;
     const int qa = e / pk, qb = e % pk;
-    double v = acc[cov_off[k] + e] / n;
+    // symmetric part: tensor-core partial sums of (a, b) and (b, a) round differently
+    double v = 0.5 * (acc[cov_off[k] + e] + acc[cov_off[k] + qb * pk + qa]) / n;
     if (k == 0) {
         double da = sum0[qa] / n, db = sum0[qb] / n;
         v -= da * db;
@@ -222,6 +223,7 @@ int ffb_launch_cov_shift(ffb_plan_t p, const float *d_coef, int64_t n, cudaStrea
 }
 
 int ffb_launch_cov(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
+    if (ffb_tc_cov_supported(p)) return ffb_launch_cov_tc(p, d_coef, n, s);
     const int64_t per = 2048;
     int64_t ns = (n + per - 1) / per;
     if (ns > 65535) return FFB_ERR_ARG;

@@ -241,6 +241,16 @@ struct WarpSync {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
 
+// float32 rounded to the nearest tf32 (10 explicit mantissa bits), ties away
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    return __uint_as_float(u);
+}
+
+// Operand formats the ring FFT can write for the radial quadrature.
+enum { FFB_FMT_F32 = 0, FFB_FMT_TF32 = 1, FFB_FMT_TF32X2 = 2, FFB_FMT_BF16 = 3, FFB_FMT_BF16X2 = 4 };
+
 // Exponential-of-semicircle kernel psi(x) = exp(beta (sqrt(1 - (2x/w)^2) - 1)),
 // |x| < w/2, in fine-grid units.
 __device__ __forceinline__ float es_kernel(float x, float two_over_w, float beta) {
@@ -256,15 +266,23 @@ int ffb_ensure_scratch_grid(ffb_plan_t plan);
 bool ffb_fused_supported(ffb_plan_t plan);
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
                            cudaStream_t s);
-int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, cudaStream_t s);
+struct RingOut {
+    int fmt;           // FFB_FMT_*
+    void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra)
+    int ld;            // row length of the planes (>= n_xi)
+};
+int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, const RingOut &out, cudaStream_t s);
+int ffb_tc_prepare(ffb_plan_t plan, cudaStream_t s, RingOut *out);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);
 int ffb_launch_polar(ffb_plan_t plan, int nimg, float *d_F, cudaStream_t s);
 int ffb_launch_interp_ring(ffb_plan_t plan, int nimg, cudaStream_t s);
-int ffb_launch_bessel(ffb_plan_t plan, int nimg, float *d_coef_chunk, cudaStream_t s);
-int ffb_launch_bessel_tc(ffb_plan_t plan, int nimg, float *d_coef_chunk, cudaStream_t s);
+int ffb_launch_bessel(ffb_plan_t plan, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s);
+int ffb_launch_bessel_tc(ffb_plan_t plan, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s);
 bool ffb_tc_supported(ffb_plan_t plan);
+bool ffb_tc_cov_supported(ffb_plan_t plan);
+int ffb_launch_cov_tc(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
 void ffb_tc_release(ffb_plan_t plan);
 int ffb_launch_cov(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
 int ffb_launch_cov_shift(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);

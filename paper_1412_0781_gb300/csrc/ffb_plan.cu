@@ -441,6 +441,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     int st = ffb_check_cuda(cudaMalloc(&p->d_status, sizeof(int)));
     if (st == FFB_OK) st = ffb_check_cuda(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     if (st == FFB_OK) st = build_plan(p, s);
+    if (st == FFB_OK && p->precision != FFB_FP32 && !ffb_tc_supported(p)) st = FFB_ERR_UNSUPPORTED;
     if (st == FFB_OK && ffb_fused_supported(p)) {
         p->fused = 1;
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
@@ -496,7 +497,12 @@ extern "C" int ffb_plan_tables(ffb_plan_t p, double *h_zeros, double *h_xi, doub
 
 extern "C" int ffb_set_precision(ffb_plan_t p, int precision) {
     if (!p || precision < FFB_FP32 || precision > FFB_TF32X3) return FFB_ERR_ARG;
+    const int old = p->precision;
     p->precision = precision;
+    if (precision != FFB_FP32 && !ffb_tc_supported(p)) {
+        p->precision = old;
+        return FFB_ERR_UNSUPPORTED;
+    }
     return FFB_OK;
 }
 

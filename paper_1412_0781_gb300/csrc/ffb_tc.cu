@@ -30,23 +30,18 @@
 // ---------------------------------------------------------------------------
 // operand preparation
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;  // nearest, ties away
-    return __uint_as_float(u);
-}
-
-// Bpad[plane][k][BN][n_xi]: rows q < p_k from B64, zero rows beyond.
+// Bpad[plane][k][BN][ld]: rows q < p_k, columns j < n_xi from B64, zero
+// elsewhere (ld = n_xi rounded up to whole 128-byte K chunks).
 template <bool BF16>
 __global__ void k_prep_bpad(const double *__restrict__ B64, const int *__restrict__ pk_, const int *__restrict__ off_,
-                            int kmax, int BN, int n_xi, void *hi, void *lo) {
+                            int kmax, int BN, int n_xi, int ld, void *hi, void *lo) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t tot = (int64_t)(kmax + 1) * BN * n_xi;
+    const int64_t tot = (int64_t)(kmax + 1) * BN * ld;
     if (t >= tot) return;
-    const int j = (int)(t % n_xi);
-    const int q = (int)((t / n_xi) % BN);
-    const int k = (int)(t / ((int64_t)n_xi * BN));
-    double v = (q < pk_[k]) ? B64[(size_t)(off_[k] + q) * n_xi + j] : 0.0;
+    const int j = (int)(t % ld);
+    const int q = (int)((t / ld) % BN);
+    const int k = (int)(t / ((int64_t)ld * BN));
+    double v = (q < pk_[k] && j < n_xi) ? B64[(size_t)(off_[k] + q) * n_xi + j] : 0.0;
     if (BF16) {
         __nv_bfloat16 h = __float2bfloat16_rn((float)v);
         __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
@@ -59,12 +54,14 @@ __global__ void k_prep_bpad(const double *__restrict__ B64, const int *__restric
     }
 }
 
-// ring spectra float32 -> operand planes (same [k][rows][n_xi] layout)
+// ring spectra float32 [k][rows][n_xi] -> operand planes [k][rows][ld]
+// (separate-kernel path; the fused path's ring FFT writes the planes itself)
 template <bool BF16, bool TWO>
-__global__ void k_split_planes(const float *__restrict__ src, int64_t total, void *hi, void *lo) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const float x = src[t];
+__global__ void k_split_planes(const float *__restrict__ src, int64_t total, int n_xi, int ld, void *hi, void *lo) {
+    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s0 >= total) return;
+    const float x = src[s0];
+    const int64_t t = (s0 / n_xi) * ld + (s0 % n_xi);
     if (BF16) {
         __nv_bfloat16 h = __float2bfloat16_rn(x);
         ((__nv_bfloat16 *)hi)[t] = h;
@@ -82,19 +79,21 @@ __global__ void k_split_planes(const float *__restrict__ src, int64_t total, voi
 template <int KIND, int NPA, int NPB, int NPROD>
 __global__ void __launch_bounds__(128, 1)
 k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-            const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int n_xi,
+            const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int ld,
             int nimg, const int *__restrict__ pk_, const int *__restrict__ off_, int P, float *__restrict__ coef,
             int BNmax, int tmem_cols, int *status) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per 128-byte row
-    const int NCH = n_xi / KCH;
+    const int NCH = ld / KCH;
     const uint32_t a_bytes = 128u * 128u;       // one plane, one K chunk, 128 rows
     const uint32_t b_bytes = (uint32_t)BNmax * 128u;
     uint8_t *As = sm;
     uint8_t *Bs = sm + (size_t)NPA * NCH * a_bytes;
-    uint64_t *bars = (uint64_t *)(Bs + (size_t)NPB * NCH * b_bytes);   // [0] loads, [1] mma done
+    const size_t tiles = (size_t)NPA * NCH * a_bytes + (size_t)NPB * NCH * b_bytes;
+    const size_t stage_bytes = (size_t)64 * (2 * BNmax + 2) * 4;      // epilogue reuse of the tiles
+    uint64_t *bars = (uint64_t *)(sm + (tiles > stage_bytes ? tiles : stage_bytes));  // [0] loads, [1] mma done
     uint32_t *slot = (uint32_t *)(bars + 2);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -163,19 +162,27 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     tc::fence_after_sync();
     __syncthreads();
     if (*okflag) {
+        // drain TMEM into a padded [64 images][BN q][re, im] stage (the operand
+        // tiles are no longer needed), then write each image's p_k complex
+        // coefficients as one contiguous run
+        float *stage = (float *)sm;
+        const int ldst = 2 * BN + 2;               // floats per image row, +2 breaks bank aliasing
         const int r = 32 * warp + lane;            // accumulator row = TMEM lane
-        const int R = 128 * m + r;
-        const int img = R >> 1, cc = R & 1;
         for (int c16 = 0; c16 < BN; c16 += 16) {
             float v[16];
             tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c16, v);
-            if (img < nimg) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int q = c16 + i;
-                    if (q < pk) coef[((size_t)img * P + o + q) * 2 + cc] = (k == 0 && cc == 1) ? 0.f : v[i];
-                }
-            }
+            for (int i = 0; i < 16; ++i) stage[(r >> 1) * ldst + 2 * (c16 + i) + (r & 1)] = v[i];
+        }
+        __syncthreads();
+        const int i0 = 64 * m;
+        const int nimg_t = min(64, nimg - i0);
+        float2 *out = (float2 *)coef;
+        for (int t = threadIdx.x; t < nimg_t * pk; t += 128) {
+            const int ii = t / pk, q = t - ii * pk;
+            float2 val = make_float2(stage[ii * ldst + 2 * q], stage[ii * ldst + 2 * q + 1]);
+            if (k == 0) val.y = 0.f;
+            out[(size_t)(i0 + ii) * P + o + q] = val;
         }
     }
     tc::fence_before_sync();
@@ -218,9 +225,9 @@ static int make_map(CUtensorMap *map, void *base, bool bf16, uint64_t d0, uint64
 
 struct TcState {
     int prepared = -1;       // precision the tables were built for
-    int BN = 0, tmem_cols = 0;
-    void *bhi = nullptr, *blo = nullptr;   // padded radial tables
-    void *ahi = nullptr, *alo = nullptr;   // split ring spectra
+    int BN = 0, tmem_cols = 0, ld = 0;
+    void *bhi = nullptr, *blo = nullptr;   // padded radial tables [k][BN][ld]
+    void *ahi = nullptr, *alo = nullptr;   // ring spectra planes [k][2 chunk][ld]
     CUtensorMap mA0, mA1, mB0, mB1;
 };
 
@@ -239,50 +246,90 @@ void ffb_tc_release(ffb_plan_t p) {
     p->tc = nullptr;
 }
 
-static int tc_prepare(ffb_plan_t p, cudaStream_t s) {
+static bool is_bf16(int prec) { return prec == FFB_BF16 || prec == FFB_BF16X3; }
+static bool is_x3(int prec) { return prec == FFB_BF16X3 || prec == FFB_TF32X3; }
+
+static size_t tc_smem_bytes(int prec, int ld, int BN) {
+    const int es = is_bf16(prec) ? 2 : 4;
+    const int nch = ld / (128 / es);
+    const int np = is_x3(prec) ? 2 : 1;
+    const size_t tiles = (size_t)np * nch * 128 * 128 + (size_t)np * nch * BN * 128;
+    const size_t stage = (size_t)64 * (2 * BN + 2) * 4;
+    return 1024 + (tiles > stage ? tiles : stage) + 64;
+}
+
+// shared memory of one CTA: all K of the A and B planes must fit
+bool ffb_tc_supported(ffb_plan_t p) {
+    const int es = is_bf16(p->precision) ? 2 : 4;
+    const int kch = 128 / es;
+    const int ld = (p->n_xi + kch - 1) / kch * kch;
+    const int BN = (p->pmax + 15) & ~15;
+    if (BN > 256) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return tc_smem_bytes(p->precision, ld, BN) <= (size_t)optin;
+}
+
+int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
     TcState *t = tc_state(p);
-    if (t->prepared == p->precision) return FFB_OK;
-    const bool bf16 = (p->precision == FFB_BF16 || p->precision == FFB_BF16X3);
+    const bool bf16 = is_bf16(p->precision);
     const size_t es = bf16 ? 2 : 4;
-    const int kch = (int)(128 / es);
-    if (p->n_xi % kch) return FFB_ERR_UNSUPPORTED;
-    t->BN = (p->pmax + 15) & ~15;
-    if (t->BN > 256) return FFB_ERR_UNSUPPORTED;
-    t->tmem_cols = 32;
-    while (t->tmem_cols < t->BN) t->tmem_cols <<= 1;
-    for (void **q : {&t->bhi, &t->blo, &t->ahi, &t->alo})
-        if (*q) {
-            cudaFree(*q);
-            *q = nullptr;
+    if (t->prepared != p->precision) {
+        const int kch = (int)(128 / es);
+        t->ld = (p->n_xi + kch - 1) / kch * kch;
+        t->BN = (p->pmax + 15) & ~15;
+        if (t->BN > 256) return FFB_ERR_UNSUPPORTED;
+        t->tmem_cols = 32;
+        while (t->tmem_cols < t->BN) t->tmem_cols <<= 1;
+        for (void **q : {&t->bhi, &t->blo, &t->ahi, &t->alo})
+            if (*q) {
+                cudaFree(*q);
+                *q = nullptr;
+            }
+        const size_t nb = (size_t)(p->k_max + 1) * t->BN * t->ld;
+        const size_t na = (size_t)(p->k_max + 1) * p->chunk * 2 * t->ld;
+        int e;
+        if ((e = ffb_check_cuda(cudaMalloc(&t->bhi, nb * es)))) return e;
+        if ((e = ffb_check_cuda(cudaMalloc(&t->blo, nb * es)))) return e;
+        if ((e = ffb_check_cuda(cudaMalloc(&t->ahi, na * es)))) return e;
+        if ((e = ffb_check_cuda(cudaMalloc(&t->alo, na * es)))) return e;
+        // padding columns j >= n_xi stay zero for the whole life of the plan
+        if ((e = ffb_check_cuda(cudaMemsetAsync(t->ahi, 0, na * es, s)))) return e;
+        if ((e = ffb_check_cuda(cudaMemsetAsync(t->alo, 0, na * es, s)))) return e;
+        const unsigned g = (unsigned)((nb + 255) / 256);
+        if (bf16)
+            k_prep_bpad<true><<<g, 256, 0, s>>>(p->d_B64, p->d_p, p->d_off, p->k_max, t->BN, p->n_xi, t->ld,
+                                                t->bhi, t->blo);
+        else
+            k_prep_bpad<false><<<g, 256, 0, s>>>(p->d_B64, p->d_p, p->d_off, p->k_max, t->BN, p->n_xi, t->ld,
+                                                 t->bhi, t->blo);
+        p->launches++;
+        if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
+        const uint64_t rows = 2ull * p->chunk;
+        if ((e = make_map(&t->mA0, t->ahi, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
+        if ((e = make_map(&t->mA1, t->alo, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
+        if ((e = make_map(&t->mB0, t->bhi, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
+        if ((e = make_map(&t->mB1, t->blo, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
+        t->prepared = p->precision;
+    }
+    if (out) {
+        switch (p->precision) {
+            case FFB_TF32: out->fmt = FFB_FMT_TF32; break;
+            case FFB_TF32X3: out->fmt = FFB_FMT_TF32X2; break;
+            case FFB_BF16: out->fmt = FFB_FMT_BF16; break;
+            default: out->fmt = FFB_FMT_BF16X2; break;
         }
-    const size_t nb = (size_t)(p->k_max + 1) * t->BN * p->n_xi;
-    const size_t na = (size_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi;
-    int e;
-    if ((e = ffb_check_cuda(cudaMalloc(&t->bhi, nb * es)))) return e;
-    if ((e = ffb_check_cuda(cudaMalloc(&t->blo, nb * es)))) return e;
-    if ((e = ffb_check_cuda(cudaMalloc(&t->ahi, na * es)))) return e;
-    if ((e = ffb_check_cuda(cudaMalloc(&t->alo, na * es)))) return e;
-    const unsigned g = (unsigned)((nb + 255) / 256);
-    if (bf16) k_prep_bpad<true><<<g, 256, 0, s>>>(p->d_B64, p->d_p, p->d_off, p->k_max, t->BN, p->n_xi, t->bhi, t->blo);
-    else k_prep_bpad<false><<<g, 256, 0, s>>>(p->d_B64, p->d_p, p->d_off, p->k_max, t->BN, p->n_xi, t->bhi, t->blo);
-    p->launches++;
-    if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
-    const uint64_t rows = 2ull * p->chunk;
-    // plain TF32 reads the float32 spectra directly
-    void *a0 = (p->precision == FFB_TF32) ? (void *)p->d_Fhat : t->ahi;
-    if ((e = make_map(&t->mA0, a0, bf16, p->n_xi, rows, p->k_max + 1, 128))) return e;
-    if ((e = make_map(&t->mA1, t->alo, bf16, p->n_xi, rows, p->k_max + 1, 128))) return e;
-    if ((e = make_map(&t->mB0, t->bhi, bf16, p->n_xi, t->BN, p->k_max + 1, t->BN))) return e;
-    if ((e = make_map(&t->mB1, t->blo, bf16, p->n_xi, t->BN, p->k_max + 1, t->BN))) return e;
-    t->prepared = p->precision;
+        out->p0 = t->ahi;
+        out->p1 = t->alo;
+        out->ld = t->ld;
+    }
     return FFB_OK;
 }
 
 template <int KIND, int NPA, int NPB, int NPROD>
 static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    const int es = (KIND == 0) ? 4 : 2;
-    const int nch = p->n_xi / (128 / es);
-    const size_t smem = 1024 + (size_t)NPA * nch * 128 * 128 + (size_t)NPB * nch * t->BN * 128 + 64;
+    const size_t smem = tc_smem_bytes(p->precision, t->ld, t->BN);
     static int attr = 0;
     if (attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD>,
@@ -292,41 +339,26 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     }
     dim3 g((2 * nimg + 127) / 128, p->k_max + 1);
     ProfScope ps(p, FFB_KC_BESSEL, s);
-    k_tc_bessel<KIND, NPA, NPB, NPROD><<<g, 128, smem, s>>>(t->mA0, t->mA1, t->mB0, t->mB1, p->n_xi, nimg, p->d_p,
+    k_tc_bessel<KIND, NPA, NPB, NPROD><<<g, 128, smem, s>>>(t->mA0, t->mA1, t->mB0, t->mB1, t->ld, nimg, p->d_p,
                                                            p->d_off, p->P, d_coef_chunk, t->BN, t->tmem_cols,
                                                            p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
 
-// shared memory of one CTA: all K of the A and B planes must fit
-bool ffb_tc_supported(ffb_plan_t p) {
-    const bool bf16 = (p->precision == FFB_BF16 || p->precision == FFB_BF16X3);
-    const bool two = (p->precision == FFB_BF16X3 || p->precision == FFB_TF32X3);
-    const int es = bf16 ? 2 : 4;
-    if (p->n_xi % (128 / es)) return false;
-    const int nch = p->n_xi / (128 / es);
-    const int BN = (p->pmax + 15) & ~15;
-    if (BN > 256) return false;
-    const size_t smem = 1024 + (size_t)(two ? 2 : 1) * nch * 128 * 128 + (size_t)(two ? 2 : 1) * nch * BN * 128 + 64;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return smem <= (size_t)optin;
-}
-
-int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    int e = tc_prepare(p, s);
+int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s) {
+    int e = ffb_tc_prepare(p, s, nullptr);
     if (e) return e;
     TcState *t = tc_state(p);
-    const int64_t total = (int64_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi;
-    const unsigned g = (unsigned)((total + 255) / 256);
-    if (p->precision != FFB_TF32) {
+    if (!planes_ready) {
+        const int64_t total = (int64_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi;
+        const unsigned g = (unsigned)((total + 255) / 256);
         ProfScope ps(p, FFB_KC_BESSEL, s);
         switch (p->precision) {
-            case FFB_TF32X3: k_split_planes<false, true><<<g, 256, 0, s>>>(p->d_Fhat, total, t->ahi, t->alo); break;
-            case FFB_BF16: k_split_planes<true, false><<<g, 256, 0, s>>>(p->d_Fhat, total, t->ahi, t->alo); break;
-            default: k_split_planes<true, true><<<g, 256, 0, s>>>(p->d_Fhat, total, t->ahi, t->alo); break;
+            case FFB_TF32: k_split_planes<false, false><<<g, 256, 0, s>>>(p->d_Fhat, total, p->n_xi, t->ld, t->ahi, t->alo); break;
+            case FFB_TF32X3: k_split_planes<false, true><<<g, 256, 0, s>>>(p->d_Fhat, total, p->n_xi, t->ld, t->ahi, t->alo); break;
+            case FFB_BF16: k_split_planes<true, false><<<g, 256, 0, s>>>(p->d_Fhat, total, p->n_xi, t->ld, t->ahi, t->alo); break;
+            default: k_split_planes<true, true><<<g, 256, 0, s>>>(p->d_Fhat, total, p->n_xi, t->ld, t->ahi, t->alo); break;
         }
         p->launches++;
         if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
@@ -338,4 +370,251 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream
         case FFB_BF16X3: return launch_tc<1, 2, 2, 3>(p, t, nimg, d_coef_chunk, s);
         default: return FFB_ERR_ARG;
     }
+}
+
+// ---------------------------------------------------------------------------
+// a6/a7 on the tensor cores: C^(k) += X X^T, X = [Re A^(k), Im A^(k)] with rows
+// q (padded to M = 128 with zero rows) and K = (image, re/im).  One CTA owns
+// one k and a range of images; it stages tiles of TI images from the
+// interleaved coefficient array into the 128-byte-swizzle K-major layout
+// (hi/lo split in registers, the k = 0 rows shifted by the pilot mean and
+// their imaginary column zero) while the next tile's coefficients are already
+// in flight to registers, and issues the MMA chain (double-buffered tiles,
+// mbarrier per buffer).  Tile t accumulates into TMEM accumulator t mod NACC:
+// the tensor core's float32 accumulation error grows with the number of
+// accumulate steps, so no chain covers more than ~128 images; the NACC
+// accumulators are summed in float64 and added to the float64 accumulator.
+// ---------------------------------------------------------------------------
+#define COV_PF 16   // coefficient values per thread per tile held in registers
+
+template <int KIND, int NP>
+__global__ void __launch_bounds__(128, 1)
+k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restrict__ pk_,
+         const int *__restrict__ off_, const int *__restrict__ cov_off, const float *__restrict__ shift,
+         int64_t per, double *__restrict__ acc, int acc_cols, int nacc, int *status) {
+    constexpr int ES = (KIND == 0) ? 4 : 2;
+    constexpr int KCH = 128 / ES;               // K elements per chunk
+    constexpr int NCHT = 2;                     // chunks per tile
+    constexpr int TI = NCHT * KCH / 2;          // images per tile (2 K entries each)
+    constexpr uint32_t CH_BYTES = 128u * 128u;  // one chunk of 128 rows
+    constexpr uint32_t BUF_BYTES = NP * NCHT * CH_BYTES;
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(sm + 2 * BUF_BYTES);   // [0], [1]: buffer free
+    uint32_t *slot = (uint32_t *)(bars + 4);
+    int *okflag = (int *)(slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x;
+    const int p = pk_[k], o = off_[k];
+    const int BN = max(16, (p + 15) & ~15);
+    const int64_t ib = (int64_t)blockIdx.y * per;
+    const int64_t ie = min(n, ib + per);
+    const int ntiles = (int)((ie - ib + TI - 1) / TI);
+    const int items = TI * p;                   // (image, q) pairs per tile, <= 128 * COV_PF
+
+    for (uint32_t i = threadIdx.x; i < 2 * BUF_BYTES / 16; i += 128)
+        ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::fence_mbar_init();
+        *okflag = (items <= 128 * COV_PF) ? 1 : 0;
+        if (items > 128 * COV_PF) ffb_flag(status, FFB_ERR_UNSUPPORTED);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 512u);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *slot;
+    const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
+
+    float2 pre[COV_PF];
+    auto load_tile = [&](int t) {
+        const int64_t i0 = ib + (int64_t)t * TI;
+#pragma unroll
+        for (int u = 0; u < COV_PF; ++u) {
+            const int it = threadIdx.x + 128 * u;
+            float2 v = make_float2(0.f, 0.f);
+            if (it < items) {
+                const int ii = it / p, q = it - ii * p;
+                if (i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
+            }
+            pre[u] = v;
+        }
+    };
+    if (*okflag && ntiles > 0) load_tile(0);
+    for (int t = 0; t < ntiles && *okflag; ++t) {
+        const int buf = t & 1;
+        uint8_t *B0 = sm + buf * BUF_BYTES;
+        if (t >= 2) {
+            if (!tc::mbar_wait(&bars[buf], (uint32_t)(((t - 2) >> 1) & 1), TC_BUDGET)) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+        }
+        float2 cur[COV_PF];
+#pragma unroll
+        for (int u = 0; u < COV_PF; ++u) cur[u] = pre[u];
+        if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
+#pragma unroll
+        for (int u = 0; u < COV_PF; ++u) {
+            const int it = threadIdx.x + 128 * u;
+            if (it >= items) break;
+            const int ii = it / p, q = it - ii * p;
+            float re = cur[u].x, im = cur[u].y;
+            if (k == 0) {   // shifted real part; images past the range stay zero
+                re = (ib + (int64_t)t * TI + ii < ie) ? re - shift[q] : 0.f;
+                im = 0.f;
+            }
+            const int kidx = 2 * ii;                 // K index of the real part
+            const int ch = kidx / KCH, e = kidx % KCH;
+            const uint32_t byte = (uint32_t)e * ES;
+            const uint32_t off = ch * CH_BYTES + (q >> 3) * 1024u + (q & 7) * 128u +
+                                 ((((byte >> 4) ^ (uint32_t)(q & 7)) << 4) | (byte & 15u));
+            if (KIND == 0) {
+                const float rh = tf32_round(re), ih = tf32_round(im);
+                *(float2 *)(B0 + off) = make_float2(rh, ih);
+                if (NP > 1) *(float2 *)(B0 + NCHT * CH_BYTES + off) = make_float2(re - rh, im - ih);
+            } else {
+                const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+                *(__nv_bfloat162 *)(B0 + off) = __halves2bfloat162(rh, ih);
+                if (NP > 1)
+                    *(__nv_bfloat162 *)(B0 + NCHT * CH_BYTES + off) = __halves2bfloat162(
+                        __float2bfloat16_rn(re - __bfloat162float(rh)), __float2bfloat16_rn(im - __bfloat162float(ih)));
+            }
+        }
+        tc::fence_async_shared();   // generic-proxy writes -> visible to the tensor core
+        __syncthreads();
+        if (threadIdx.x == 0 && *okflag) {
+            tc::fence_after_sync();
+            const int a = t % nacc;
+            const uint32_t dt = tbase + (uint32_t)(a * acc_cols);
+#pragma unroll
+            for (int pr = 0; pr < (NP > 1 ? 3 : 1); ++pr) {
+                const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+                for (int ch = 0; ch < NCHT; ++ch) {
+                    const uint32_t a0 = tc::smem_u32(B0 + (size_t)(pa * NCHT + ch) * CH_BYTES);
+                    const uint32_t b0 = tc::smem_u32(B0 + (size_t)(pb * NCHT + ch) * CH_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
+                        const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
+                        const uint32_t accf = (t >= nacc || pr > 0 || ch > 0 || ks > 0) ? 1u : 0u;
+                        if (KIND == 0) tc::mma_tf32(dt, ad, bd, id, accf);
+                        else tc::mma_bf16(dt, ad, bd, id, accf);
+                    }
+                }
+            }
+            tc::mma_commit(&bars[buf]);
+        }
+    }
+    __syncthreads();
+    // the last commit covers every MMA issued before it
+    if (ntiles > 0 && *okflag) {
+        const int t = ntiles - 1;
+        if (!tc::mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1), TC_BUDGET)) {
+            ffb_flag(status, FFB_ERR_TIMEOUT);
+            atomicExch(okflag, 0);
+        }
+    }
+    tc::fence_after_sync();
+    __syncthreads();
+    if (ntiles > 0 && *okflag) {
+        const int q = 32 * warp + lane;
+        const int used = min(nacc, ntiles);
+        double *blk = acc + cov_off[k];
+        for (int c16 = 0; c16 < BN; c16 += 16) {
+            double sum[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sum[i] = 0.0;
+            for (int a = 0; a < used; ++a) {
+                float v[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * acc_cols + c16), v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[i] += (double)v[i];
+            }
+            if (q < p) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c16 + i < p) atomicAdd(&blk[(size_t)q * p + c16 + i], sum[i]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512u);
+}
+
+// k = 0 mean: sum0[q] += sum_i (Re a_{i,0,q} - shift_q), float64, one CTA per
+// image range
+__global__ void k_cov_sum0(const float2 *__restrict__ coef, int64_t n, int P, int p0, const float *__restrict__ shift,
+                           int64_t per, double *__restrict__ sum0) {
+    const int64_t ib = (int64_t)blockIdx.x * per;
+    const int64_t ie = min(n, ib + per);
+    for (int q = threadIdx.x; q < p0; q += blockDim.x) {
+        double s = 0.0;
+        for (int64_t i = ib; i < ie; ++i) s += (double)(coef[i * P + q].x - shift[q]);
+        atomicAdd(&sum0[q], s);
+    }
+}
+
+// sized for two planes in every precision: one CTA per SM, so the 512-column
+// TMEM allocation never waits for another CTA
+static size_t tc_cov_smem(int prec) {
+    (void)prec;
+    return 1024 + 2 * (size_t)2 * 2 * 128 * 128 + 64;
+}
+
+bool ffb_tc_cov_supported(ffb_plan_t p) {
+    if (p->precision == FFB_FP32) return false;
+    if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
+    const int ti = is_bf16(p->precision) ? 64 : 32;
+    if (ti * p->pmax > 128 * COV_PF) return false;    // one tile's values fit the register prefetch
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return tc_cov_smem(p->precision) <= (size_t)optin;
+}
+
+template <int KIND, int NP>
+static int launch_tc_cov(ffb_plan_t p, const float *d_coef, int64_t n, int64_t per, cudaStream_t s) {
+    const size_t smem = tc_cov_smem(p->precision);
+    static int attr = 0;
+    if (attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_cov<KIND, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    int cols = 32;
+    while (cols < ((p->pmax + 15) & ~15)) cols <<= 1;
+    const int nacc = 512 / cols > 8 ? 8 : 512 / cols;   // rotating float32 accumulators in TMEM
+    dim3 g(p->k_max + 1, (unsigned)((n + per - 1) / per));
+    ProfScope ps(p, FFB_KC_COV, s);
+    k_tc_cov<KIND, NP><<<g, 128, smem, s>>>((const float2 *)d_coef, n, p->P, p->d_p, p->d_off, p->d_cov_off,
+                                           p->d_shift, per, p->d_acc, cols, nacc, p->d_status);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
+    const int64_t per = 1024;
+    if ((n + per - 1) / per > 65535) return FFB_ERR_ARG;
+    int e;
+    switch (p->precision) {
+        case FFB_TF32: e = launch_tc_cov<0, 1>(p, d_coef, n, per, s); break;
+        case FFB_TF32X3: e = launch_tc_cov<0, 2>(p, d_coef, n, per, s); break;
+        case FFB_BF16: e = launch_tc_cov<1, 1>(p, d_coef, n, per, s); break;
+        default: e = launch_tc_cov<1, 2>(p, d_coef, n, per, s); break;
+    }
+    if (e) return e;
+    const int64_t per0 = 2048;
+    ProfScope ps(p, FFB_KC_COVAUX, s);
+    k_cov_sum0<<<(unsigned)((n + per0 - 1) / per0), 64, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0],
+                                                                p->d_shift, per0, p->d_sum0);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
 }

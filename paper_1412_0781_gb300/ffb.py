@@ -37,6 +37,9 @@ SIGNATURES = {
     "ffb_expand_adjoint": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_covariance": (_i, [_vp, _vp, _i64, _i, _vp]),
     "ffb_cov_get": (_i, [_vp, _vp, _vp, _vp]),
+    "ffb_cov_export": (_i, [_vp, _pd, _vp]),
+    "ffb_cov_merge": (_i, [_i, _pi, _i, _pd, _pd]),
+    "ffb_cov_import": (_i, [_vp, _pd, _vp]),
     "ffb_eig": (_i, [_vp, _vp, _vp, _vp]),
     "ffb_eig_blocks": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ffb_select": (_i, [_vp, _i, _i, _d, _i64, _pd, _vp]),
@@ -66,6 +69,18 @@ def load(path=LIB_PATH):
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def cov_merge(p, states):
+    """Host-only pooling of covariance states (rows of ``states``) for block
+    sizes ``p`` (list of p_k); see ffb_cov_merge."""
+    import numpy as np
+    st = np.ascontiguousarray(states, dtype=np.float64)
+    pk = (ctypes.c_int * len(p))(*p)
+    out = np.zeros(st.shape[-1])
+    _check(load().ffb_cov_merge(len(p) - 1, pk, int(st.shape[0]), st.ctypes.data_as(_pd),
+                                out.ctypes.data_as(_pd)), "ffb_cov_merge")
+    return out
 
 
 class FFBError(RuntimeError):
@@ -208,6 +223,21 @@ class Plan:
         _check(load().ffb_cov_get(self._h, _ptr(mean, torch.float64, "mean"), _ptr(C, torch.float64, "C"),
                                   _stream(stream)), "ffb_cov_get")
         return mean, C
+
+    def state_len(self):
+        return 1 + self.p[0] + self.cov_total
+
+    def cov_export(self, stream=None):
+        """Synchronising: float64 numpy state [n, mean0, packed C]."""
+        import numpy as np
+        st = np.zeros(self.state_len())
+        _check(load().ffb_cov_export(self._h, st.ctypes.data_as(_pd), _stream(stream)), "ffb_cov_export")
+        return st
+
+    def cov_import(self, state, stream=None):
+        import numpy as np
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        _check(load().ffb_cov_import(self._h, st.ctypes.data_as(_pd), _stream(stream)), "ffb_cov_import")
 
     def eig(self, device="cuda", stream=None):
         """Synchronising: (evals float64 (P,), packed evecs float64 (sum p_k^2,))."""

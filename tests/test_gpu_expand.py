@@ -265,3 +265,26 @@ def test_launch_count_grows(dev):
     before = gp.launch_count()
     gp.expand(torch.zeros((5, 32, 32), device=dev))
     assert gp.launch_count() >= before + 4
+
+
+def test_cov_export_merge_import_roundtrip(dev):
+    """Statistics of two disjoint halves pooled with ffb_cov_merge equal the
+    statistics of the whole stack; importing them reproduces its eigenpairs."""
+    from paper_1412_0781_gb300.ffb import cov_merge
+    spec = data.TINY
+    imgs, _, _ = data.blob_stack(spec)
+    gp = gplan(spec.L)
+    coef = gp.expand(imgs.to(dev))
+    gp.covariance(coef, reset=True)
+    full = gp.cov_export()
+    ev_full, _ = gp.eig()
+    gp.covariance(coef[:120].contiguous(), reset=True)
+    s1 = gp.cov_export()
+    gp.covariance(coef[120:].contiguous(), reset=True)
+    s2 = gp.cov_export()
+    pooled = cov_merge(gp.p, np.stack([s1, s2]))
+    assert pooled[0] == full[0] == spec.n
+    assert rel(pooled[1:], full[1:]) < 1e-6
+    gp.cov_import(pooled)
+    ev, _ = gp.eig()
+    assert rel(ev.cpu().numpy(), ev_full.cpu().numpy()) < 1e-6

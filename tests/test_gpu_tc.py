@@ -53,6 +53,31 @@ def test_tc_quadrature_matches_oracle(dev, L, n, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("L,n", [(32, 200), (128, 3000)])
+def test_tc_covariance_matches_oracle(dev, L, n):
+    """Covariance blocks (Eqs. ck, ck_0) from the tensor-core SYRK, fed the
+    oracle's own coefficients (rounded to float32), against the oracle's
+    two-pass float64 covariance."""
+    op = fb.make_plan(L, 0.5, L / 2)
+    rng = np.random.default_rng(L)
+    a = (rng.standard_normal((n, op.P)) + 1j * rng.standard_normal((n, op.P))) + 2.0
+    a[:, :op.p[0]] = a[:, :op.p[0]].real
+    a = a.astype(np.complex64).astype(np.complex128)
+    mean0, blocks = fb.covariance(op, a)
+    Co = np.concatenate([b.ravel() for b in blocks])
+    coef = torch.view_as_real(torch.from_numpy(a.astype(np.complex64))).contiguous().to(dev)
+    for prec, tol in (("tf32x3", 1e-5), ("bf16x3", 1e-5), ("tf32", 5e-3), ("bf16", 3e-2)):
+        plan = Plan(L, 0.5, L / 2, eps=1e-6, precision=prec)
+        plan.covariance(coef[: n // 3].contiguous(), reset=True)
+        plan.covariance(coef[n // 3:].contiguous(), reset=False)
+        m, C = plan.cov_get()
+        err = np.linalg.norm(C.cpu().numpy() - Co) / np.linalg.norm(Co)
+        print("L=%d %s covariance rel L2: %.3e" % (L, prec, err))
+        assert err <= tol
+        assert np.linalg.norm(m.cpu().numpy() - mean0) / np.linalg.norm(mean0) <= 1e-6
+        plan.close()
+
+
 def test_tc_covariance_and_eigs_with_compensated_quadrature(dev):
     spec = data.TINY
     imgs, _, _ = data.blob_stack(spec)
