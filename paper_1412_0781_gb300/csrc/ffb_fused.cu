@@ -22,6 +22,8 @@
 //
 // Both halves compute the same row transforms (phase 1); the columns and the
 // nodes are split.
+#include <cuda_bf16.h>
+
 #include "ffb_internal.cuh"
 
 #define FUS_WARPS 16
@@ -32,15 +34,25 @@
 // Stockham FFT of compile-time power-of-two length by one warp (radix 4,
 // then one radix-2 stage when log2(N) is odd).  Same pass structure as
 // smem_fft, with every division and modulo by a power of two.
-// ---------------------------------------------------------------------------
-template <int N, bool INV>
+//
+// The buffers are addressed through swz(i) = i ^ (5 ((i >> 4) & 3)): with
+// t = bits 4-5 of the complex index, the low nibble is XORed with (t, t).
+// A radix-4 stage with Ns = 1 stores a half warp's outputs at i = 4j + r
+// (j = lane, bits 2-5) and one with Ns = 4 at i = 16(j/4) + j%4 + 4r; without
+// the swizzle four lanes share each 8-byte bank slot (i mod 16); with it the
+// 16 lanes of every store land on 16 distinct slots, and runs of consecutive
+// indices (all loads, the Ns >= 16 stores) stay distinct as well.  Every
+// access to a buffer handed to warp_fft_pow2 goes through swz().
+__device__ __forceinline__ int swz(int i) { return i ^ (5 * ((i >> 4) & 3)); }
+
+template <int N, bool INV, int FIRST = 0>
 __device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const float2 *__restrict__ tw, int lane) {
     constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9 : (N == 1024) ? 10 : -1;
     static_assert(LOG > 0, "power-of-two length 64..1024");
     constexpr int N4 = LOG / 2;           // radix-4 stages
     constexpr bool TAIL2 = (LOG & 1);     // one radix-2 stage
 #pragma unroll
-    for (int s = 0; s < N4; ++s) {
+    for (int s = FIRST; s < N4; ++s) {
         const int Ns = 1 << (2 * s);
         constexpr int nb = N / 4;
         const int tshift = LOG - 2 * s - 2;   // tstep = N / (Ns * 4)
@@ -50,7 +62,7 @@ __device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const flo
             const int k = j & (Ns - 1);
             float2 v[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) v[r] = a[j + r * nb];
+            for (int r = 0; r < 4; ++r) v[r] = a[swz(j + r * nb)];
 #pragma unroll
             for (int r = 1; r < 4; ++r) {
                 float2 wv = __ldg(&tw[((r * k) << tshift) & (N - 1)]);
@@ -60,7 +72,7 @@ __device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const flo
             dft4<INV>(v);
             const int base = ((j >> (2 * s)) << (2 * s + 2)) + k;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) b[base + r * Ns] = v[r];
+            for (int r = 0; r < 4; ++r) b[swz(base + r * Ns)] = v[r];
         }
         __syncwarp();
         float2 *t = a;
@@ -75,15 +87,15 @@ __device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const flo
             const int j = lane + 32 * jj;
             const int k = j & (Ns - 1);
             float2 v[2];
-            v[0] = a[j];
-            v[1] = a[j + nb];
+            v[0] = a[swz(j)];
+            v[1] = a[swz(j + nb)];
             float2 wv = __ldg(&tw[k & (N - 1)]);  // tstep = 1
             if (INV) wv.y = -wv.y;
             v[1] = cmul(v[1], wv);
             dft2<INV>(v);
             const int base = ((j / Ns) * Ns * 2) + k;
-            b[base] = v[0];
-            b[base + Ns] = v[1];
+            b[swz(base)] = v[0];
+            b[swz(base + Ns)] = v[1];
         }
         __syncwarp();
         float2 *t = a;
@@ -97,6 +109,30 @@ __device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const flo
 template <int N>
 __host__ __device__ constexpr bool fft_pow2_result_in_b() {
     return (((N == 64) ? 3 : (N == 128) ? 4 : (N == 256) ? 4 : (N == 512) ? 5 : 5) & 1) != 0;
+}
+
+// Length-N forward DFT of a sequence whose only nonzeros are the L = N/2
+// values placed at (a - L/2) mod N, a = lane + 32 q (q < N/64), given in z[q]:
+// they occupy [0, N/4) and [3N/4, N).  Every radix-4 butterfly of the first
+// Stockham stage (Ns = 1, inputs j, j + N/4, j + N/2, j + 3N/4) then has two
+// zero inputs and its two nonzero ones in the same lane (z[N/128 + jj] at j,
+// z[jj] at j + 3N/4 for j = lane + 32 jj), so that stage runs from registers
+// and the remaining stages continue in shared memory.
+template <int N>
+__device__ __forceinline__ float2 *warp_fft_halfzero(const float2 *z, float2 *a, float2 *b,
+                                                     const float2 *__restrict__ tw, int lane) {
+#pragma unroll
+    for (int jj = 0; jj < N / 128; ++jj) {
+        const int j = lane + 32 * jj;
+        const float2 v0 = z[N / 128 + jj], v3 = z[jj];
+        // dft4 of (v0, 0, 0, v3), forward: (v0 + v3, v0 + i v3, v0 - v3, v0 - i v3)
+        a[swz(4 * j + 0)] = cadd(v0, v3);
+        a[swz(4 * j + 1)] = make_float2(v0.x - v3.y, v0.y + v3.x);
+        a[swz(4 * j + 2)] = csub(v0, v3);
+        a[swz(4 * j + 3)] = make_float2(v0.x + v3.y, v0.y - v3.x);
+    }
+    __syncwarp();
+    return warp_fft_pow2<N, false, 1>(a, b, tw, lane);
 }
 
 template <int N, int W>
@@ -128,23 +164,20 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             x[q] = __ldg(&im[(size_t)a1 * L + lane + 32 * q]);
             y[q] = __ldg(&im[(size_t)(a1 + 1) * L + lane + 32 * q]);
         }
-#pragma unroll
-        for (int q = 0; q < N / 32; ++q) bufA[lane + 32 * q] = make_float2(0.f, 0.f);
-        __syncwarp();
         const float c1 = corr[a1], c2 = corr[a1 + 1];
+        float2 z[L / 32];
 #pragma unroll
         for (int q = 0; q < L / 32; ++q) {
             const int a2 = lane + 32 * q;
             bad |= !(isfinite(x[q]) && isfinite(y[q]));
             const float ca = corr[a2];
-            bufA[(a2 - off) & (N - 1)] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
+            z[q] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
         }
-        __syncwarp();
-        const float2 *X = warp_fft_pow2<N, false>(bufA, bufB, tw, lane);
+        const float2 *X = warp_fft_halfzero<N>(z, bufA, bufB, tw, lane);
         for (int e = lane; e < MH; e += 32) {
             const int m = (e - H) & (N - 1);
-            const float2 Z = X[m];
-            const float2 Zc = cconj(X[(N - m) & (N - 1)]);
+            const float2 Z = X[swz(m)];
+            const float2 Zc = cconj(X[swz((N - m) & (N - 1))]);
             const float2 D = csub(Z, Zc);
             S[e * SLD + a1] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
             S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
@@ -158,17 +191,11 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     const int m1lo = (half == 0) ? -H : -(N / 2) - H;
     for (int e = warp; e < MH; e += FUS_WARPS) {
         float2 *row = S + e * SLD;
+        float2 z[L / 32];
 #pragma unroll
-        for (int q = 0; q < N / 32; ++q) bufA[lane + 32 * q] = make_float2(0.f, 0.f);
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < L / 32; ++q) {
-            const int a1 = lane + 32 * q;
-            bufA[(a1 - off) & (N - 1)] = row[a1];
-        }
-        __syncwarp();
-        const float2 *X = warp_fft_pow2<N, false>(bufA, bufB, tw, lane);
-        for (int c = lane; c < MH; c += 32) row[c] = X[(c + m1lo) & (N - 1)];
+        for (int q = 0; q < L / 32; ++q) z[q] = row[lane + 32 * q];
+        const float2 *X = warp_fft_halfzero<N>(z, bufA, bufB, tw, lane);
+        for (int c = lane; c < MH; c += 32) row[c] = X[swz((c + m1lo) & (N - 1))];
         __syncwarp();
     }
     __syncthreads();
@@ -226,10 +253,10 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 // with the conjugate completion of the ring and the 2 pi / n_theta weight.
 // grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads (one warp per ring)
 // ---------------------------------------------------------------------------
-template <int NTH>
+template <int NTH, int FMT>
 __global__ void __launch_bounds__(32 * RFFT_RB)
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
-           float *__restrict__ Fhat) {
+           void *__restrict__ out0, void *__restrict__ out1, int ld) {
     constexpr int NH = NTH / 2;
     extern __shared__ float2 smr[];
     float2 *ringA = smr;                    // [RFFT_RB][NTH]
@@ -242,8 +269,8 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
     for (int t = threadIdx.x; t < nrings * NH; t += 32 * RFFT_RB) {
         const int jj = t / NH, l = t - jj * NH;
         const float2 v = src[(size_t)jj * NH + l];
-        ringA[jj * NTH + l] = v;
-        ringA[jj * NTH + l + NH] = cconj(v);
+        ringA[jj * NTH + swz(l)] = v;
+        ringA[jj * NTH + swz(l + NH)] = cconj(v);
     }
     __syncthreads();
     if (warp < nrings) warp_fft_pow2<NTH, false>(ringA + warp * NTH, ringB + warp * NTH, twT, lane);
@@ -253,8 +280,20 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
     for (int t = threadIdx.x; t < (kmax + 1) * 2 * RFFT_RB; t += 32 * RFFT_RB) {
         const int jj = t % RFFT_RB, cc = (t / RFFT_RB) & 1, k = t / (2 * RFFT_RB);
         if (jj < nrings) {
-            const float2 v = res[jj * NTH + k];
-            Fhat[(((size_t)k * chunk + img) * 2 + cc) * n_xi + j0 + jj] = scale * (cc ? v.y : v.x);
+            const float2 v = res[jj * NTH + swz(k)];
+            const float x = scale * (cc ? v.y : v.x);
+            const size_t idx = (((size_t)k * chunk + img) * 2 + cc) * ld + j0 + jj;
+            if (FMT == FFB_FMT_F32) {
+                ((float *)out0)[idx] = x;
+            } else if (FMT == FFB_FMT_TF32 || FMT == FFB_FMT_TF32X2) {
+                const float h = tf32_round(x);
+                ((float *)out0)[idx] = h;
+                if (FMT == FFB_FMT_TF32X2) ((float *)out1)[idx] = x - h;
+            } else {
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                ((__nv_bfloat16 *)out0)[idx] = h;
+                if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
         }
     }
 }
@@ -305,29 +344,41 @@ int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int 
     return FFB_ERR_UNSUPPORTED;
 }
 
-template <int NTH>
-static int launch_ring(ffb_plan_t p, int m, const float2 *Fpol, cudaStream_t s) {
+template <int NTH, int FMT>
+static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
     static int attr = 0;
     const size_t smem = sizeof(float2) * 2 * RFFT_RB * (size_t)NTH;
     if (smem > 48 * 1024 && attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_fft<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem));
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_fft<NTH, FMT>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         attr = (int)smem;
     }
     dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
     ProfScope ps(p, FFB_KC_RING_FFT, s);
-    k_ring_fft<NTH><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, p->chunk, p->d_twT, p->d_Fhat);
+    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, p->chunk, p->d_twT, o.p0, o.p1, o.ld);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
 
-int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, cudaStream_t s) {
+template <int NTH>
+static int launch_ring(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
+    switch (o.fmt) {
+        case FFB_FMT_F32: return launch_ring_fmt<NTH, FFB_FMT_F32>(p, m, Fpol, o, s);
+        case FFB_FMT_TF32: return launch_ring_fmt<NTH, FFB_FMT_TF32>(p, m, Fpol, o, s);
+        case FFB_FMT_TF32X2: return launch_ring_fmt<NTH, FFB_FMT_TF32X2>(p, m, Fpol, o, s);
+        case FFB_FMT_BF16: return launch_ring_fmt<NTH, FFB_FMT_BF16>(p, m, Fpol, o, s);
+        case FFB_FMT_BF16X2: return launch_ring_fmt<NTH, FFB_FMT_BF16X2>(p, m, Fpol, o, s);
+        default: return FFB_ERR_ARG;
+    }
+}
+
+int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
     switch (p->n_theta) {
-        case 128: return launch_ring<128>(p, m, Fpol, s);
-        case 256: return launch_ring<256>(p, m, Fpol, s);
-        case 512: return launch_ring<512>(p, m, Fpol, s);
-        case 1024: return launch_ring<1024>(p, m, Fpol, s);
+        case 128: return launch_ring<128>(p, m, Fpol, o, s);
+        case 256: return launch_ring<256>(p, m, Fpol, o, s);
+        case 512: return launch_ring<512>(p, m, Fpol, o, s);
+        case 1024: return launch_ring<1024>(p, m, Fpol, o, s);
         default: return FFB_ERR_UNSUPPORTED;
     }
 }

@@ -394,8 +394,8 @@ k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restric
          int64_t per, double *__restrict__ acc, int acc_cols, int nacc, int *status) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per chunk
-    constexpr int NCHT = 2;                     // chunks per tile
-    constexpr int TI = NCHT * KCH / 2;          // images per tile (2 K entries each)
+    constexpr int NCHT = (KIND == 0) ? 2 : 1;   // chunks per tile
+    constexpr int TI = NCHT * KCH / 2;          // images per tile (2 K entries each): 32
     constexpr uint32_t CH_BYTES = 128u * 128u;  // one chunk of 128 rows
     constexpr uint32_t BUF_BYTES = NP * NCHT * CH_BYTES;
     extern __shared__ uint8_t smraw[];
@@ -571,8 +571,7 @@ static size_t tc_cov_smem(int prec) {
 bool ffb_tc_cov_supported(ffb_plan_t p) {
     if (p->precision == FFB_FP32) return false;
     if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
-    const int ti = is_bf16(p->precision) ? 64 : 32;
-    if (ti * p->pmax > 128 * COV_PF) return false;    // one tile's values fit the register prefetch
+    if (32 * p->pmax > 128 * COV_PF) return false;    // one 32-image tile fits the register prefetch
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
