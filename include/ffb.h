@@ -182,6 +182,22 @@ int ffb_eig(ffb_plan_t plan, double *d_evals, double *d_evecs, void *stream);
 int ffb_eig_blocks(ffb_plan_t plan, const double *d_C, double *d_evals, double *d_evecs,
                    void *stream);
 
+/* ffb_radial_eigenfunctions -- Alg. 2 step 5 (Eq. sPCArad) in float64 from
+ * the eigenvectors of the last ffb_eig / ffb_eig_blocks / ffb_denoise:
+ * f^{k,l}(xi_j) = sum_q N_{k,q} J_k(R_{k,q} xi_j / c) u^(k)_l(q), written to
+ * d_f[offset[k] * n_xi + j * p_k + l] (n_xi * P values).  Asynchronous. */
+int ffb_radial_eigenfunctions(ffb_plan_t plan, double *d_f, void *stream);
+
+/* ffb_eigenimages -- the steerable principal components on the pixel grid
+ * (Sec. V, built from Eq. IFT_FB): g^{k,l}(r, phi) = sum_q u^(k)_l(q)
+ * F^{-1}(psi^{k,q})(r, phi), complex, for npairs pairs (h_k[i], h_l[i]) (host
+ * arrays), written as d_out[i][a1][a2][re, im] float64.  The phase factor is
+ * i^k (as derived from Eq. IPFT; the printed equation has i^{-k}).  For k > 0
+ * the real and imaginary parts are the two real eigenimages of the pair.
+ * Synchronises. */
+int ffb_eigenimages(ffb_plan_t plan, int npairs, const int *h_k, const int *h_l, double *d_out,
+                    void *stream);
+
 /* ffb_select -- Sec. V component selection from the eigenpairs of the last
  * ffb_eig/ffb_denoise call: gains h^(k)_l per ffb_denoise_mode (K pairs for
  * TOPK, noise variance sigma2 and image count n for MP_WIENER), stored in the

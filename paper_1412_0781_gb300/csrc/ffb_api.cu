@@ -127,6 +127,7 @@ extern "C" int ffb_eig(ffb_plan_t p, double *d_evals, double *d_evecs, void *str
     if (p->n_acc <= 0) return FFB_ERR_STATE;
     CK(ffb_launch_cov_final(p, s));
     CK(ffb_launch_eig(p, s));
+    p->eig_ready = 1;
     if (d_evals)
         CK(ffb_check_cuda(cudaMemcpyAsync(d_evals, p->d_evals, sizeof(double) * p->P, cudaMemcpyDeviceToDevice, s)));
     if (d_evecs)
@@ -139,6 +140,7 @@ extern "C" int ffb_eig_blocks(ffb_plan_t p, const double *d_C, double *d_evals, 
     cudaStream_t s = (cudaStream_t)stream;
     CK(ffb_check_cuda(cudaMemcpyAsync(p->d_Cfin, d_C, sizeof(double) * p->cov_total, cudaMemcpyDeviceToDevice, s)));
     CK(ffb_launch_eig(p, s));
+    p->eig_ready = 1;
     if (d_evals)
         CK(ffb_check_cuda(cudaMemcpyAsync(d_evals, p->d_evals, sizeof(double) * p->P, cudaMemcpyDeviceToDevice, s)));
     if (d_evecs)
@@ -239,6 +241,7 @@ extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int m
     CK(ffb_covariance(p, coef, n, 1, stream));
     CK(ffb_launch_cov_final(p, s));
     CK(ffb_launch_eig(p, s));
+    p->eig_ready = 1;
     CK(ffb_select(p, mode, K, sigma2, n, nullptr, stream));
     CK(ffb_launch_filter(p, coef, n, coef, FFB_FILTER_WEIGHT, s));
     CK(ffb_launch_adjoint(p, coef, n, d_out, s));

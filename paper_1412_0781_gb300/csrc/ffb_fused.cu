@@ -22,13 +22,32 @@
 //
 // Both halves compute the same row transforms (phase 1); the columns and the
 // nodes are split.
+//
+// Node order in phase 3.  Each node gathers a W x W window of S starting at
+// S[r0][c0]; one 8-byte load of a half warp is served in a single shared-
+// memory wavefront when the 16 window origins r0 * SLD + c0 fall in distinct
+// 8-byte bank slots (the origin mod 16) or coincide.  Lanes that take
+// consecutive angles of one ring do not: about half of the gather loads
+// replay.  The plan therefore regroups, within every block of FUS_GB
+// consecutive nodes, the nodes into half warps with distinct slots (built on
+// the host from the node geometry, ffb_fused_prepare), and the kernel stages
+// each block's results in shared memory to store them in natural order.
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "ffb_internal.cuh"
 
 #define FUS_WARPS 16
 #define FUS_NT (32 * FUS_WARPS)
 #define RFFT_RB 8
+#define FUS_GB 2048   // nodes per regrouped block (phase 3)
+
+// rows of the shared-memory grid block and its row pitch (complex entries)
+__host__ __device__ constexpr int fus_mh(int N, int W) { return N / 2 + 1 + 2 * ((W + 1) / 2); }
+__host__ __device__ constexpr int fus_sld(int N, int W) { return (fus_mh(N, W) > N / 2) ? fus_mh(N, W) : N / 2; }
 
 // ---------------------------------------------------------------------------
 // Stockham FFT of compile-time power-of-two length by one warp (radix 4,
@@ -139,12 +158,13 @@ template <int N, int W>
 __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
                    const float2 *__restrict__ tw, float beta, const float2 *__restrict__ rad,
-                   const float4 *__restrict__ ang, int n_xi, int n_theta, int nq0, float2 *__restrict__ Fpol,
-                   int *status) {
+                   const float4 *__restrict__ ang, int n_xi, int n_theta, int nq0,
+                   const unsigned short *__restrict__ gperm, int nblk, float2 *__restrict__ Fpol, int *status) {
     constexpr int L = N / 2;
     constexpr int H = (W + 1) / 2;
-    constexpr int MH = N / 2 + 1 + 2 * H;         // rows of S (m2 + h)
-    constexpr int SLD = (MH > L) ? MH : L;        // row length of S
+    constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
+    constexpr int SLD = fus_sld(N, W);            // row length of S
+    static_assert(2 * FUS_GB <= FUS_WARPS * 2 * N, "phase-3 staging must fit in the warp buffers");
     extern __shared__ float2 smz[];
     float2 *S = smz;                               // [MH][SLD]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -201,6 +221,9 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     __syncthreads();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
+    // node t = j * nl + (l - lbeg); block b holds t in [b FUS_GB, (b + 1) FUS_GB),
+    // visited in the plan's regrouped order and staged in the (now idle) warp
+    // buffers, two blocks deep so that one barrier per block suffices.
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
     const int nl = (half == 0) ? nq0 : nh - nq0;
@@ -208,43 +231,60 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     constexpr float halfw = 0.5f * W;
     constexpr float two_over_w = 2.0f / W;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
-    for (int t = threadIdx.x; t < npts; t += FUS_NT) {
-        const int j = t / nl;
-        const int l = lbeg + (t - j * nl);
-        const float2 r = __ldg(&rad[j]);
-        const float4 a = __ldg(&ang[l]);
-        const float p1 = r.x * a.x;
-        const float e1 = fmaf(r.x, a.x, -p1) + fmaf(r.x, a.y, r.y * a.x);
-        const float p2 = r.x * a.z;
-        const float e2 = fmaf(r.x, a.z, -p2) + fmaf(r.x, a.w, r.y * a.z);
-        const float m1f = ceilf(p1 - halfw), m2f = ceilf(p2 - halfw);
-        const float f1 = (p1 - m1f) + e1, f2 = (p2 - m2f) + e2;
-        const int c0 = (int)m1f - m1lo;     // column of the first tap in S
-        const int r0 = (int)m2f + H;        // row of the first tap in S
-        float2 acc = make_float2(0.f, 0.f);
-        if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) {
-            ffb_flag(status, FFB_ERR_ARG);
-        } else {
-            float wx[W];
+    float2 *stage0 = smz + MH * SLD;
+    for (int b = 0; b * FUS_GB < npts; ++b) {
+        const int t0 = b * FUS_GB;
+        const int cnt = min(FUS_GB, npts - t0);
+        float2 *stage = stage0 + (b & 1) * FUS_GB;
+        const unsigned short *pm = gperm + ((size_t)half * nblk + b) * FUS_GB;
+        for (int s = threadIdx.x; s < FUS_GB; s += FUS_NT) {
+            const int loc = pm[s];
+            if (loc >= cnt) continue;
+            const int t = t0 + loc;
+            const int j = t / nl;
+            const int l = lbeg + (t - j * nl);
+            const float2 r = __ldg(&rad[j]);
+            const float4 a = __ldg(&ang[l]);
+            const float p1 = r.x * a.x;
+            const float e1 = fmaf(r.x, a.x, -p1) + fmaf(r.x, a.y, r.y * a.x);
+            const float p2 = r.x * a.z;
+            const float e2 = fmaf(r.x, a.z, -p2) + fmaf(r.x, a.w, r.y * a.z);
+            const float m1f = ceilf(p1 - halfw), m2f = ceilf(p2 - halfw);
+            const float f1 = (p1 - m1f) + e1, f2 = (p2 - m2f) + e2;
+            const int c0 = (int)m1f - m1lo;     // column of the first tap in S
+            const int r0 = (int)m2f + H;        // row of the first tap in S
+            float2 acc = make_float2(0.f, 0.f);
+            if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) {
+                ffb_flag(status, FFB_ERR_ARG);
+            } else {
+                float wx[W];
 #pragma unroll
-            for (int q = 0; q < W; ++q) wx[q] = es_kernel(f1 - (float)q, two_over_w, beta);
-            const float2 *base = S + r0 * SLD + c0;
+                for (int q = 0; q < W; ++q) wx[q] = es_kernel(f1 - (float)q, two_over_w, beta);
+                const float2 *base = S + r0 * SLD + c0;
 #pragma unroll
-            for (int bq = 0; bq < W; ++bq) {
-                const float wy = es_kernel(f2 - (float)bq, two_over_w, beta);
-                const float2 *row = base + bq * SLD;
-                float sx = 0.f, sy = 0.f;
+                for (int bq = 0; bq < W; ++bq) {
+                    const float wy = es_kernel(f2 - (float)bq, two_over_w, beta);
+                    const float2 *row = base + bq * SLD;
+                    float sx = 0.f, sy = 0.f;
 #pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    const float2 g = row[q];
-                    sx = fmaf(wx[q], g.x, sx);
-                    sy = fmaf(wx[q], g.y, sy);
+                    for (int q = 0; q < W; ++q) {
+                        const float2 g = row[q];
+                        sx = fmaf(wx[q], g.x, sx);
+                        sy = fmaf(wx[q], g.y, sy);
+                    }
+                    acc.x = fmaf(wy, sx, acc.x);
+                    acc.y = fmaf(wy, sy, acc.y);
                 }
-                acc.x = fmaf(wy, sx, acc.x);
-                acc.y = fmaf(wy, sy, acc.y);
             }
+            stage[loc] = acc;
         }
-        Fout[(size_t)j * nh + l] = acc;
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += FUS_NT) {
+            const int t = t0 + i;
+            const int j = t / nl;
+            const int l = lbeg + (t - j * nl);
+            Fout[(size_t)j * nh + l] = stage[i];
+        }
     }
 }
 
@@ -303,8 +343,7 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
 // ---------------------------------------------------------------------------
 template <int N, int W>
 static size_t fused_smem() {
-    constexpr int L = N / 2, H = (W + 1) / 2, MH = N / 2 + 1 + 2 * H, SLD = (MH > L) ? MH : L;
-    return sizeof(float2) * ((size_t)MH * SLD + (size_t)FUS_WARPS * 2 * N);
+    return sizeof(float2) * ((size_t)fus_mh(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * 2 * N);
 }
 
 template <int N, int W>
@@ -321,7 +360,8 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
     k_grid_interp_half<N, W><<<g, FUS_NT, smem, s>>>(d_images + (size_t)i0 * p->L * p->L, p->off, p->d_corr,
                                                      p->d_twN, (float)p->beta, p->d_rad, p->d_ang, p->n_xi,
-                                                     p->n_theta, p->nq0, Fpol, p->d_status);
+                                                     p->n_theta, p->nq0, p->d_gperm, p->gperm_nblk, Fpol,
+                                                     p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -336,6 +376,68 @@ bool ffb_fused_supported(ffb_plan_t p) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return smem <= (size_t)optin;
+}
+
+// Regrouped node order of phase 3 (see the file header): for each half and
+// block of FUS_GB nodes, block-local node indices in lane order; entries past
+// the block's node count hold 0xFFFF.  Greedy per half warp: one node from
+// every nonempty bank slot, fullest slot first, then fill from the fullest.
+int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
+    const int N = p->N, W = p->w, H = (W + 1) / 2, SLD = fus_sld(N, W);
+    const int nh = p->n_theta / 2;
+    const int nblk = (p->n_xi * p->nq0 + FUS_GB - 1) / FUS_GB;   // half 0 has the most nodes
+    std::vector<double> xi(p->n_xi);
+    int e = ffb_check_cuda(cudaMemcpyAsync(xi.data(), p->d_xi, sizeof(double) * p->n_xi, cudaMemcpyDeviceToHost, s));
+    if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
+    if (e) return e;
+    std::vector<unsigned short> perm((size_t)2 * nblk * FUS_GB, 0xFFFF);
+    for (int half = 0; half < 2; ++half) {
+        const int lbeg = (half == 0) ? 0 : p->nq0;
+        const int nl = (half == 0) ? p->nq0 : nh - p->nq0;
+        const int npts = p->n_xi * nl;
+        const int m1lo = (half == 0) ? -H : -(N / 2) - H;
+        for (int b = 0; b * FUS_GB < npts; ++b) {
+            const int t0 = b * FUS_GB, cnt = std::min(FUS_GB, npts - t0);
+            std::vector<int> bucket[16];
+            for (int i = cnt - 1; i >= 0; --i) {
+                const int t = t0 + i, j = t / nl, l = lbeg + t % nl;
+                const double th = 2.0 * M_PI * (double)l / (double)p->n_theta;
+                const double p1 = N * xi[j] * cos(th), p2 = N * xi[j] * sin(th);
+                const long c0 = (long)ceil(p1 - 0.5 * W) - m1lo, r0 = (long)ceil(p2 - 0.5 * W) + H;
+                bucket[(r0 * SLD + c0) & 15].push_back(i);
+            }
+            unsigned short *out = perm.data() + ((size_t)half * nblk + b) * FUS_GB;
+            int pos = 0;
+            while (pos < cnt) {
+                int order[16];
+                for (int r = 0; r < 16; ++r) order[r] = r;
+                std::stable_sort(order, order + 16, [&](int x, int y) { return bucket[x].size() > bucket[y].size(); });
+                int taken = 0;
+                for (int r : order) {
+                    if (bucket[r].empty()) continue;
+                    out[pos++] = (unsigned short)bucket[r].back();
+                    bucket[r].pop_back();
+                    ++taken;
+                }
+                while (taken < 16 && pos < cnt) {
+                    int rb = 0;
+                    for (int r = 1; r < 16; ++r)
+                        if (bucket[r].size() > bucket[rb].size()) rb = r;
+                    out[pos++] = (unsigned short)bucket[rb].back();
+                    bucket[rb].pop_back();
+                    ++taken;
+                }
+            }
+        }
+    }
+    if (p->d_gperm) cudaFree(p->d_gperm);
+    p->d_gperm = nullptr;
+    e = ffb_check_cuda(cudaMalloc((void **)&p->d_gperm, sizeof(unsigned short) * perm.size()));
+    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_gperm, perm.data(), sizeof(unsigned short) * perm.size(),
+                                               cudaMemcpyHostToDevice, s));
+    if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
+    p->gperm_nblk = nblk;
+    return e;
 }
 
 int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {

@@ -69,6 +69,8 @@ struct ffb_plan_s {
     float2 *d_G = nullptr;       // [chunk][Mh][N]
     float *d_Fhat = nullptr;     // [k_max+1][chunk][2][n_xi]
     float2 *d_Fpol = nullptr;    // [chunk][n_xi][n_theta/2] (fused path)
+    unsigned short *d_gperm = nullptr;  // [2][gperm_nblk][2048] phase-3 node order (fused path)
+    int gperm_nblk = 0;
     // covariance state
     double *d_acc = nullptr;     // [cov_total] sum Re(a a^*), k = 0 shifted
     double *d_sum0 = nullptr;    // [p0] sum (a0 - shift)
@@ -87,6 +89,7 @@ struct ffb_plan_s {
     double *d_gain = nullptr;      // [P]
     float *d_M = nullptr;          // [cov_total] U diag(h) U^T per block
     int selected = 0;              // filter matrices valid
+    int eig_ready = 0;             // d_evals / d_evecs hold eigenpairs
     // status word written by kernels (first nonzero error wins)
     int *d_status = nullptr;
     int64_t launches = 0;
@@ -259,11 +262,42 @@ __device__ __forceinline__ float es_kernel(float x, float two_over_w, float beta
     return (u > 0.0f) ? __expf(beta * (sqrtf(u) - 1.0f)) : 0.0f;
 }
 
+// J_k(x), x >= 0, by Miller's backward recurrence: starting far above both k
+// and x with (t_{M+1}, t_M) = (0, tiny), t_{m-1} = (2m/x) t_m - t_{m+1} is
+// proportional to J_{m-1}(x) (the minimal solution); the constant follows from
+// J_0 + 2 sum_{m>=1} J_{2m} = 1.  Values are rescaled when they grow large.
+__device__ __forceinline__ double bessel_j_miller(int k, double x) {
+    if (x <= 0.0) return (k == 0) ? 1.0 : 0.0;
+    double top = fmax((double)k, x);
+    int M = (int)(top + 16.0 * cbrt(0.5 * top) + 24.0);
+    M += (M & 1);  // even start
+    double tp1 = 0.0, t = 1e-300, sum = 0.0, jk = 0.0;
+    for (int m = M; m >= 1; --m) {
+        // here t = t_m, tp1 = t_{m+1}
+        if (m == k) jk = t;
+        if ((m & 1) == 0) sum += 2.0 * t;
+        double tm1 = (2.0 * m / x) * t - tp1;
+        tp1 = t;
+        t = tm1;
+        if (fabs(t) > 1e250) {
+            t *= 1e-250;
+            tp1 *= 1e-250;
+            sum *= 1e-250;
+            jk *= 1e-250;
+        }
+    }
+    // t = t_0
+    if (k == 0) jk = t;
+    sum += t;
+    return jk / sum;
+}
+
 // Host helpers (implemented in ffb_plan.cu).
 int ffb_check_cuda(cudaError_t e);
 int ffb_ensure_scratch(ffb_plan_t plan);
 int ffb_ensure_scratch_grid(ffb_plan_t plan);
 bool ffb_fused_supported(ffb_plan_t plan);
+int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
                            cudaStream_t s);
 struct RingOut {

@@ -14,36 +14,6 @@
 // float64 special functions (device)
 // ---------------------------------------------------------------------------
 
-// J_k(x), x >= 0, by Miller's backward recurrence: starting far above both k
-// and x with (t_{M+1}, t_M) = (0, tiny), t_{m-1} = (2m/x) t_m - t_{m+1} is
-// proportional to J_{m-1}(x) (the minimal solution); the constant follows from
-// J_0 + 2 sum_{m>=1} J_{2m} = 1.  Values are rescaled when they grow large.
-__device__ double bessel_j_miller(int k, double x) {
-    if (x <= 0.0) return (k == 0) ? 1.0 : 0.0;
-    double top = fmax((double)k, x);
-    int M = (int)(top + 16.0 * cbrt(0.5 * top) + 24.0);
-    M += (M & 1);  // even start
-    double tp1 = 0.0, t = 1e-300, sum = 0.0, jk = 0.0;
-    for (int m = M; m >= 1; --m) {
-        // here t = t_m, tp1 = t_{m+1}
-        if (m == k) jk = t;
-        if ((m & 1) == 0) sum += 2.0 * t;
-        double tm1 = (2.0 * m / x) * t - tp1;
-        tp1 = t;
-        t = tm1;
-        if (fabs(t) > 1e250) {
-            t *= 1e-250;
-            tp1 *= 1e-250;
-            sum *= 1e-250;
-            jk *= 1e-250;
-        }
-    }
-    // t = t_0
-    if (k == 0) jk = t;
-    sum += t;
-    return jk / sum;
-}
-
 // Bessel zeros: one block per order k scans [lo, X + 2 step] on a grid of
 // spacing `step` (< the 2.4 minimum gap between positive zeros), brackets
 // sign changes, ranks the brackets and refines each by bisection.  Writes
@@ -212,7 +182,7 @@ static void free_plan(ffb_plan_t p) {
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
                     p->d_cov_work, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
-                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol};
+                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_gperm};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (ProfEv &e : p->prof) {
@@ -445,6 +415,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     if (st == FFB_OK && ffb_fused_supported(p)) {
         p->fused = 1;
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
+        st = ffb_fused_prepare(p, s);
     }
     if (st != FFB_OK) {
         cudaStreamSynchronize(s);

@@ -42,6 +42,8 @@ SIGNATURES = {
     "ffb_cov_import": (_i, [_vp, _pd, _vp]),
     "ffb_eig": (_i, [_vp, _vp, _vp, _vp]),
     "ffb_eig_blocks": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ffb_radial_eigenfunctions": (_i, [_vp, _vp, _vp]),
+    "ffb_eigenimages": (_i, [_vp, _i, _pi, _pi, _vp, _vp]),
     "ffb_select": (_i, [_vp, _i, _i, _d, _i64, _pd, _vp]),
     "ffb_filter": (_i, [_vp, _vp, _i64, _vp, _i, _vp]),
     "ffb_weight": (_i, [_vp, _vp, _i64, _vp, _vp]),
@@ -254,6 +256,26 @@ class Plan:
         _check(load().ffb_eig_blocks(self._h, _ptr(C, torch.float64, "C"), _ptr(ev, torch.float64, "evals"),
                                      _ptr(U, torch.float64, "evecs"), _stream(stream)), "ffb_eig_blocks")
         return ev, U
+
+    def radial_eigenfunctions(self, stream=None):
+        """float64 (n_xi * P,) packed: block k at offset[k]*n_xi as (n_xi, p_k)."""
+        out = torch.empty(self.n_xi * self.P, device="cuda", dtype=torch.float64)
+        _check(load().ffb_radial_eigenfunctions(self._h, _ptr(out, torch.float64, "out"), _stream(stream)),
+               "ffb_radial_eigenfunctions")
+        return out
+
+    def radial_block(self, packed, k):
+        o, pk = self.offset[k], self.p[k]
+        return packed[o * self.n_xi:(o + pk) * self.n_xi].view(self.n_xi, pk)
+
+    def eigenimages(self, pairs, stream=None):
+        """Complex128 (len(pairs), L, L) eigenimages of the (k, l) pairs."""
+        ks = (ctypes.c_int * len(pairs))(*[int(k) for k, _ in pairs])
+        ls = (ctypes.c_int * len(pairs))(*[int(l) for _, l in pairs])
+        out = torch.empty((len(pairs), self.L, self.L, 2), device="cuda", dtype=torch.float64)
+        _check(load().ffb_eigenimages(self._h, len(pairs), ks, ls, _ptr(out, torch.float64, "out"),
+                                      _stream(stream)), "ffb_eigenimages")
+        return torch.view_as_complex(out)
 
     def select(self, mode="topk", K=0, sigma2=0.0, n=0, stream=None):
         """Synchronising: gains h (numpy, P) of the selected components; stores
