@@ -40,8 +40,8 @@
 
 #include "ffb_internal.cuh"
 
-#define FUS_WARPS 16
-#define FUS_NT (32 * FUS_WARPS)
+#define FUS_WARPS 16                 // warps with FFT buffers (phases 1-2)
+#define FUS_NT 1024                  // threads per CTA; all of them interpolate (phase 3)
 #define RFFT_RB 8
 #define FUS_GB 2048   // nodes per regrouped block (phase 3)
 
@@ -168,7 +168,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     extern __shared__ float2 smz[];
     float2 *S = smz;                               // [MH][SLD]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *bufA = smz + MH * SLD + warp * 2 * N;
+    float2 *bufA = smz + MH * SLD + (warp < FUS_WARPS ? warp : 0) * 2 * N;   // FFT warps only
     float2 *bufB = bufA + N;
     const int half = blockIdx.x;
     const int img = blockIdx.y;
@@ -176,7 +176,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 
     // ---- phase 1: row transforms (two pixel rows per complex FFT) --------
     bool bad = false;
-    for (int rp = warp; rp < L / 2; rp += FUS_WARPS) {
+    for (int rp = warp; warp < FUS_WARPS && rp < L / 2; rp += FUS_WARPS) {
         const int a1 = 2 * rp;
         float x[L / 32], y[L / 32];
 #pragma unroll
@@ -209,7 +209,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 
     // ---- phase 2: column transforms, in place per row of S ---------------
     const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-    for (int e = warp; e < MH; e += FUS_WARPS) {
+    for (int e = warp; warp < FUS_WARPS && e < MH; e += FUS_WARPS) {
         float2 *row = S + e * SLD;
         float2 z[L / 32];
 #pragma unroll
