@@ -254,8 +254,67 @@ int ffb_profile(ffb_plan_t plan, int enable);
 int ffb_profile_read(ffb_plan_t plan, double *h_ms, int64_t *h_calls);
 
 /* Number of kernel launches issued by this plan since creation (for
- * accounting of GPU work). */
+ * accounting of GPU work).  Launches replayed from a group's CUDA graph are
+ * counted on the plan whose stack they belong to. */
 int64_t ffb_launch_count(ffb_plan_t plan);
+
+/* ---- batching: many stacks of uneven L and n ----------------------------
+ * Sec. IV notes that the expansion and the covariance are sums over images
+ * that may be split among workers.  A group runs S independent stacks
+ * (1 <= S <= 64), each with its own plan, through a1-a7 in one call:
+ *   - each stack's expansion (a1-a5) runs on its own branch stream;
+ *   - the covariance of all stacks (a6/a7) is ONE persistent launch over the
+ *     (stack, k block, image range) items of every stack: a grouped SYRK over
+ *     the uneven per-k block sizes p_k (tensor cores in the plans' precision,
+ *     or float32 tiles for FFB_FP32), plus one launch of the k = 0 sums;
+ *   - the first call with a given set of pointers, sizes and reset flags runs
+ *     eagerly; once per group it also times the candidate item shapes of the
+ *     grouped launch (images per item, images per tensor-core tile, grid) on
+ *     that call's coefficients, accumulating into scratch, and keeps the
+ *     fastest (ffb_group_tuning lists them); the second call with the same
+ *     arguments captures the launches into a CUDA graph; later ones replay it.
+ * Results are those of ffb_expand + ffb_covariance on each plan: the same
+ * coefficients bit for bit; the covariance accumulated in another order.
+ * The plans stay owned by the caller and must outlive the group; they must
+ * be distinct, share one precision (ffb_set_precision on a member afterwards
+ * makes the group's calls return FFB_ERR_STATE), and with a tensor-core
+ * precision every p_k must be <= 128 (FFB_ERR_UNSUPPORTED otherwise).  While
+ * a group call is in flight its plans must not be used on other streams. */
+typedef struct ffb_group_s *ffb_group_t;
+
+/* ffb_group_create -- allocates each plan's scratch, the branch streams and
+ * the tuner's scratch accumulator; synchronises `stream`. */
+int ffb_group_create(ffb_group_t *out, int S, const ffb_plan_t *plans, void *stream);
+int ffb_group_destroy(ffb_group_t group);
+
+/* ffb_group_expand_cov -- for every stack s with h_n[s] > 0: expand the
+ * images h_images[s] (device [h_n[s]][L_s][L_s]) into h_coef[s] (device
+ * [h_n[s]][P_s][2]) and add them to the stack's covariance (restarted first
+ * when reset != 0).  h_images, h_n, h_coef are host arrays of S entries; a
+ * stack with h_n[s] == 0 is skipped (its pointers may be NULL).  Asynchronous
+ * on `stream`; device errors are returned by ffb_group_sync or by the plans'
+ * synchronising calls (ffb_cov_get, ffb_eig). */
+int ffb_group_expand_cov(ffb_group_t group, const float *const *h_images, const int64_t *h_n,
+                         float *const *h_coef, int reset, void *stream);
+
+/* ffb_group_covariance -- a6/a7 only, for coefficients already computed
+ * (h_coef[s]: device [h_n[s]][P_s][2]), as one grouped launch. */
+int ffb_group_covariance(ffb_group_t group, const float *const *h_coef, const int64_t *h_n, int reset,
+                         void *stream);
+
+/* ffb_group_sync -- synchronises `stream` and returns the first device error
+ * of the grouped launches or of any member plan. */
+int ffb_group_sync(ffb_group_t group, void *stream);
+
+/* ffb_group_info -- h_info[10]: S, precision, tuned images per item, tuned
+ * images per tensor-core tile, tuned grid (CTAs), graphs instantiated, graph
+ * replays, eager calls, kernel launches of the last call, tuning candidates. */
+int ffb_group_info(ffb_group_t group, int64_t *h_info);
+
+/* ffb_group_tuning -- the timed candidates (up to max): images per item,
+ * images per tile, grid, milliseconds of one grouped launch.  Returns the
+ * number written (a negative ffb_status on error). */
+int ffb_group_tuning(ffb_group_t group, int max, int *h_per, int *h_tile, int *h_grid, float *h_ms);
 
 const char *ffb_strerror(int status);
 

@@ -69,10 +69,9 @@ extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *
     return FFB_OK;
 }
 
-extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef, void *stream) {
-    if (!p || n < 0 || (n > 0 && (!d_images || !d_coef))) return FFB_ERR_ARG;
+// a1-a5 launches for n images on stream s (arguments already validated)
+int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef, cudaStream_t s) {
     if (n == 0) return FFB_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     CK(ffb_ensure_scratch(p));
     RingOut ring{FFB_FMT_F32, p->d_Fhat, nullptr, p->n_xi};
     if (p->precision != FFB_FP32) CK(ffb_tc_prepare(p, s, &ring));
@@ -88,6 +87,11 @@ extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float 
         CK(ffb_launch_bessel(p, m, d_coef + (size_t)i0 * p->P * 2, p->fused != 0, s));
     }
     return FFB_OK;
+}
+
+extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef, void *stream) {
+    if (!p || n < 0 || (n > 0 && (!d_images || !d_coef))) return FFB_ERR_ARG;
+    return ffb_expand_on(p, d_images, n, d_coef, (cudaStream_t)stream);
 }
 
 extern "C" int ffb_covariance(ffb_plan_t p, const float *d_coef, int64_t n, int reset, void *stream) {

@@ -89,100 +89,144 @@ int ffb_launch_bessel(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_r
 }
 
 // ---------------------------------------------------------------------------
-// a6/a7: covariance accumulation.  Work item (k, q0, q1) is the 64 x 64 tile
-// of block k at rows q0.., columns q1..; blockIdx.y splits the images.  Each
-// thread owns a 4 x 4 sub-tile, sums 128 images in float32 and folds the
-// partial sums into float64 registers; the CTA result is added to the
-// float64 accumulator with atomics (both the tile and, off the diagonal, its
-// transpose).  For k = 0 the values are shifted by `shift` (a pilot mean):
-// sum (a - s)(a - s)^T, finalised as C = acc/n - d d^T with d = sum(a - s)/n.
+// a6/a7: covariance accumulation in float32 tiles.  A persistent CTA walks the
+// items of a stack table (CovGroup): item = (stack, tile (k, q0, q1) of the
+// stack's tile list, image range).  The tile is the 64 x 64 block of C^(k) at
+// rows q0.., columns q1..; each thread owns a 4 x 4 sub-tile, sums 128 images
+// in float32 and folds the partial sums into float64 registers; the result is
+// added to the float64 accumulator with atomics (both the tile and, off the
+// diagonal, its transpose).  For k = 0 the values are shifted by `shift` (a
+// pilot mean): sum (a - s)(a - s)^T, finalised as C = acc/n - d d^T with
+// d = sum(a - s)/n; the diagonal tiles of block 0 also accumulate sum(a - s).
 // ---------------------------------------------------------------------------
 #define COV_TI 32
 __global__ void __launch_bounds__(256)
-k_cov_fp32(const float2 *__restrict__ coef, int64_t n, int P, const int *__restrict__ pk_,
-           const int *__restrict__ off_, const int *__restrict__ cov_off, const int4 *__restrict__ work,
-           const float *__restrict__ shift, int64_t per, double *__restrict__ acc, double *__restrict__ sum0) {
+k_cov_fp32(const __grid_constant__ CovGroup g) {
     __shared__ float2 Xa[COV_TI][64];
     __shared__ float2 Xb[COV_TI][64];
-    const int4 wk = work[blockIdx.x];
-    const int k = wk.x, q0 = wk.y, q1 = wk.z;
-    const int pk = pk_[k], o = off_[k];
-    const int64_t ib = (int64_t)blockIdx.y * per;
-    const int64_t ie = min(n, ib + per);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const bool do_sum = (k == 0 && q0 == q1);  // diagonal tiles of block 0 carry the mean
-    float accf[4][4];
-    double accd[4][4];
+    for (int64_t item = blockIdx.x; item < g.nitems; item += gridDim.x) {
+        const CovStack &S = g.st[cov_stack_of(g, item)];
+        const int64_t local = item - S.item0;
+        const int4 wk = S.work[local % S.nk];
+        const int k = wk.x, q0 = wk.y, q1 = wk.z;
+        const int pk = S.pk[k], o = S.off[k];
+        const int64_t ib = (local / S.nk) * (int64_t)S.per;
+        const int64_t ie = min(S.n, ib + (int64_t)S.per);
+        const float2 *coef = S.coef;
+        const int P = S.P;
+        const float *shift = S.shift;
+        const bool do_sum = (k == 0 && q0 == q1);  // diagonal tiles of block 0 carry the mean
+        float accf[4][4];
+        double accd[4][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            accf[r][c] = 0.f;
-            accd[r][c] = 0.0;
-        }
-    float sf = 0.f;
-    double sd = 0.0;
-    int tiles = 0;
-    for (int64_t i = ib; i < ie; i += COV_TI) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < COV_TI * 64; t += 256) {
-            int ii = t >> 6, qq = t & 63;
-            int64_t img = i + ii;
-            float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-            if (img < ie) {
-                if (q0 + qq < pk) va = __ldg(&coef[img * P + o + q0 + qq]);
-                if (q1 + qq < pk) vb = __ldg(&coef[img * P + o + q1 + qq]);
-                if (k == 0) {
-                    va = make_float2(q0 + qq < pk ? va.x - shift[q0 + qq] : 0.f, 0.f);
-                    vb = make_float2(q1 + qq < pk ? vb.x - shift[q1 + qq] : 0.f, 0.f);
-                }
+            for (int c = 0; c < 4; ++c) {
+                accf[r][c] = 0.f;
+                accd[r][c] = 0.0;
             }
-            Xa[ii][qq] = va;
-            Xb[ii][qq] = vb;
-        }
-        __syncthreads();
+        float sf = 0.f;
+        double sd = 0.0;
+        int tiles = 0;
+        for (int64_t i = ib; i < ie; i += COV_TI) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < COV_TI * 64; t += 256) {
+                int ii = t >> 6, qq = t & 63;
+                int64_t img = i + ii;
+                float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+                if (img < ie) {
+                    if (q0 + qq < pk) va = __ldg(&coef[img * P + o + q0 + qq]);
+                    if (q1 + qq < pk) vb = __ldg(&coef[img * P + o + q1 + qq]);
+                    if (k == 0) {
+                        va = make_float2(q0 + qq < pk ? va.x - shift[q0 + qq] : 0.f, 0.f);
+                        vb = make_float2(q1 + qq < pk ? vb.x - shift[q1 + qq] : 0.f, 0.f);
+                    }
+                }
+                Xa[ii][qq] = va;
+                Xb[ii][qq] = vb;
+            }
+            __syncthreads();
 #pragma unroll 4
-        for (int ii = 0; ii < COV_TI; ++ii) {
-            float2 a[4], b[4];
+            for (int ii = 0; ii < COV_TI; ++ii) {
+                float2 a[4], b[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = Xa[ii][ty * 4 + r];
+                for (int r = 0; r < 4; ++r) a[r] = Xa[ii][ty * 4 + r];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Xb[ii][tx * 4 + c];
+                for (int c = 0; c < 4; ++c) b[c] = Xb[ii][tx * 4 + c];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
-        }
-        if (do_sum && threadIdx.x < 64) {
-            for (int ii = 0; ii < COV_TI; ++ii) sf += Xa[ii][threadIdx.x].x;
-        }
-        if (++tiles == 4) {
-            tiles = 0;
+                    for (int c = 0; c < 4; ++c) accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
+            }
+            if (do_sum && threadIdx.x < 64) {
+                for (int ii = 0; ii < COV_TI; ++ii) sf += Xa[ii][threadIdx.x].x;
+            }
+            if (++tiles == 4) {
+                tiles = 0;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    accd[r][c] += (double)accf[r][c];
-                    accf[r][c] = 0.f;
-                }
-            sd += (double)sf;
-            sf = 0.f;
-        }
-    }
-    double *blk = acc + cov_off[k];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int qa = q0 + ty * 4 + r, qb = q1 + tx * 4 + c;
-            if (qa < pk && qb < pk) {
-                double v = accd[r][c] + (double)accf[r][c];
-                atomicAdd(&blk[(size_t)qa * pk + qb], v);
-                if (q0 != q1) atomicAdd(&blk[(size_t)qb * pk + qa], v);
+                    for (int c = 0; c < 4; ++c) {
+                        accd[r][c] += (double)accf[r][c];
+                        accf[r][c] = 0.f;
+                    }
+                sd += (double)sf;
+                sf = 0.f;
             }
         }
-    if (do_sum && threadIdx.x < 64 && q0 + (int)threadIdx.x < pk)
-        atomicAdd(&sum0[q0 + threadIdx.x], sd + (double)sf);
+        double *blk = S.acc + S.cov_off[k];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int qa = q0 + ty * 4 + r, qb = q1 + tx * 4 + c;
+                if (qa < pk && qb < pk) {
+                    double v = accd[r][c] + (double)accf[r][c];
+                    atomicAdd(&blk[(size_t)qa * pk + qb], v);
+                    if (q0 != q1) atomicAdd(&blk[(size_t)qb * pk + qa], v);
+                }
+            }
+        if (do_sum && threadIdx.x < 64 && q0 + (int)threadIdx.x < pk)
+            atomicAdd(&S.sum0[q0 + threadIdx.x], sd + (double)sf);
+    }
+}
+
+void ffb_cov_stack(ffb_plan_t p, const float *d_coef, int64_t n, bool tc, CovStack *st) {
+    st->coef = (const float2 *)d_coef;
+    st->n = n;
+    st->item0 = 0;
+    st->pk = p->d_p;
+    st->off = p->d_off;
+    st->cov_off = p->d_cov_off;
+    st->work = p->d_cov_work;
+    st->shift = p->d_shift;
+    st->acc = p->d_acc;
+    st->sum0 = p->d_sum0;
+    st->P = p->P;
+    st->nk = tc ? p->k_max + 1 : p->n_cov_work;
+    st->per = tc ? 1024 : 2048;
+    st->pmax = p->pmax;
+}
+
+int ffb_cov_grid_default(int precision) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (precision != FFB_FP32) return sms;   // one CTA per SM: it holds all 512 TMEM columns
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cov_fp32, 256, 0);
+    return sms * (occ > 0 ? occ : 1);
+}
+
+int ffb_launch_cov_group(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s) {
+    if (g.S < 1 || g.S > FFB_GROUP_MAX) return FFB_ERR_ARG;
+    if (g.nitems <= 0) return FFB_OK;
+    if (precision != FFB_FP32) return ffb_launch_cov_group_tc(precision, g, grid, status, s);
+    if (grid <= 0) grid = ffb_cov_grid_default(precision);
+    if ((int64_t)grid > g.nitems) grid = (int)g.nitems;
+    k_cov_fp32<<<grid, 256, 0, s>>>(g);
+    return ffb_check_cuda(cudaGetLastError());
 }
 
 // pilot shift for the k = 0 block: mean of a_0 over the first min(n, 4096)
@@ -224,15 +268,15 @@ int ffb_launch_cov_shift(ffb_plan_t p, const float *d_coef, int64_t n, cudaStrea
 
 int ffb_launch_cov(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
     if (ffb_tc_cov_supported(p)) return ffb_launch_cov_tc(p, d_coef, n, s);
-    const int64_t per = 2048;
-    int64_t ns = (n + per - 1) / per;
-    if (ns > 65535) return FFB_ERR_ARG;
-    dim3 g(p->n_cov_work, (unsigned)ns);
+    CovGroup g;          // copied into the launch's parameters
+    g.S = 1;
+    g.tile_imgs = 32;
+    ffb_cov_stack(p, d_coef, n, false, &g.st[0]);
+    g.nitems = (int64_t)g.st[0].nk * ((n + g.st[0].per - 1) / g.st[0].per);
     ProfScope ps(p, FFB_KC_COV, s);
-    k_cov_fp32<<<g, 256, 0, s>>>((const float2 *)d_coef, n, p->P, p->d_p, p->d_off, p->d_cov_off, p->d_cov_work,
-                                 p->d_shift, per, p->d_acc, p->d_sum0);
+    const int e = ffb_launch_cov_group(FFB_FP32, g, 0, p->d_status, s);
     p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
+    return e;
 }
 
 int ffb_launch_cov_final(ffb_plan_t p, cudaStream_t s) {

@@ -322,6 +322,47 @@ int ffb_launch_cov(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t
 int ffb_launch_cov_shift(ffb_plan_t plan, const float *d_coef, int64_t n, cudaStream_t s);
 int ffb_launch_cov_final(ffb_plan_t plan, cudaStream_t s);
 int ffb_launch_eig(ffb_plan_t plan, cudaStream_t s);
+
+// ---- covariance over one or several stacks in one launch (a6/a7) ----------
+// A launch covers the stacks st[0..S); stack s contributes items
+// [item0, item0 + nk * ceil(n / per)): item i of the stack is image range
+// i / nk (per images) of block or tile i % nk.  The table travels as a kernel
+// parameter (about 6 KB for 64 stacks), so a captured graph keeps its own copy.
+#define FFB_GROUP_MAX 64
+struct CovStack {
+    const float2 *coef;     // [n][P] coefficients of the stack
+    int64_t n;              // images
+    int64_t item0;          // first item of the stack in the launch
+    const int *pk, *off, *cov_off;
+    const int4 *work;       // FP32 kernel: (k, q0, q1) tiles
+    const float *shift;     // k = 0 pilot mean
+    double *acc, *sum0;     // float64 accumulators
+    int P;
+    int nk;                 // items per image range: k blocks (tensor cores) or tiles (FP32)
+    int per;                // images per item
+    int pmax;
+};
+struct CovGroup {
+    int S;
+    int tile_imgs;          // tensor cores: images per MMA tile, 16 or 32
+    int64_t nitems;
+    CovStack st[FFB_GROUP_MAX];
+};
+__device__ __forceinline__ int cov_stack_of(const CovGroup &g, int64_t item) {
+    int s = 0;
+    while (s + 1 < g.S && g.st[s + 1].item0 <= item) ++s;
+    return s;
+}
+// fills st for plan p (item0 and per are set by the caller); tc selects the
+// item kind: k blocks (tensor cores) or the plan's FP32 tile list
+void ffb_cov_stack(ffb_plan_t p, const float *d_coef, int64_t n, bool tc, CovStack *st);
+// covariance launches over a stack table; precision selects the kernel
+// (FFB_FP32: float32 tiles; otherwise the tensor-core form); grid <= 0 picks
+// one CTA per SM (tensor cores) or a full wave (FP32)
+int ffb_launch_cov_group(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s);
+int ffb_cov_grid_default(int precision);
+int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s);
+int ffb_expand_on(ffb_plan_t plan, const float *d_images, int64_t n, float *d_coef, cudaStream_t s);
 int ffb_launch_adjoint(ffb_plan_t plan, const float *d_coef, int64_t n, float *d_images,
                        cudaStream_t s);
 int ffb_launch_filter_matrix(ffb_plan_t plan, cudaStream_t s);

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(128, 1)
 k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
             const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int ld,
             int nimg, const int *__restrict__ pk_, const int *__restrict__ off_, int P, float *__restrict__ coef,
-            int BNmax, int tmem_cols, int *status) {
+            int BNmax, int tmem_cols, int nst, int *status) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     constexpr int ES = (KIND == 0) ? 4 : 2;
@@ -89,12 +89,12 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     const int NCH = ld / KCH;
     const uint32_t a_bytes = 128u * 128u;       // one plane, one K chunk, 128 rows
     const uint32_t b_bytes = (uint32_t)BNmax * 128u;
-    uint8_t *As = sm;
-    uint8_t *Bs = sm + (size_t)NPA * NCH * a_bytes;
-    const size_t tiles = (size_t)NPA * NCH * a_bytes + (size_t)NPB * NCH * b_bytes;
-    const size_t stage_bytes = (size_t)64 * (2 * BNmax + 2) * 4;      // epilogue reuse of the tiles
-    uint64_t *bars = (uint64_t *)(sm + (tiles > stage_bytes ? tiles : stage_bytes));  // [0] loads, [1] mma done
-    uint32_t *slot = (uint32_t *)(bars + 2);
+    const uint32_t st_bytes = NPA * a_bytes + NPB * b_bytes;   // one stage: every plane of one K chunk
+    const size_t ring = (size_t)nst * st_bytes;
+    const size_t stage_bytes = (size_t)64 * (2 * BNmax + 2) * 4;      // epilogue reuse of the ring
+    uint64_t *bars = (uint64_t *)(sm + (ring > stage_bytes ? ring : stage_bytes));
+    uint64_t *full = bars, *empty = bars + nst, *done = bars + 2 * nst;
+    uint32_t *slot = (uint32_t *)(done + 1);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x, k = blockIdx.y;
@@ -102,8 +102,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     const int BN = max(16, (pk + 15) & ~15);
 
     if (threadIdx.x == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
+        for (int i = 0; i < 2 * nst + 1; ++i) tc::mbar_init(&bars[i], 1);
         tc::fence_mbar_init();
         *okflag = 1;
     }
@@ -117,53 +116,80 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     const uint32_t tbase = *slot;
 
     if (threadIdx.x == 0) {
-        tc::mbar_arrive_expect_tx(&bars[0], NPA * NCH * a_bytes + NPB * NCH * b_bytes);
-        for (int ch = 0; ch < NCH; ++ch) {
-            tc::tma_load_3d(As + (size_t)(0 * NCH + ch) * a_bytes, &mapA0, &bars[0], ch * KCH, 128 * m, k);
-            if (NPA > 1) tc::tma_load_3d(As + (size_t)(1 * NCH + ch) * a_bytes, &mapA1, &bars[0], ch * KCH, 128 * m, k);
-            tc::tma_load_3d(Bs + (size_t)(0 * NCH + ch) * b_bytes, &mapB0, &bars[0], ch * KCH, 0, k);
-            if (NPB > 1) tc::tma_load_3d(Bs + (size_t)(1 * NCH + ch) * b_bytes, &mapB1, &bars[0], ch * KCH, 0, k);
-        }
-        if (!tc::mbar_wait(&bars[0], 0, TC_BUDGET)) {
-            ffb_flag(status, FFB_ERR_TIMEOUT);
-            *okflag = 0;
-            tc::mbar_wait(&bars[0], 0, TC_BUDGET);  // let in-flight copies land
-        } else {
+        // K chunk ch lives in stage ch % nst; its load arrives on full[stage].
+        // The stage of chunk ch - 1 is refilled with chunk ch - 1 + nst right
+        // after the MMAs of chunk ch are queued, so the tensor pipe always has
+        // work while the copy runs.
+        auto load = [&](int ch) {
+            uint8_t *st = sm + (size_t)(ch % nst) * st_bytes;
+            uint64_t *bar = &full[ch % nst];
+            tc::mbar_arrive_expect_tx(bar, st_bytes);
+            tc::tma_load_3d(st, &mapA0, bar, ch * KCH, 128 * m, k);
+            if (NPA > 1) tc::tma_load_3d(st + a_bytes, &mapA1, bar, ch * KCH, 128 * m, k);
+            tc::tma_load_3d(st + NPA * a_bytes, &mapB0, bar, ch * KCH, 0, k);
+            if (NPB > 1) tc::tma_load_3d(st + NPA * a_bytes + b_bytes, &mapB1, bar, ch * KCH, 0, k);
+        };
+        const int npre = min(nst, NCH);
+        for (int ch = 0; ch < npre; ++ch) load(ch);
+        int issued = npre;        // chunks whose load has been issued
+        int waited = 0;           // chunks whose load has been waited for
+        bool ok = true;
+        const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
+        uint32_t acc = 0;
+        for (int ch = 0; ch < NCH && ok; ++ch) {
+            const int si = ch % nst;
+            if (!tc::mbar_wait(&full[si], (uint32_t)((ch / nst) & 1), TC_BUDGET)) {
+                ok = false;
+                break;
+            }
+            waited = ch + 1;
             tc::fence_after_sync();
-            const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
-            uint32_t acc = 0;
+            const uint32_t sa = tc::smem_u32(sm + (size_t)si * st_bytes);
 #pragma unroll
             for (int pr = 0; pr < NPROD; ++pr) {
                 const int pa = (pr == 2) ? 1 : 0;   // products (0,0), (0,1), (1,0)
                 const int pb = (pr == 1) ? 1 : 0;
-                for (int ch = 0; ch < NCH; ++ch) {
-                    const uint32_t a0 = tc::smem_u32(As + (size_t)(pa * NCH + ch) * a_bytes);
-                    const uint32_t b0 = tc::smem_u32(Bs + (size_t)(pb * NCH + ch) * b_bytes);
+                const uint32_t a0 = sa + pa * a_bytes;
+                const uint32_t b0 = sa + NPA * a_bytes + pb * b_bytes;
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
-                        const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
-                        if (KIND == 0) tc::mma_tf32(tbase, ad, bd, id, acc);
-                        else tc::mma_bf16(tbase, ad, bd, id, acc);
-                        acc = 1;
-                    }
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
+                    const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
+                    if (KIND == 0) tc::mma_tf32(tbase, ad, bd, id, acc);
+                    else tc::mma_bf16(tbase, ad, bd, id, acc);
+                    acc = 1;
                 }
             }
-            tc::mma_commit(&bars[1]);
+            tc::mma_commit(&empty[si]);
+            const int prev = ch - 1;
+            if (prev >= 0 && issued < NCH) {
+                // the MMAs of chunk prev are done reading their stage
+                if (!tc::mbar_wait(&empty[prev % nst], (uint32_t)((prev / nst) & 1), TC_BUDGET)) {
+                    ok = false;
+                    break;
+                }
+                load(issued++);
+            }
+        }
+        // the last commit covers every MMA issued before it
+        tc::mma_commit(done);
+        if (!ok) {
+            ffb_flag(status, FFB_ERR_TIMEOUT);
+            *okflag = 0;
+            for (int ch = waited; ch < issued; ++ch)   // let in-flight copies land
+                tc::mbar_wait(&full[ch % nst], (uint32_t)((ch / nst) & 1), TC_BUDGET);
         }
     }
     __syncthreads();
-    if (*okflag) {
-        if (!tc::mbar_wait(&bars[1], 0, TC_BUDGET)) {
-            ffb_flag(status, FFB_ERR_TIMEOUT);
-            atomicExch(okflag, 0);
-        }
+    if (!tc::mbar_wait(done, 0, TC_BUDGET)) {
+        ffb_flag(status, FFB_ERR_TIMEOUT);
+        atomicExch(okflag, 0);
     }
     tc::fence_after_sync();
     __syncthreads();
     if (*okflag) {
         // drain TMEM into a padded [64 images][BN q][re, im] stage (the operand
-        // tiles are no longer needed), then write each image's p_k complex
+        // ring is no longer needed), then write each image's p_k complex
         // coefficients as one contiguous run
         float *stage = (float *)sm;
         const int ldst = 2 * BN + 2;               // floats per image row, +2 breaks bank aliasing
@@ -249,26 +275,39 @@ void ffb_tc_release(ffb_plan_t p) {
 static bool is_bf16(int prec) { return prec == FFB_BF16 || prec == FFB_BF16X3; }
 static bool is_x3(int prec) { return prec == FFB_BF16X3 || prec == FFB_TF32X3; }
 
-static size_t tc_smem_bytes(int prec, int ld, int BN) {
-    const int es = is_bf16(prec) ? 2 : 4;
-    const int nch = ld / (128 / es);
+// one pipeline stage holds every plane of one 128-byte K chunk: A (128 rows)
+// and B (BN rows), hi and lo for the compensated forms
+static size_t tc_stage_bytes(int prec, int BN) {
     const int np = is_x3(prec) ? 2 : 1;
-    const size_t tiles = (size_t)np * nch * 128 * 128 + (size_t)np * nch * BN * 128;
-    const size_t stage = (size_t)64 * (2 * BN + 2) * 4;
-    return 1024 + (tiles > stage ? tiles : stage) + 64;
+    return (size_t)np * 128 * 128 + (size_t)np * BN * 128;
 }
 
-// shared memory of one CTA: all K of the A and B planes must fit
+static size_t tc_smem_bytes(int prec, int BN, int nst) {
+    const size_t ring = (size_t)nst * tc_stage_bytes(prec, BN);
+    const size_t stage = (size_t)64 * (2 * BN + 2) * 4;
+    return 1024 + (ring > stage ? ring : stage) + 8 * (2 * nst + 1) + 16;
+}
+
+// stages of the K pipeline: as many as fit in one CTA's shared memory, at
+// most the number of K chunks and at most 4; 0 when not even one fits
+static int tc_stages(int prec, int ld, int BN) {
+    const int es = is_bf16(prec) ? 2 : 4;
+    const int nch = ld / (128 / es);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int nst = nch < 4 ? nch : 4;
+    while (nst > 0 && tc_smem_bytes(prec, BN, nst) > (size_t)optin) --nst;
+    return nst;
+}
+
 bool ffb_tc_supported(ffb_plan_t p) {
     const int es = is_bf16(p->precision) ? 2 : 4;
     const int kch = 128 / es;
     const int ld = (p->n_xi + kch - 1) / kch * kch;
     const int BN = (p->pmax + 15) & ~15;
     if (BN > 256) return false;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return tc_smem_bytes(p->precision, ld, BN) <= (size_t)optin;
+    return tc_stages(p->precision, ld, BN) > 0;
 }
 
 int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
@@ -329,7 +368,9 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
 
 template <int KIND, int NPA, int NPB, int NPROD>
 static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    const size_t smem = tc_smem_bytes(p->precision, t->ld, t->BN);
+    const int nst = tc_stages(p->precision, t->ld, t->BN);
+    if (nst <= 0) return FFB_ERR_UNSUPPORTED;
+    const size_t smem = tc_smem_bytes(p->precision, t->BN, nst);
     static int attr = 0;
     if (attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD>,
@@ -341,7 +382,7 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     ProfScope ps(p, FFB_KC_BESSEL, s);
     k_tc_bessel<KIND, NPA, NPB, NPROD><<<g, 128, smem, s>>>(t->mA0, t->mA1, t->mB0, t->mB1, t->ld, nimg, p->d_p,
                                                            p->d_off, p->P, d_coef_chunk, t->BN, t->tmem_cols,
-                                                           p->d_status);
+                                                           nst, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -374,28 +415,30 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 
 // ---------------------------------------------------------------------------
 // a6/a7 on the tensor cores: C^(k) += X X^T, X = [Re A^(k), Im A^(k)] with rows
-// q (padded to M = 128 with zero rows) and K = (image, re/im).  One CTA owns
-// one k and a range of images; it stages tiles of TI images from the
-// interleaved coefficient array into the 128-byte-swizzle K-major layout
-// (hi/lo split in registers, the k = 0 rows shifted by the pilot mean and
-// their imaginary column zero) while the next tile's coefficients are already
-// in flight to registers, and issues the MMA chain (double-buffered tiles,
-// mbarrier per buffer).  Tile t accumulates into TMEM accumulator t mod NACC:
+// q (padded to M = 128) and K = (image, re/im).  A persistent CTA walks the
+// items of a stack table (CovGroup: one k and one image range of one stack
+// per item).  For each item it stages tiles of TI images from the interleaved
+// coefficient array into the 128-byte-swizzle K-major layout (hi/lo split in
+// registers, the k = 0 rows shifted by the pilot mean and their imaginary
+// column zero) while the next tile's coefficients are already in flight to
+// registers, and issues the MMA chain (double-buffered tiles, mbarrier per
+// buffer).  Tile t of an item accumulates into TMEM accumulator t mod nacc:
 // the tensor core's float32 accumulation error grows with the number of
-// accumulate steps, so no chain covers more than ~128 images; the NACC
+// accumulate steps, so no chain covers more than ~128 images; the nacc
 // accumulators are summed in float64 and added to the float64 accumulator.
+// TI is 32 images when 32 p_k values fit the register prefetch, else 16; rows
+// q >= p_k of the staging buffer may hold another item's values, which only
+// reach accumulator entries that are never read.
 // ---------------------------------------------------------------------------
 #define COV_PF 16   // coefficient values per thread per tile held in registers
 
 template <int KIND, int NP>
 __global__ void __launch_bounds__(128, 1)
-k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restrict__ pk_,
-         const int *__restrict__ off_, const int *__restrict__ cov_off, const float *__restrict__ shift,
-         int64_t per, double *__restrict__ acc, int acc_cols, int nacc, int *status) {
+k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per chunk
-    constexpr int NCHT = (KIND == 0) ? 2 : 1;   // chunks per tile
-    constexpr int TI = NCHT * KCH / 2;          // images per tile (2 K entries each): 32
+    constexpr int NCHT = (KIND == 0) ? 2 : 1;   // chunks per tile of 32 images
+    constexpr int KINST = (KIND == 0) ? 8 : 16; // K per MMA instruction
     constexpr uint32_t CH_BYTES = 128u * 128u;  // one chunk of 128 rows
     constexpr uint32_t BUF_BYTES = NP * NCHT * CH_BYTES;
     extern __shared__ uint8_t smraw[];
@@ -404,13 +447,6 @@ k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restric
     uint32_t *slot = (uint32_t *)(bars + 4);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x;
-    const int p = pk_[k], o = off_[k];
-    const int BN = max(16, (p + 15) & ~15);
-    const int64_t ib = (int64_t)blockIdx.y * per;
-    const int64_t ie = min(n, ib + per);
-    const int ntiles = (int)((ie - ib + TI - 1) / TI);
-    const int items = TI * p;                   // (image, q) pairs per tile, <= 128 * COV_PF
 
     for (uint32_t i = threadIdx.x; i < 2 * BUF_BYTES / 16; i += 128)
         ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -418,8 +454,7 @@ k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restric
         tc::mbar_init(&bars[0], 1);
         tc::mbar_init(&bars[1], 1);
         tc::fence_mbar_init();
-        *okflag = (items <= 128 * COV_PF) ? 1 : 0;
-        if (items > 128 * COV_PF) ffb_flag(status, FFB_ERR_UNSUPPORTED);
+        *okflag = 1;
     }
     if (warp == 0) {
         tc::tmem_alloc(slot, 512u);
@@ -429,135 +464,162 @@ k_tc_cov(const float2 *__restrict__ coef, int64_t n, int P, const int *__restric
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *slot;
-    const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
+    int64_t gt = 0;   // tiles committed by this CTA: buffer gt & 1, mbarrier phase (gt >> 1) & 1
 
-    float2 pre[COV_PF];
-    auto load_tile = [&](int t) {
-        const int64_t i0 = ib + (int64_t)t * TI;
-#pragma unroll
-        for (int u = 0; u < COV_PF; ++u) {
-            const int it = threadIdx.x + 128 * u;
-            float2 v = make_float2(0.f, 0.f);
-            if (it < items) {
-                const int ii = it / p, q = it - ii * p;
-                if (i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
-            }
-            pre[u] = v;
+    for (int64_t item = blockIdx.x; item < g.nitems && *okflag; item += gridDim.x) {
+        const CovStack &S = g.st[cov_stack_of(g, item)];
+        const int64_t local = item - S.item0;
+        const int k = (int)(local % S.nk);
+        const int64_t ib = (local / S.nk) * (int64_t)S.per;
+        const int64_t ie = min(S.n, ib + (int64_t)S.per);
+        const int p = S.pk[k], o = S.off[k];
+        const int BN = max(16, (p + 15) & ~15);
+        const int TI = (g.tile_imgs >= 32 && 32 * p <= 128 * COV_PF) ? 32 : 16;
+        const int items = TI * p;                   // (image, q) pairs per tile
+        const int kent = 2 * TI;                    // K entries per tile
+        const int ntiles = (ie > ib) ? (int)((ie - ib + TI - 1) / TI) : 0;
+        if (items > 128 * COV_PF || BN > acc_cols) {   // uniform across the CTA
+            if (threadIdx.x == 0) ffb_flag(status, FFB_ERR_UNSUPPORTED);
+            continue;
         }
-    };
-    if (*okflag && ntiles > 0) load_tile(0);
-    for (int t = 0; t < ntiles && *okflag; ++t) {
-        const int buf = t & 1;
-        uint8_t *B0 = sm + buf * BUF_BYTES;
-        if (t >= 2) {
-            if (!tc::mbar_wait(&bars[buf], (uint32_t)(((t - 2) >> 1) & 1), TC_BUDGET)) {
+        const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
+        const float2 *coef = S.coef;
+        const int P = S.P;
+
+        float2 pre[COV_PF];
+        auto load_tile = [&](int t) {
+            const int64_t i0 = ib + (int64_t)t * TI;
+#pragma unroll
+            for (int u = 0; u < COV_PF; ++u) {
+                const int it = threadIdx.x + 128 * u;
+                float2 v = make_float2(0.f, 0.f);
+                if (it < items) {
+                    const int ii = it / p, q = it - ii * p;
+                    if (i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
+                }
+                pre[u] = v;
+            }
+        };
+        if (ntiles > 0) load_tile(0);
+        for (int t = 0; t < ntiles && *okflag; ++t, ++gt) {
+            const int buf = (int)(gt & 1);
+            uint8_t *B0 = sm + buf * BUF_BYTES;
+            if (gt >= 2) {
+                if (!tc::mbar_wait(&bars[buf], (uint32_t)(((gt - 2) >> 1) & 1), TC_BUDGET)) {
+                    ffb_flag(status, FFB_ERR_TIMEOUT);
+                    atomicExch(okflag, 0);
+                }
+            }
+            float2 cur[COV_PF];
+#pragma unroll
+            for (int u = 0; u < COV_PF; ++u) cur[u] = pre[u];
+            if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
+#pragma unroll
+            for (int u = 0; u < COV_PF; ++u) {
+                const int it = threadIdx.x + 128 * u;
+                if (it >= items) break;
+                const int ii = it / p, q = it - ii * p;
+                float re = cur[u].x, im = cur[u].y;
+                if (k == 0) {   // shifted real part; images past the range stay zero
+                    re = (ib + (int64_t)t * TI + ii < ie) ? re - S.shift[q] : 0.f;
+                    im = 0.f;
+                }
+                const int kidx = 2 * ii;                 // K index of the real part
+                const int ch = kidx / KCH, e = kidx % KCH;
+                const uint32_t byte = (uint32_t)e * ES;
+                const uint32_t off = ch * CH_BYTES + (q >> 3) * 1024u + (q & 7) * 128u +
+                                     ((((byte >> 4) ^ (uint32_t)(q & 7)) << 4) | (byte & 15u));
+                if (KIND == 0) {
+                    const float rh = tf32_round(re), ih = tf32_round(im);
+                    *(float2 *)(B0 + off) = make_float2(rh, ih);
+                    if (NP > 1) *(float2 *)(B0 + NCHT * CH_BYTES + off) = make_float2(re - rh, im - ih);
+                } else {
+                    const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+                    *(__nv_bfloat162 *)(B0 + off) = __halves2bfloat162(rh, ih);
+                    if (NP > 1)
+                        *(__nv_bfloat162 *)(B0 + NCHT * CH_BYTES + off) = __halves2bfloat162(
+                            __float2bfloat16_rn(re - __bfloat162float(rh)),
+                            __float2bfloat16_rn(im - __bfloat162float(ih)));
+                }
+            }
+            tc::fence_async_shared();   // generic-proxy writes -> visible to the tensor core
+            __syncthreads();
+            if (threadIdx.x == 0 && *okflag) {
+                tc::fence_after_sync();
+                const uint32_t dt = tbase + (uint32_t)((t % nacc) * acc_cols);
+                const int nch = (kent + KCH - 1) / KCH;
+#pragma unroll
+                for (int pr = 0; pr < (NP > 1 ? 3 : 1); ++pr) {
+                    const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+                    for (int ch = 0; ch < nch; ++ch) {
+                        const uint32_t a0 = tc::smem_u32(B0 + (size_t)(pa * NCHT + ch) * CH_BYTES);
+                        const uint32_t b0 = tc::smem_u32(B0 + (size_t)(pb * NCHT + ch) * CH_BYTES);
+                        const int nks = min(KCH, kent - ch * KCH) / KINST;
+                        for (int ks = 0; ks < nks; ++ks) {
+                            const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
+                            const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
+                            const uint32_t accf = (t >= nacc || pr > 0 || ch > 0 || ks > 0) ? 1u : 0u;
+                            if (KIND == 0) tc::mma_tf32(dt, ad, bd, id, accf);
+                            else tc::mma_bf16(dt, ad, bd, id, accf);
+                        }
+                    }
+                }
+                tc::mma_commit(&bars[buf]);
+            }
+        }
+        __syncthreads();
+        // the last commit covers every MMA issued before it
+        if (ntiles > 0 && *okflag) {
+            if (!tc::mbar_wait(&bars[(gt - 1) & 1], (uint32_t)(((gt - 1) >> 1) & 1), TC_BUDGET)) {
                 ffb_flag(status, FFB_ERR_TIMEOUT);
                 atomicExch(okflag, 0);
             }
         }
-        float2 cur[COV_PF];
-#pragma unroll
-        for (int u = 0; u < COV_PF; ++u) cur[u] = pre[u];
-        if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
-#pragma unroll
-        for (int u = 0; u < COV_PF; ++u) {
-            const int it = threadIdx.x + 128 * u;
-            if (it >= items) break;
-            const int ii = it / p, q = it - ii * p;
-            float re = cur[u].x, im = cur[u].y;
-            if (k == 0) {   // shifted real part; images past the range stay zero
-                re = (ib + (int64_t)t * TI + ii < ie) ? re - shift[q] : 0.f;
-                im = 0.f;
-            }
-            const int kidx = 2 * ii;                 // K index of the real part
-            const int ch = kidx / KCH, e = kidx % KCH;
-            const uint32_t byte = (uint32_t)e * ES;
-            const uint32_t off = ch * CH_BYTES + (q >> 3) * 1024u + (q & 7) * 128u +
-                                 ((((byte >> 4) ^ (uint32_t)(q & 7)) << 4) | (byte & 15u));
-            if (KIND == 0) {
-                const float rh = tf32_round(re), ih = tf32_round(im);
-                *(float2 *)(B0 + off) = make_float2(rh, ih);
-                if (NP > 1) *(float2 *)(B0 + NCHT * CH_BYTES + off) = make_float2(re - rh, im - ih);
-            } else {
-                const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
-                *(__nv_bfloat162 *)(B0 + off) = __halves2bfloat162(rh, ih);
-                if (NP > 1)
-                    *(__nv_bfloat162 *)(B0 + NCHT * CH_BYTES + off) = __halves2bfloat162(
-                        __float2bfloat16_rn(re - __bfloat162float(rh)), __float2bfloat16_rn(im - __bfloat162float(ih)));
-            }
-        }
-        tc::fence_async_shared();   // generic-proxy writes -> visible to the tensor core
+        tc::fence_after_sync();
         __syncthreads();
-        if (threadIdx.x == 0 && *okflag) {
-            tc::fence_after_sync();
-            const int a = t % nacc;
-            const uint32_t dt = tbase + (uint32_t)(a * acc_cols);
+        if (ntiles > 0 && *okflag) {
+            const int q = 32 * warp + lane;
+            const int used = min(nacc, ntiles);
+            double *blk = S.acc + S.cov_off[k];
+            for (int c16 = 0; c16 < BN; c16 += 16) {
+                double sum[16];
 #pragma unroll
-            for (int pr = 0; pr < (NP > 1 ? 3 : 1); ++pr) {
-                const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-                for (int ch = 0; ch < NCHT; ++ch) {
-                    const uint32_t a0 = tc::smem_u32(B0 + (size_t)(pa * NCHT + ch) * CH_BYTES);
-                    const uint32_t b0 = tc::smem_u32(B0 + (size_t)(pb * NCHT + ch) * CH_BYTES);
+                for (int i = 0; i < 16; ++i) sum[i] = 0.0;
+                for (int a = 0; a < used; ++a) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * acc_cols + c16), v);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
-                        const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
-                        const uint32_t accf = (t >= nacc || pr > 0 || ch > 0 || ks > 0) ? 1u : 0u;
-                        if (KIND == 0) tc::mma_tf32(dt, ad, bd, id, accf);
-                        else tc::mma_bf16(dt, ad, bd, id, accf);
-                    }
+                    for (int i = 0; i < 16; ++i) sum[i] += (double)v[i];
+                }
+                if (q < p) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c16 + i < p) atomicAdd(&blk[(size_t)q * p + c16 + i], sum[i]);
                 }
             }
-            tc::mma_commit(&bars[buf]);
         }
-    }
-    __syncthreads();
-    // the last commit covers every MMA issued before it
-    if (ntiles > 0 && *okflag) {
-        const int t = ntiles - 1;
-        if (!tc::mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1), TC_BUDGET)) {
-            ffb_flag(status, FFB_ERR_TIMEOUT);
-            atomicExch(okflag, 0);
-        }
-    }
-    tc::fence_after_sync();
-    __syncthreads();
-    if (ntiles > 0 && *okflag) {
-        const int q = 32 * warp + lane;
-        const int used = min(nacc, ntiles);
-        double *blk = acc + cov_off[k];
-        for (int c16 = 0; c16 < BN; c16 += 16) {
-            double sum[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) sum[i] = 0.0;
-            for (int a = 0; a < used; ++a) {
-                float v[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * acc_cols + c16), v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) sum[i] += (double)v[i];
-            }
-            if (q < p) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c16 + i < p) atomicAdd(&blk[(size_t)q * p + c16 + i], sum[i]);
-            }
-        }
+        // accumulator reads complete before the next item's MMAs overwrite them
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, 512u);
 }
 
-// k = 0 mean: sum0[q] += sum_i (Re a_{i,0,q} - shift_q), float64, one CTA per
-// image range
-__global__ void k_cov_sum0(const float2 *__restrict__ coef, int64_t n, int P, int p0, const float *__restrict__ shift,
-                           int64_t per, double *__restrict__ sum0) {
-    const int64_t ib = (int64_t)blockIdx.x * per;
-    const int64_t ie = min(n, ib + per);
+// k = 0 mean: sum0[q] += sum_i (Re a_{i,0,q} - shift_q), float64; grid
+// (image ranges, stacks)
+__global__ void k_cov_sum0(const __grid_constant__ CovGroup g, int64_t per0) {
+    const CovStack &S = g.st[blockIdx.y];
+    const int64_t ib = (int64_t)blockIdx.x * per0;
+    if (ib >= S.n) return;
+    const int64_t ie = min(S.n, ib + per0);
+    const int p0 = S.pk[0];
     for (int q = threadIdx.x; q < p0; q += blockDim.x) {
         double s = 0.0;
-        for (int64_t i = ib; i < ie; ++i) s += (double)(coef[i * P + q].x - shift[q]);
-        atomicAdd(&sum0[q], s);
+        for (int64_t i = ib; i < ie; ++i) s += (double)(S.coef[i * S.P + q].x - S.shift[q]);
+        atomicAdd(&S.sum0[q], s);
     }
 }
 
@@ -571,7 +633,7 @@ static size_t tc_cov_smem(int prec) {
 bool ffb_tc_cov_supported(ffb_plan_t p) {
     if (p->precision == FFB_FP32) return false;
     if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
-    if (32 * p->pmax > 128 * COV_PF) return false;    // one 32-image tile fits the register prefetch
+    if (16 * p->pmax > 128 * COV_PF) return false;    // a 16-image tile fits the register prefetch
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -579,8 +641,8 @@ bool ffb_tc_cov_supported(ffb_plan_t p) {
 }
 
 template <int KIND, int NP>
-static int launch_tc_cov(ffb_plan_t p, const float *d_coef, int64_t n, int64_t per, cudaStream_t s) {
-    const size_t smem = tc_cov_smem(p->precision);
+static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t s) {
+    const size_t smem = tc_cov_smem(0);
     static int attr = 0;
     if (attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_cov<KIND, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -588,32 +650,47 @@ static int launch_tc_cov(ffb_plan_t p, const float *d_coef, int64_t n, int64_t p
         if (e) return e;
         attr = (int)smem;
     }
+    int pmax = 16;
+    for (int i = 0; i < g.S; ++i) pmax = max(pmax, g.st[i].pmax);
     int cols = 32;
-    while (cols < ((p->pmax + 15) & ~15)) cols <<= 1;
+    while (cols < ((pmax + 15) & ~15)) cols <<= 1;
+    if (cols > 128) return FFB_ERR_UNSUPPORTED;
     const int nacc = 512 / cols > 8 ? 8 : 512 / cols;   // rotating float32 accumulators in TMEM
-    dim3 g(p->k_max + 1, (unsigned)((n + per - 1) / per));
-    ProfScope ps(p, FFB_KC_COV, s);
-    k_tc_cov<KIND, NP><<<g, 128, smem, s>>>((const float2 *)d_coef, n, p->P, p->d_p, p->d_off, p->d_cov_off,
-                                           p->d_shift, per, p->d_acc, cols, nacc, p->d_status);
-    p->launches++;
+    k_tc_cov<KIND, NP><<<grid, 128, smem, s>>>(g, cols, nacc, status);
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s) {
+    if (g.nitems <= 0) return FFB_OK;
+    if (grid <= 0) grid = ffb_cov_grid_default(precision);
+    if ((int64_t)grid > g.nitems) grid = (int)g.nitems;
+    int e;
+    switch (precision) {
+        case FFB_TF32: e = launch_tc_cov<0, 1>(g, grid, status, s); break;
+        case FFB_TF32X3: e = launch_tc_cov<0, 2>(g, grid, status, s); break;
+        case FFB_BF16: e = launch_tc_cov<1, 1>(g, grid, status, s); break;
+        case FFB_BF16X3: e = launch_tc_cov<1, 2>(g, grid, status, s); break;
+        default: return FFB_ERR_ARG;
+    }
+    if (e) return e;
+    const int64_t per0 = 2048;
+    int64_t nr = 1;
+    for (int i = 0; i < g.S; ++i) nr = max(nr, (g.st[i].n + per0 - 1) / per0);
+    if (nr > 65535 * 16) return FFB_ERR_ARG;
+    k_cov_sum0<<<dim3((unsigned)nr, (unsigned)g.S), 64, 0, s>>>(g, per0);
     return ffb_check_cuda(cudaGetLastError());
 }
 
 int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
-    const int64_t per = 1024;
-    if ((n + per - 1) / per > 65535) return FFB_ERR_ARG;
-    int e;
-    switch (p->precision) {
-        case FFB_TF32: e = launch_tc_cov<0, 1>(p, d_coef, n, per, s); break;
-        case FFB_TF32X3: e = launch_tc_cov<0, 2>(p, d_coef, n, per, s); break;
-        case FFB_BF16: e = launch_tc_cov<1, 1>(p, d_coef, n, per, s); break;
-        default: e = launch_tc_cov<1, 2>(p, d_coef, n, per, s); break;
-    }
-    if (e) return e;
-    const int64_t per0 = 2048;
-    ProfScope ps(p, FFB_KC_COVAUX, s);
-    k_cov_sum0<<<(unsigned)((n + per0 - 1) / per0), 64, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0],
-                                                                p->d_shift, per0, p->d_sum0);
-    p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
+    CovGroup g;          // copied into the launch's parameters
+    g.S = 1;
+    g.tile_imgs = 32;
+    ffb_cov_stack(p, d_coef, n, true, &g.st[0]);
+    g.st[0].item0 = 0;
+    g.st[0].per = 1024;
+    g.nitems = (int64_t)g.st[0].nk * ((n + 1023) / 1024);
+    ProfScope ps(p, FFB_KC_COV, s);
+    const int e = ffb_launch_cov_group_tc(p->precision, g, 0, p->d_status, s);
+    p->launches += 2;
+    return e;
 }

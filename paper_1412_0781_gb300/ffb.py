@@ -52,6 +52,14 @@ SIGNATURES = {
     "ffb_profile": (_i, [_vp, _i]),
     "ffb_profile_read": (_i, [_vp, _pd, ctypes.POINTER(ctypes.c_int64)]),
     "ffb_launch_count": (_i64, [_vp]),
+    "ffb_group_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), _vp]),
+    "ffb_group_destroy": (_i, [_vp]),
+    "ffb_group_expand_cov": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(_vp), _i, _vp]),
+    "ffb_group_covariance": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int64), _i, _vp]),
+    "ffb_group_sync": (_i, [_vp, _vp]),
+    "ffb_group_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "ffb_group_tuning": (_i, [_vp, _i, _pi, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
     "ffb_strerror": (ctypes.c_char_p, [_i]),
 }
 
@@ -329,3 +337,82 @@ class Plan:
             out.append(packed[o:o + pk * pk].view(pk, pk))
             o += pk * pk
         return out
+
+
+class Group:
+    """Several stacks of uneven L and n through a1-a7 in one call (see the
+    batching section of include/ffb.h).  ``plans`` are distinct Plans of one
+    precision; they must outlive the group."""
+
+    INFO = ("S", "precision", "per", "tile", "grid", "graphs", "replays", "eager", "launches", "candidates")
+
+    def __init__(self, plans, stream=None):
+        lib = load()
+        self.plans = list(plans)
+        hs = (_vp * len(self.plans))(*[p.handle.value for p in self.plans])
+        self._h = _vp()
+        _check(lib.ffb_group_create(ctypes.byref(self._h), len(self.plans), hs, _stream(stream)),
+               "ffb_group_create")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ffb_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, tensors, dtype, name, allow_none):
+        ptrs = []
+        for i, t in enumerate(tensors):
+            if t is None and allow_none[i]:
+                ptrs.append(None)
+            else:
+                ptrs.append(_ptr(t, dtype, "%s[%d]" % (name, i)).value)
+        return (_vp * len(ptrs))(*ptrs)
+
+    def expand_cov(self, images, coefs, reset=True, stream=None):
+        """images[s]: float32 [n_s, L_s, L_s]; coefs[s]: float32 [n_s, P_s, 2]
+        written by the call.  Returns coefs."""
+        if len(images) != len(self.plans) or len(coefs) != len(self.plans):
+            raise ValueError("one images and one coefficient tensor per stack")
+        n = [0 if x is None else int(x.shape[0]) for x in images]
+        for s, (p, x, c) in enumerate(zip(self.plans, images, coefs)):
+            if n[s] and (tuple(x.shape[1:]) != (p.L, p.L) or c is None or tuple(c.shape) != (n[s], p.P, 2)):
+                raise ValueError("stack %d: shapes do not match its plan" % s)
+        zero = [v == 0 for v in n]
+        _check(load().ffb_group_expand_cov(self._h, self._arrays(images, torch.float32, "images", zero),
+                                           (ctypes.c_int64 * len(n))(*n),
+                                           self._arrays(coefs, torch.float32, "coefs", zero), int(bool(reset)),
+                                           _stream(stream)), "ffb_group_expand_cov")
+        return coefs
+
+    def covariance(self, coefs, reset=True, stream=None):
+        n = [0 if c is None else int(c.shape[0]) for c in coefs]
+        for s, (p, c) in enumerate(zip(self.plans, coefs)):
+            if n[s] and tuple(c.shape[1:]) != (p.P, 2):
+                raise ValueError("stack %d: coefficient shape does not match its plan" % s)
+        zero = [v == 0 for v in n]
+        _check(load().ffb_group_covariance(self._h, self._arrays(coefs, torch.float32, "coefs", zero),
+                                           (ctypes.c_int64 * len(n))(*n), int(bool(reset)), _stream(stream)),
+               "ffb_group_covariance")
+
+    def sync(self, stream=None):
+        _check(load().ffb_group_sync(self._h, _stream(stream)), "ffb_group_sync")
+
+    def info(self):
+        out = (ctypes.c_int64 * 10)()
+        _check(load().ffb_group_info(self._h, out), "ffb_group_info")
+        return dict(zip(self.INFO, list(out)))
+
+    def tuning(self):
+        m = 32
+        per, tile, grid = (ctypes.c_int * m)(), (ctypes.c_int * m)(), (ctypes.c_int * m)()
+        ms = (ctypes.c_float * m)()
+        k = load().ffb_group_tuning(self._h, m, per, tile, grid, ms)
+        if k < 0:
+            raise FFBError(k, "ffb_group_tuning")
+        return [{"per": per[i], "tile": tile[i], "grid": grid[i], "ms": ms[i]} for i in range(k)]

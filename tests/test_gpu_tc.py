@@ -39,9 +39,12 @@ def _oracle(L, imgs):
     return _REF[key]
 
 
-@pytest.mark.parametrize("L,n", [(32, 300), (128, 160)])
+@pytest.mark.parametrize("L,n", [(32, 300), (128, 160), (180, 20), (256, 8)])
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
 def test_tc_quadrature_matches_oracle(dev, L, n, prec):
+    """L = 180 (n_theta = 720, the separate-kernel NUFFT) and L = 256 (K = 256
+    in four bf16 / eight tf32 chunks streamed through a three-stage pipeline)
+    cover the K-pipelined contraction beyond one resident tile."""
     imgs = _stack(L, n)
     ref = _oracle(L, imgs)
     plan = Plan(L, 0.5, L / 2, eps=1e-6, precision=prec)

@@ -73,3 +73,22 @@ def test_null_plan_is_rejected(lib):
                                ctypes.c_void_p]
     assert lib.ffb_expand(None, None, 1, None, None) == -1
     assert lib.ffb_plan_destroy(None) == 0
+
+
+def test_group_calls_reject_bad_arguments(lib):
+    vp = ctypes.c_void_p
+    lib.ffb_group_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), vp]
+    h = vp()
+    plans = (vp * 2)(None, None)
+    assert lib.ffb_group_create(ctypes.byref(h), 0, plans, None) == -1     # S < 1
+    assert lib.ffb_group_create(ctypes.byref(h), 65, plans, None) == -1    # S > 64
+    assert lib.ffb_group_create(ctypes.byref(h), 2, plans, None) == -1     # NULL plans
+    assert not h.value
+    lib.ffb_group_expand_cov.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(vp), ctypes.c_int, vp]
+    assert lib.ffb_group_expand_cov(None, None, None, None, 1, None) == -1
+    lib.ffb_group_covariance.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.c_int, vp]
+    assert lib.ffb_group_covariance(None, None, None, 1, None) == -1
+    lib.ffb_group_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    assert lib.ffb_group_info(None, None) == -1
+    assert lib.ffb_group_destroy(None) == 0
