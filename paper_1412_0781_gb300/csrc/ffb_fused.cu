@@ -232,6 +232,8 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     constexpr float two_over_w = 2.0f / W;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
     float2 *stage0 = smz + MH * SLD;
+    // t / nl as a multiply-high: exact for t < 2^32 / nl
+    const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;
     for (int b = 0; b * FUS_GB < npts; ++b) {
         const int t0 = b * FUS_GB;
         const int cnt = min(FUS_GB, npts - t0);
@@ -241,7 +243,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             const int loc = pm[s];
             if (loc >= cnt) continue;
             const int t = t0 + loc;
-            const int j = t / nl;
+            const int j = (int)__umulhi((unsigned)t, nl_magic);
             const int l = lbeg + (t - j * nl);
             const float2 r = __ldg(&rad[j]);
             const float4 a = __ldg(&ang[l]);
@@ -257,31 +259,49 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) {
                 ffb_flag(status, FFB_ERR_ARG);
             } else {
-                float wx[W];
-#pragma unroll
-                for (int q = 0; q < W; ++q) wx[q] = es_kernel(f1 - (float)q, two_over_w, beta);
+                // column sums over the W rows first: every row issues 2 W
+                // independent FMAs; the column weights are applied at the end
                 const float2 *base = S + r0 * SLD + c0;
+                float2 cs[W];
+                {
+                    const float wy = es_kernel(f2, two_over_w, beta);
 #pragma unroll
-                for (int bq = 0; bq < W; ++bq) {
+                    for (int q = 0; q < W; ++q) {
+                        const float2 g = base[q];
+                        cs[q] = make_float2(wy * g.x, wy * g.y);
+                    }
+                }
+#pragma unroll
+                for (int bq = 1; bq < W; ++bq) {
                     const float wy = es_kernel(f2 - (float)bq, two_over_w, beta);
                     const float2 *row = base + bq * SLD;
-                    float sx = 0.f, sy = 0.f;
 #pragma unroll
                     for (int q = 0; q < W; ++q) {
                         const float2 g = row[q];
-                        sx = fmaf(wx[q], g.x, sx);
-                        sy = fmaf(wx[q], g.y, sy);
+                        cs[q].x = fmaf(wy, g.x, cs[q].x);
+                        cs[q].y = fmaf(wy, g.y, cs[q].y);
                     }
-                    acc.x = fmaf(wy, sx, acc.x);
-                    acc.y = fmaf(wy, sy, acc.y);
                 }
+                float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < W; q += 2) {
+                    const float w0 = es_kernel(f1 - (float)q, two_over_w, beta);
+                    ax0 = fmaf(w0, cs[q].x, ax0);
+                    ay0 = fmaf(w0, cs[q].y, ay0);
+                    if (q + 1 < W) {
+                        const float w1v = es_kernel(f1 - (float)(q + 1), two_over_w, beta);
+                        ax1 = fmaf(w1v, cs[q + 1].x, ax1);
+                        ay1 = fmaf(w1v, cs[q + 1].y, ay1);
+                    }
+                }
+                acc = make_float2(ax0 + ax1, ay0 + ay1);
             }
             stage[loc] = acc;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += FUS_NT) {
             const int t = t0 + i;
-            const int j = t / nl;
+            const int j = (int)__umulhi((unsigned)t, nl_magic);
             const int l = lbeg + (t - j * nl);
             Fout[(size_t)j * nh + l] = stage[i];
         }

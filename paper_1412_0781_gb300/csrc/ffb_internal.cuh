@@ -254,12 +254,17 @@ __device__ __forceinline__ float tf32_round(float x) {
 // Operand formats the ring FFT can write for the radial quadrature.
 enum { FFB_FMT_F32 = 0, FFB_FMT_TF32 = 1, FFB_FMT_TF32X2 = 2, FFB_FMT_BF16 = 3, FFB_FMT_BF16X2 = 4 };
 
-// Exponential-of-semicircle kernel psi(x) = exp(beta (sqrt(1 - (2x/w)^2) - 1)),
-// |x| < w/2, in fine-grid units.
+// Exponential-of-semicircle kernel psi(x) = exp(beta (sqrt(1 - z^2) - 1)),
+// z = 2x/w, |x| < w/2, in fine-grid units, evaluated as
+// exp(-beta z^2 / (1 + sqrt(1 - z^2))): the exponent carries a small relative
+// error instead of the absolute error of sqrt(u) - 1 near the centre, so the
+// approximate square root and quotient suffice (weight error <= ~2e-7).
 __device__ __forceinline__ float es_kernel(float x, float two_over_w, float beta) {
-    float t = x * two_over_w;
-    float u = fmaxf(1.0f - t * t, 0.0f);
-    return (u > 0.0f) ? __expf(beta * (sqrtf(u) - 1.0f)) : 0.0f;
+    const float z = x * two_over_w;
+    const float z2 = z * z;
+    const float u = 1.0f - z2;
+    if (!(u > 0.0f)) return 0.0f;
+    return __expf(-__fdividef(beta * z2, 1.0f + u * rsqrtf(u)));
 }
 
 // J_k(x), x >= 0, by Miller's backward recurrence: starting far above both k
