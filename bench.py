@@ -125,19 +125,35 @@ def algorithmic_flops(plan):
 # capture (profiles/k_grid_interp_half_L128.md: 152-image launch), valid only
 # while the kernel's source file is byte-identical to the profiled one.
 NCU_TRAFFIC = {
-    "grid_interp": {"source": "paper_1412_0781_gb300/csrc/ffb_fused.cu",
-                    "sha256": "89a7418cf11c0694bddc10e8db57692784acf88d8a9926ca7ea482859f58e4c5",
-                    "bytes_per_launch": 10075392 + 6656, "images_per_launch": 152},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the
+    # dominant kernel, valid while the source it was captured from is unchanged
+    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_fused.cu:k_grid_interp_half",
+                                "paper_1412_0781_gb300/csrc/ffb_internal.cuh"],
+                    "sha256": "db46cb94189b8aab20c2b3072fbada93b80d5bbb3171aadcfce666462a51a0de",
+                    "bytes_per_launch": 10081024 + 8448, "images_per_launch": 152},
 }
 
 
-def ncu_traffic(kernel, images_per_launch):
+def _source_digest(sources):
+    """sha256 over the listed files; "file:kernel" hashes only the text from the
+    kernel's template line to the next section banner."""
     import hashlib
+    h = hashlib.sha256()
+    for src in sources:
+        path, _, kern = src.partition(":")
+        txt = open(os.path.join(ROOT, path)).read()
+        if kern:
+            a = txt.index(kern + "(")
+            a = txt.rindex("template", 0, a)
+            b = txt.index("\n// " + "-" * 75 + "\n", a)   # the next full-width section banner
+            txt = txt[a:b]
+        h.update(txt.encode())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel, images_per_launch):
     rec = NCU_TRAFFIC.get(kernel)
-    if rec is None:
-        return None
-    path = os.path.join(ROOT, rec["source"])
-    if hashlib.sha256(open(path, "rb").read()).hexdigest() != rec["sha256"]:
+    if rec is None or _source_digest(rec["sources"]) != rec["sha256"]:
         return None
     return rec["bytes_per_launch"] * images_per_launch / rec["images_per_launch"]
 
@@ -300,7 +316,9 @@ def run_ours(args):
         out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
 
         copy_stream = torch.cuda.Stream(device=dev)
-        nparts = 8
+        # host->device copies of at most ~200 MB each: on this system larger
+        # single copies from pinned memory ran an order of magnitude slower
+        nparts = max(8, -(-hbuf.numel() * 4 // (200 << 20)))
         bounds = [(n * c // nparts, n * (c + 1) // nparts) for c in range(nparts)]
         events = [torch.cuda.Event() for _ in range(nparts)]
 
@@ -318,17 +336,23 @@ def run_ours(args):
             out_mean.copy_(m)
             out_C.copy_(C)
 
-        for _ in range(2):
+        for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k = max(3, args.steps // 4)
+        # host clock around every step (each ends with the covariance on the
+        # host); the value is total images / total time over k steps
+        k = max(5, args.steps // 2)
+        steps_ms = []
         for _ in range(k):
+            ts = time.perf_counter()
             e2e_step()
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / k
+            torch.cuda.synchronize()
+            steps_ms.append((time.perf_counter() - ts) * 1e3)
+        dt = sum(steps_ms) / 1e3 / k
         e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
-               "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8)}
+               "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8), "steps": k,
+               "median_step_ms": statistics.median(steps_ms), "max_step_ms": max(steps_ms),
+               "h2d_parts": nparts}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:

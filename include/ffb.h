@@ -66,7 +66,8 @@ typedef enum {
     FFB_DENOISE_TOPK = 0,       /* keep the K (k,l) pairs of largest eigenvalue, gain 1 */
     FFB_DENOISE_MP_WIENER = 1,  /* keep lambda > sigma2 (1+sqrt(gamma_k))^2 (Eq. compselect),
                                    gain (lambda - sigma2)/lambda                          */
-    FFB_DENOISE_ALL = 2         /* every component, gain 1 (projection onto the span)    */
+    FFB_DENOISE_ALL = 2,        /* every component, gain 1 (projection onto the span)    */
+    FFB_DENOISE_MP_HARD = 3     /* keep lambda > sigma2 (1+sqrt(gamma_k))^2, gain 1       */
 } ffb_denoise_mode;
 
 /* ffb_plan -- Alg. 1 steps 1-2 (precomputation), Sec. II-A and II-B.
@@ -252,6 +253,55 @@ int ffb_profile(ffb_plan_t plan, int enable);
  * 13 shared-memory grid + interpolation, 14 ring FFT from the polar buffer.
  * Synchronises on the recorded events. */
 int ffb_profile_read(ffb_plan_t plan, double *h_ms, int64_t *h_calls);
+
+/* ffb_invariants -- rotation-invariant features of n images from their
+ * steerable PCA coefficients c_{k,l} = u^(k)_l^T (a^(k) - mean [k = 0])
+ * (Eq. sPCAcoeff, eigenpairs and k = 0 mean of the last ffb_eig / ffb_svd):
+ * the bispectrum-like features of Sec. I.
+ *   power:      d_pow[i][t] = |c_{k,l}|^2 for the npow pairs h_pairs[t] = (k, l);
+ *   bispectrum: d_bis[i][t] = c_{k1,l1} c_{k2,l2} conj(c_{k1+k2,l3}) (complex,
+ *               [re, im]) for the nbis quintuples h_triples[t] = (k1, l1, k2, l2, l3).
+ * An in-plane rotation multiplies c_{k,l} by e^{-ik alpha}, which cancels in
+ * both; a reflection leaves the power and conjugates the bispectrum.
+ * d_coef: device [n][P][2]; d_pow float32 [n][npow]; d_bis float32
+ * [n][nbis][2]; index lists are host arrays (FFB_ERR_ARG for a pair outside
+ * the basis or k1 + k2 > k_max; FFB_ERR_STATE before any eigendecomposition).
+ * Synchronises. */
+int ffb_invariants(ffb_plan_t plan, const float *d_coef, int64_t n, int npow, const int *h_pairs, float *d_pow,
+                   int nbis, const int *h_triples, float *d_bis, void *stream);
+
+/* ffb_svd -- Alg. 2 step 4 by the SVD route of Sec. III: the eigenpairs of every
+ * C^(k) from the coefficient matrices of n images (d_coef: device [n][P][2])
+ * without forming the covariance from the data.  For each k, X_k stacks the
+ * rows (Re a_{i,k,.}, Im a_{i,k,.}) (k > 0) or Re a_{i,0,.} - mean (k = 0);
+ * a tall-skinny QR X_k = Q_k R_k (float32 Householder in shared memory,
+ * float64 norms, per image range and then merged) is followed by the float64
+ * Jacobi eigensolver on R_k^T R_k / n, whose eigenvectors are the singular
+ * vectors of A^(k) and eigenvalues s^2 / n.  Outputs as ffb_eig (device,
+ * may be NULL); the plan's eigenpairs, k = 0 mean and finalised covariance
+ * (R^T R / n) are replaced, so ffb_select / ffb_filter / ffb_radial_* use
+ * them.  Requires p_k <= 128 (FFB_ERR_UNSUPPORTED otherwise); synchronises. */
+int ffb_svd(ffb_plan_t plan, const float *d_coef, int64_t n, double *d_evals, double *d_evecs, void *stream);
+
+/* ffb_estimate_support -- radius of compact support R and band limit c of a
+ * stack, estimated from the noisy images (the procedure of Sec. V applied to
+ * the simulated ribosome projections).  Real domain: subtract the mean image,
+ * average the per-pixel variance over rings r = round(|i|) < L/2 (the mean
+ * radial variance), subtract the noise variance, clip at zero and accumulate
+ * with the weight r; R is the first ring at which the cumulative sum reaches
+ * `frac` (0 < frac <= 1, the paper uses 0.999) of its total.  Fourier domain:
+ * the same with the angular average of the mean power spectrum
+ * (1/L^2) |F(I - mean)(xi_j, theta_l)|^2 on the plan's polar grid and the
+ * weight xi_j w_j; c is the node xi_j reached.  Use a plan with c = 1/2 and
+ * R = L/2 so that the polar grid spans the whole band.  sigma2 >= 0 is the
+ * noise variance; sigma2 < 0 estimates it as the mean variance of the pixels
+ * with |i| >= L/2.  Outputs (host): h_out[4] = {R in pixels, c in cycles per
+ * pixel, the noise variance used, index of c's node}; h_radvar[L/2] the mean
+ * radial variance, h_radpow[n_xi] the radial power spectrum (both may be
+ * NULL).  d_images: device [n][L][L], n >= 1.  Allocates and frees its own
+ * scratch on `stream` and synchronises it. */
+int ffb_estimate_support(ffb_plan_t plan, const float *d_images, int64_t n, double frac, double sigma2,
+                         double *h_out, double *h_radvar, double *h_radpow, void *stream);
 
 /* Number of kernel launches issued by this plan since creation (for
  * accounting of GPU work).  Launches replayed from a group's CUDA graph are

@@ -272,7 +272,8 @@ def select_filter(plan, lams, mode, K=None, sigma2=None, n=None):
     Marchenko-Pastur edge lambda > sigma^2 (1 + sqrt(gamma_k))^2 with
     gamma_0 = p_0/n, gamma_k = p_k/(2n) (Eq. compselect), h = (lambda -
     sigma^2)/lambda (the soft threshold (lambda - sigma^2)_+ of Sec. V as a
-    per-coefficient Wiener gain).  ``all``: h = 1 everywhere."""
+    per-coefficient Wiener gain); ``mp_hard``: the same selection with h = 1.
+    ``all``: h = 1 everywhere."""
     hs = [np.zeros_like(l) for l in lams]
     if mode == "all":
         return [np.ones_like(l) for l in lams]
@@ -282,12 +283,12 @@ def select_filter(plan, lams, mode, K=None, sigma2=None, n=None):
         for _, k, l in cand[:K]:
             hs[k][l] = 1.0
         return hs
-    if mode == "mp_wiener":
+    if mode in ("mp_wiener", "mp_hard"):
         for k, lam in enumerate(lams):
             gamma = plan.p[k] / n if k == 0 else plan.p[k] / (2.0 * n)
             thr = sigma2 * (1.0 + math.sqrt(gamma)) ** 2
             keep = lam > thr
-            hs[k][keep] = (lam[keep] - sigma2) / lam[keep]
+            hs[k][keep] = 1.0 if mode == "mp_hard" else (lam[keep] - sigma2) / lam[keep]
         return hs
     raise ValueError(mode)
 
@@ -333,3 +334,54 @@ def radial_eigenfunctions(plan, vecs):
         tab = plan.B[k] / (plan.xi * plan.w)[None, :]     # N J_k(R xi_j/c)
         out.append(tab.T @ vecs[k])
     return out
+
+
+# ----------------------------------------------------------------------------
+# SVD route (Sec. III after Eqs. ck, ck_0; Alg. 2 step 4, second alternative)
+# ----------------------------------------------------------------------------
+def svd_route(plan, a):
+    """Eigenpairs of every C^(k) from the SVD of the coefficient matrix:
+    X_k has the rows (Re a_{i,k,.}, Im a_{i,k,.}) for k > 0 and
+    Re a_{i,0,.} - mean for k = 0, so C^(k) = X_k^T X_k / n; its right
+    singular vectors (the left singular vectors of A^(k) as a p_k x n matrix)
+    and s^2 / n are the eigenpairs, descending, signed as in eig_blocks."""
+    a = np.asarray(a)
+    n = a.shape[0]
+    lams, vecs = [], []
+    for k, (o, pk) in enumerate(zip(plan.offset, plan.p)):
+        blk = a[:, o:o + pk]
+        if k == 0:
+            X = blk.real - blk.real.mean(axis=0)
+        else:
+            X = np.concatenate([blk.real, blk.imag], axis=0)
+        _, s, Vt = np.linalg.svd(X, full_matrices=False)
+        lam = s ** 2 / n
+        V = Vt.T
+        if V.shape[1] < pk:              # fewer rows than p_k: the rest has eigenvalue 0
+            Q, _ = np.linalg.qr(np.concatenate([V, np.eye(pk)], axis=1))
+            V = np.concatenate([V, Q[:, V.shape[1]:pk]], axis=1)
+            lam = np.concatenate([lam, np.zeros(pk - len(lam))])
+        piv = np.argmax(np.abs(V), axis=0)
+        sgn = np.sign(V[piv, np.arange(V.shape[1])])
+        sgn[sgn == 0] = 1.0
+        lams.append(lam)
+        vecs.append(V * sgn[None, :])
+    return lams, vecs
+
+
+# ----------------------------------------------------------------------------
+# Rotation-invariant features (Sec. I: bispectrum-like features of the
+# steerable PCA coefficients)
+# ----------------------------------------------------------------------------
+def invariant_features(plan, a, mean0, vecs, pairs, triples):
+    """Power spectrum |c_{k,l}|^2 for the (k, l) in ``pairs`` and bispectrum
+    c_{k1,l1} c_{k2,l2} conj(c_{k1+k2,l3}) for the (k1, l1, k2, l2, l3) in
+    ``triples``, with c the steerable PCA coefficients (Eq. sPCAcoeff).  An
+    in-plane rotation multiplies c_{k,l} by e^{-ik alpha}, which cancels in
+    both; a reflection conjugates c, which leaves the power and conjugates the
+    bispectrum."""
+    c = steerable_coefficients(plan, a, mean0, vecs)
+    pw = np.stack([np.abs(c[k][:, l]) ** 2 for k, l in pairs], axis=1) if pairs else np.zeros((a.shape[0], 0))
+    bs = (np.stack([c[k1][:, l1] * c[k2][:, l2] * np.conj(c[k1 + k2][:, l3]) for k1, l1, k2, l2, l3 in triples],
+                   axis=1) if triples else np.zeros((a.shape[0], 0), complex))
+    return pw, bs

@@ -182,22 +182,24 @@ static void select_gains(ffb_plan_t p, const std::vector<double> &ev, int mode, 
         for (int i = 0; i < K && i < p->P; ++i) h[idx[i]] = 1.0;
         return;
     }
-    // Marchenko-Pastur edge (Eq. compselect) with the Wiener gain (lambda - sigma2)/lambda
+    // Marchenko-Pastur edge (Eq. compselect); gain (lambda - sigma2)/lambda
+    // (Wiener form of the soft threshold) or 1 (hard selection)
     for (int k = 0; k <= p->k_max; ++k) {
         double gamma = (k == 0) ? (double)p->p[k] / (double)n : (double)p->p[k] / (2.0 * (double)n);
         double thr = sigma2 * (1.0 + std::sqrt(gamma)) * (1.0 + std::sqrt(gamma));
         for (int l = 0; l < p->p[k]; ++l) {
             double lam = ev[p->offset[k] + l];
-            if (lam > thr) h[p->offset[k] + l] = (lam - sigma2) / lam;
+            if (lam > thr) h[p->offset[k] + l] = (mode == FFB_DENOISE_MP_HARD) ? 1.0 : (lam - sigma2) / lam;
         }
     }
 }
 
 extern "C" int ffb_select(ffb_plan_t p, int mode, int K, double sigma2, int64_t n, double *h_gain, void *stream) {
     if (!p) return FFB_ERR_ARG;
-    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_ALL) return FFB_ERR_ARG;
+    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_MP_HARD) return FFB_ERR_ARG;
     if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
-    if (mode == FFB_DENOISE_MP_WIENER && (!(sigma2 >= 0.0) || n <= 0)) return FFB_ERR_ARG;
+    if ((mode == FFB_DENOISE_MP_WIENER || mode == FFB_DENOISE_MP_HARD) && (!(sigma2 >= 0.0) || n <= 0))
+        return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (!p->d_gain) CK(ffb_check_cuda(cudaMalloc(&p->d_gain, sizeof(double) * p->P)));
     if (!p->d_M) CK(ffb_check_cuda(cudaMalloc(&p->d_M, sizeof(float) * p->cov_total)));
@@ -229,9 +231,9 @@ extern "C" int ffb_weight(ffb_plan_t p, const float *d_coef_in, int64_t n, float
 extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int mode, int K, double sigma2,
                            float *d_out, void *stream) {
     if (!p || n <= 0 || !d_images || !d_out) return FFB_ERR_ARG;
-    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_ALL) return FFB_ERR_ARG;
+    if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_MP_HARD) return FFB_ERR_ARG;
     if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
-    if (mode == FFB_DENOISE_MP_WIENER && !(sigma2 >= 0.0)) return FFB_ERR_ARG;
+    if ((mode == FFB_DENOISE_MP_WIENER || mode == FFB_DENOISE_MP_HARD) && !(sigma2 >= 0.0)) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->den_cap < n) {
         if (p->d_coef_den) cudaFree(p->d_coef_den);

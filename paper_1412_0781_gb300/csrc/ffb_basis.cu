@@ -6,6 +6,8 @@
 // / ((2 pi c r)^2 - R_{k,q}^2) e^{i k phi}: the phase i^k is the one obtained
 // from the inverse-transform convention of Eq. IPFT (the equation as printed
 // carries i^{-k}).  Both in float64 on the GPU.
+#include <vector>
+
 #include "ffb_internal.cuh"
 
 // one CTA per k: f[offset_k * n_xi + j * p_k + l]
@@ -93,6 +95,118 @@ extern "C" int ffb_eigenimages(ffb_plan_t p, int npairs, const int *h_k, const i
         e = ffb_check_cuda(cudaGetLastError());
     }
     cudaFreeAsync(d_kl, s);
+    if (e) return e;
+    return ffb_check_cuda(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// Rotation-invariant features from the steerable PCA coefficients (the
+// bispectrum-like features mentioned in Sec. I):
+//   power      |c_{k,l}|^2
+//   bispectrum c_{k1,l1} c_{k2,l2} conj(c_{k1+k2,l3})
+// with c_{k,l} = sum_q u^(k)_l(q) (a_{k,q} - mean_q [k = 0]) (Eq. sPCAcoeff).
+// An in-plane rotation by alpha multiplies c_{k,l} by e^{-ik alpha}, which
+// cancels in both; a reflection conjugates every c.
+// ---------------------------------------------------------------------------
+// c[i][s] for the S distinct components (sk[s], sl[s]); thread per (i, s)
+__global__ void k_steer_coef(const float2 *__restrict__ coef, int64_t n, int P, int S, const int *__restrict__ sk,
+                             const int *__restrict__ sl, const double *__restrict__ U, const int *__restrict__ pk_,
+                             const int *__restrict__ off_, const int *__restrict__ cov_off,
+                             const double *__restrict__ mean, float2 *__restrict__ c) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * S) return;
+    const int64_t i = t / S;
+    const int s = (int)(t - i * S);
+    const int k = sk[s], l = sl[s];
+    const int p = pk_[k], o = off_[k];
+    const double *Uk = U + cov_off[k];
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < p; ++q) {
+        const float2 a = coef[i * P + o + q];
+        const double u = Uk[(size_t)q * p + l];
+        re += u * ((k == 0) ? (double)a.x - mean[q] : (double)a.x);
+        im += u * ((k == 0) ? 0.0 : (double)a.y);
+    }
+    c[t] = make_float2((float)re, (float)im);
+}
+
+// features of image i: pow[i][t] = |c_{pi[t]}|^2, bis[i][t] = c_a c_b conj(c_c)
+__global__ void k_invariants(const float2 *__restrict__ c, int64_t n, int S, int npow, const int *__restrict__ pi,
+                             int nbis, const int3 *__restrict__ bi, float *__restrict__ pw, float2 *__restrict__ bs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nf = npow + nbis;
+    if (t >= n * nf) return;
+    const int64_t i = t / nf;
+    const int f = (int)(t - i * nf);
+    const float2 *ci = c + i * S;
+    if (f < npow) {
+        const float2 v = ci[pi[f]];
+        pw[i * npow + f] = v.x * v.x + v.y * v.y;
+    } else {
+        const int3 b = bi[f - npow];
+        const float2 x = ci[b.x], y = ci[b.y], z = ci[b.z];
+        const float2 xy = make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+        bs[i * nbis + (f - npow)] = make_float2(xy.x * z.x + xy.y * z.y, xy.y * z.x - xy.x * z.y);
+    }
+}
+
+extern "C" int ffb_invariants(ffb_plan_t p, const float *d_coef, int64_t n, int npow, const int *h_pairs,
+                              float *d_pow, int nbis, const int *h_triples, float *d_bis, void *stream) {
+    if (!p || !d_coef || n < 0 || npow < 0 || nbis < 0) return FFB_ERR_ARG;
+    if ((npow > 0 && (!h_pairs || !d_pow)) || (nbis > 0 && (!h_triples || !d_bis))) return FFB_ERR_ARG;
+    if (!p->eig_ready) return FFB_ERR_STATE;
+    if (n == 0 || npow + nbis == 0) return FFB_OK;
+    // distinct components, in order of first use
+    std::vector<int> sk, sl, pi(npow);
+    std::vector<int3> bi(nbis);
+    auto comp = [&](int k, int l) -> int {
+        if (k < 0 || k > p->k_max || l < 0 || l >= p->p[k]) return -1;
+        for (size_t s = 0; s < sk.size(); ++s)
+            if (sk[s] == k && sl[s] == l) return (int)s;
+        sk.push_back(k);
+        sl.push_back(l);
+        return (int)sk.size() - 1;
+    };
+    for (int t = 0; t < npow; ++t)
+        if ((pi[t] = comp(h_pairs[2 * t], h_pairs[2 * t + 1])) < 0) return FFB_ERR_ARG;
+    for (int t = 0; t < nbis; ++t) {
+        const int *q = h_triples + 5 * t;
+        const int a = comp(q[0], q[1]), b = comp(q[2], q[3]), c = comp(q[0] + q[2], q[4]);
+        if (a < 0 || b < 0 || c < 0) return FFB_ERR_ARG;
+        bi[t] = make_int3(a, b, c);
+    }
+    const int S = (int)sk.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ints = 2 * (size_t)S + npow + 3 * (size_t)nbis;
+    char *buf = nullptr;
+    const size_t cbytes = sizeof(float2) * (size_t)n * S;
+    int e = ffb_check_cuda(cudaMallocAsync((void **)&buf, cbytes + sizeof(int) * ints + 16, s));
+    if (e) return e;
+    float2 *dc = (float2 *)buf;
+    int *di = (int *)(buf + cbytes);
+    std::vector<int> hi;
+    hi.reserve(ints);
+    hi.insert(hi.end(), sk.begin(), sk.end());
+    hi.insert(hi.end(), sl.begin(), sl.end());
+    hi.insert(hi.end(), pi.begin(), pi.end());
+    for (const int3 &b : bi) {
+        hi.push_back(b.x);
+        hi.push_back(b.y);
+        hi.push_back(b.z);
+    }
+    e = ffb_check_cuda(cudaMemcpyAsync(di, hi.data(), sizeof(int) * ints, cudaMemcpyHostToDevice, s));
+    if (!e) {
+        const int64_t t1 = n * S, t2 = n * (npow + nbis);
+        k_steer_coef<<<(unsigned)((t1 + 255) / 256), 256, 0, s>>>((const float2 *)d_coef, n, p->P, S, di, di + S,
+                                                                   p->d_evecs, p->d_p, p->d_off, p->d_cov_off,
+                                                                   p->d_mean, dc);
+        k_invariants<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(dc, n, S, npow, di + 2 * S, nbis,
+                                                                  (const int3 *)(di + 2 * S + npow), d_pow,
+                                                                  (float2 *)d_bis);
+        p->launches += 2;
+        e = ffb_check_cuda(cudaGetLastError());
+    }
+    cudaFreeAsync(buf, s);
     if (e) return e;
     return ffb_check_cuda(cudaStreamSynchronize(s));
 }

@@ -9,8 +9,9 @@
 // s = t c annihilate a_ij in J^T A J with J = [[c, s], [-s, c]] on (i, j).
 // Disjoint rotations commute, so a round applies all row rotations, then all
 // column rotations (to A and to the eigenvector matrix V).  The sweep count is
-// bounded; a block that does not reach ||offdiag||_F <= 1e-15 ||A||_F latches
-// FFB_ERR_NOT_CONVERGED and still returns its current estimate.
+// bounded; a block that does not reach ||offdiag||_F <= 2.3e-16 pp ||A||_F (a
+// few float64 ulps per element, the floor the rotations' rounding leaves)
+// latches FFB_ERR_NOT_CONVERGED and still returns its current estimate.
 #include "ffb_internal.cuh"
 
 #define EIG_MAXP 200       // A (p+1 stride, float64) must fit in shared memory
@@ -55,8 +56,11 @@ k_jacobi(const double *__restrict__ Cfin, const int *__restrict__ pk_, const int
     }
     const double fro2 = red[0];
     __syncthreads();
+    // ||offdiag||_F <= (2.3e-16 pp) ||A||_F: a few float64 ulps per element,
+    // the level the rotations' rounding leaves behind
+    const double tol2 = (2.3e-16 * pp) * (2.3e-16 * pp) * fro2;
     bool converged = (pp <= 1) || fro2 == 0.0;
-    for (int sweep = 0; sweep < EIG_MAX_SWEEPS && !converged; ++sweep) {
+    for (int sweep = 0; sweep <= EIG_MAX_SWEEPS && !converged; ++sweep) {
         // off-diagonal norm
         loc = 0.0;
         for (int e = tid; e < pp * pp; e += nt) {
@@ -74,10 +78,11 @@ k_jacobi(const double *__restrict__ Cfin, const int *__restrict__ pk_, const int
         }
         const double off2 = red[0];
         __syncthreads();
-        if (off2 <= 1e-30 * fro2) {
+        if (off2 <= tol2) {
             converged = true;
             break;
         }
+        if (sweep == EIG_MAX_SWEEPS) break;   // the state after the last sweep was checked
         for (int round = 0; round < pp - 1; ++round) {
             for (int m = tid; m < pp / 2; m += nt) {
                 int i = pos[m], j = pos[pp - 1 - m];

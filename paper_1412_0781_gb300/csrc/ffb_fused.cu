@@ -42,7 +42,7 @@
 
 #define FUS_WARPS 16                 // warps with FFT buffers (phases 1-2)
 #define FUS_NT 1024                  // threads per CTA; all of them interpolate (phase 3)
-#define RFFT_RB 8
+#define RFFT_RB 32   // rings per ring-FFT CTA (one warp each)
 #define FUS_GB 2048   // nodes per regrouped block (phase 3)
 
 // rows of the shared-memory grid block and its row pitch (complex entries)
@@ -311,38 +311,158 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 // ---------------------------------------------------------------------------
 // ring FFT: F[img][j][l] (l < n_theta/2) -> Fhat[k][img][c][j], k <= k_max,
 // with the conjugate completion of the ring and the 2 pi / n_theta weight.
-// grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads (one warp per ring)
+//
+// One warp per ring, four-step in registers: with n_theta = 32 M, sample
+// l = 32 m + j (lane j) and k = k1 + M k2,
+//   X_k = sum_j W^{j k1} [sum_m s_{32m+j} W_M^{m k1}] W_32^{j k2},  W = e^{-2 pi i / n_theta}.
+// Pass A: each lane loads its M/2 samples (m < M/2) from the polar buffer,
+// completes m >= M/2 with s_{l + n_theta/2} = conj s_l in registers and takes
+// the length-M DFT over m, then the twiddle W^{j k1}.  A transpose through
+// shared memory (row k1, column rotated by k1 R, R = 32/M, so that writes and
+// reads touch 16 distinct bank slots per half warp) gives lane (g = k1, r) the
+// values j = r + R i.  Pass B: the length-32 DFT over j for every k1 as a
+// length-M DFT over i in registers, the twiddle W_32^{r k2'} and a length-R
+// DFT across the R lanes of the group (radix-2 decimation in frequency by XOR
+// shuffles; lane r ends with t = bitreverse(r)), k2 = k2' + M t.  The results
+// with k <= k_max go to a ring-major shared stage and leave as rows of
+// RFFT_RB consecutive rings per (k, re/im) in the quadrature's operand format.
+// grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
 // ---------------------------------------------------------------------------
+template <int M>
+__host__ __device__ constexpr int bitrev_c(int i) {
+    int r = 0;
+    for (int b = 1; b < M; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
+}
+
+// W_16^e = exp(-2 pi i e / 16) for the e a radix-4 x 4 DFT needs
+#define FFB_C1 0.92387953251128676f    // cos(pi/8)
+#define FFB_S1 0.38268343236508977f    // sin(pi/8)
+#define FFB_R2 0.70710678118654752f    // sqrt(1/2)
+__device__ __forceinline__ float2 w16(int e) {
+    switch (e & 15) {
+        case 1: return make_float2(FFB_C1, -FFB_S1);
+        case 2: return make_float2(FFB_R2, -FFB_R2);
+        case 3: return make_float2(FFB_S1, -FFB_C1);
+        case 4: return make_float2(0.f, -1.f);
+        case 6: return make_float2(-FFB_R2, -FFB_R2);
+        case 9: return make_float2(-FFB_C1, FFB_S1);
+        default: return make_float2(1.f, 0.f);
+    }
+}
+
+// in-register length-M DFT, natural order in and out (forward)
+template <int M>
+__device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
+    if constexpr (M == 4) {
+        dft4<false>(x);
+    } else if constexpr (M == 8) {
+        float2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
+        dft4<false>(e);
+        dft4<false>(o);
+        const float2 w[4] = {make_float2(1.f, 0.f), make_float2(FFB_R2, -FFB_R2), make_float2(0.f, -1.f),
+                             make_float2(-FFB_R2, -FFB_R2)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 t = (k == 0) ? o[0] : cmul(o[k], w[k]);
+            x[k] = cadd(e[k], t);
+            x[k + 4] = csub(e[k], t);
+        }
+    } else {
+        static_assert(M == 16, "M in {4, 8, 16}");
+        float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 v[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+            dft4<false>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 * k1 == 0) ? v[k1] : cmul(v[k1], w16(n2 * k1));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 v[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            dft4<false>(v);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
+        }
+    }
+}
+
 template <int NTH, int FMT>
-__global__ void __launch_bounds__(32 * RFFT_RB)
+__global__ void __launch_bounds__(32 * RFFT_RB, 1)
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
            void *__restrict__ out0, void *__restrict__ out1, int ld) {
+    constexpr int M = NTH / 32;      // samples per lane
+    constexpr int R = 32 / M;        // lanes per length-32 DFT of pass B
     constexpr int NH = NTH / 2;
+    static_assert(M >= 2 && M <= 16 && M * R == 32, "n_theta in {64, 128, 256, 512}");
     extern __shared__ float2 smr[];
-    float2 *ringA = smr;                    // [RFFT_RB][NTH]
-    float2 *ringB = smr + RFFT_RB * NTH;    // [RFFT_RB][NTH]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *tb = smr + warp * (M * 32);                  // this warp's transpose buffer [M][32]
+    float *ost = (float *)(smr + RFFT_RB * M * 32);      // [RFFT_RB][ostld]: ring-major stage
+    const int ostld = (2 * (kmax + 1)) | 1;              // odd: the write-out reads conflict-free
     const int img = blockIdx.y;
     const int j0 = blockIdx.x * RFFT_RB;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float2 *src = Fpol + ((size_t)img * n_xi + j0) * NH;
-    const int nrings = min(RFFT_RB, n_xi - j0);
-    for (int t = threadIdx.x; t < nrings * NH; t += 32 * RFFT_RB) {
-        const int jj = t / NH, l = t - jj * NH;
-        const float2 v = src[(size_t)jj * NH + l];
-        ringA[jj * NTH + swz(l)] = v;
-        ringA[jj * NTH + swz(l + NH)] = cconj(v);
+    const int ring = j0 + warp;
+    const float scale = 6.283185307179586f / (float)NTH;
+    if (ring < n_xi) {
+        const float2 *src = Fpol + ((size_t)img * n_xi + ring) * NH;
+        float2 x[M];
+#pragma unroll
+        for (int m = 0; m < M / 2; ++m) {
+            x[m] = src[32 * m + lane];
+            x[m + M / 2] = cconj(x[m]);
+        }
+        dft_reg<M>(x);                         // pass A: over m
+#pragma unroll
+        for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twT[(lane * k1) & (NTH - 1)]));
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) tb[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
+        __syncwarp();
+        const int g = lane / R, r = lane % R;
+        float2 y[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = tb[g * 32 + ((r + R * i + g * R) & 31)];
+        dft_reg<M>(y);                         // pass B, part 1: over i
+#pragma unroll
+        for (int k2 = 1; k2 < M; ++k2) y[k2] = cmul(y[k2], __ldg(&twT[(r * k2 * (NTH / 32)) & (NTH - 1)]));
+#pragma unroll
+        for (int h = R / 2; h >= 1; h >>= 1) {           // pass B, part 2: across the R lanes
+            const bool up = (r & h) != 0;
+            const float2 w = __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]);
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
+                                              __shfl_xor_sync(0xffffffffu, y[k2].y, h));
+                y[k2] = up ? cmul(csub(pv, y[k2]), w) : cadd(y[k2], pv);
+            }
+        }
+        int t = 0;
+        for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
+        float *row = ost + warp * ostld;
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const int k = g + M * (k2 + M * t);
+            if (k <= kmax) {
+                row[2 * k] = scale * y[k2].x;
+                row[2 * k + 1] = scale * y[k2].y;
+            }
+        }
     }
     __syncthreads();
-    if (warp < nrings) warp_fft_pow2<NTH, false>(ringA + warp * NTH, ringB + warp * NTH, twT, lane);
-    __syncthreads();
-    const float2 *res = fft_pow2_result_in_b<NTH>() ? ringB : ringA;
-    const float scale = 6.283185307179586f / (float)NTH;
-    for (int t = threadIdx.x; t < (kmax + 1) * 2 * RFFT_RB; t += 32 * RFFT_RB) {
-        const int jj = t % RFFT_RB, cc = (t / RFFT_RB) & 1, k = t / (2 * RFFT_RB);
-        if (jj < nrings) {
-            const float2 v = res[jj * NTH + swz(k)];
-            const float x = scale * (cc ? v.y : v.x);
-            const size_t idx = (((size_t)k * chunk + img) * 2 + cc) * ld + j0 + jj;
+    // write-out: thread t owns ring jj = t % RFFT_RB and (k, re/im) rows
+    // kc = t / RFFT_RB + (32 RFFT_RB / RFFT_RB) it; consecutive rows of one
+    // thread are 16 k apart, i.e. a fixed stride in the plane
+    const int nr = min(RFFT_RB, n_xi - j0);
+    const int jj = threadIdx.x % RFFT_RB;
+    constexpr int KCSTEP = (32 * RFFT_RB) / RFFT_RB;     // 32: even, so re/im of a row is fixed per thread
+    const int kc0 = threadIdx.x / RFFT_RB;
+    const int kcend = 2 * (kmax + 1);
+    if (jj < nr) {
+        size_t idx = (((size_t)(kc0 >> 1) * chunk + img) * 2 + (kc0 & 1)) * ld + j0 + jj;
+        const size_t step = (size_t)(KCSTEP / 2) * chunk * 2 * ld;
+        for (int kc = kc0; kc < kcend; kc += KCSTEP, idx += step) {
+            const float x = ost[jj * ostld + kc];
             if (FMT == FFB_FMT_F32) {
                 ((float *)out0)[idx] = x;
             } else if (FMT == FFB_FMT_TF32 || FMT == FFB_FMT_TF32X2) {
@@ -389,7 +509,8 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
 bool ffb_fused_supported(ffb_plan_t p) {
     if (p->L * 2 != p->N || p->w != 8) return false;
     if (!(p->N == 128 || p->N == 256)) return false;
-    if (!(p->n_theta == 128 || p->n_theta == 256 || p->n_theta == 512 || p->n_theta == 1024)) return false;
+    if (!(p->n_theta == 128 || p->n_theta == 256 || p->n_theta == 512)) return false;
+    if (p->k_max >= p->n_theta / 2) return false;
     if (p->L % 32) return false;
     const size_t smem = (p->N == 256) ? fused_smem<256, 8>() : fused_smem<128, 8>();
     int dev = 0, optin = 0;
@@ -469,7 +590,7 @@ int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int 
 template <int NTH, int FMT>
 static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
     static int attr = 0;
-    const size_t smem = sizeof(float2) * 2 * RFFT_RB * (size_t)NTH;
+    const size_t smem = sizeof(float2) * RFFT_RB * (size_t)NTH + sizeof(float) * RFFT_RB * ((2 * (p->k_max + 1)) | 1);
     if (smem > 48 * 1024 && attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_fft<NTH, FMT>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -500,7 +621,6 @@ int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &
         case 128: return launch_ring<128>(p, m, Fpol, o, s);
         case 256: return launch_ring<256>(p, m, Fpol, o, s);
         case 512: return launch_ring<512>(p, m, Fpol, o, s);
-        case 1024: return launch_ring<1024>(p, m, Fpol, o, s);
         default: return FFB_ERR_UNSUPPORTED;
     }
 }

@@ -18,7 +18,7 @@ STATUS = {0: "FFB_OK", -1: "FFB_ERR_ARG", -2: "FFB_ERR_CUDA", -3: "FFB_ERR_OOM",
           -4: "FFB_ERR_NONFINITE", -5: "FFB_ERR_NOT_CONVERGED", -6: "FFB_ERR_TIMEOUT",
           -7: "FFB_ERR_STATE", -8: "FFB_ERR_UNSUPPORTED"}
 PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
-DENOISE = {"topk": 0, "mp_wiener": 1, "all": 2}
+DENOISE = {"topk": 0, "mp_wiener": 1, "all": 2, "mp_hard": 3}
 
 # every symbol declared in include/ffb.h, with (restype, argtypes)
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -52,6 +52,9 @@ SIGNATURES = {
     "ffb_profile": (_i, [_vp, _i]),
     "ffb_profile_read": (_i, [_vp, _pd, ctypes.POINTER(ctypes.c_int64)]),
     "ffb_launch_count": (_i64, [_vp]),
+    "ffb_estimate_support": (_i, [_vp, _vp, _i64, _d, _d, _pd, _pd, _pd, _vp]),
+    "ffb_svd": (_i, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "ffb_invariants": (_i, [_vp, _vp, _i64, _i, _pi, _vp, _i, _pi, _vp, _vp]),
     "ffb_group_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), _vp]),
     "ffb_group_destroy": (_i, [_vp]),
     "ffb_group_expand_cov": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int64),
@@ -257,6 +260,27 @@ class Plan:
                               _stream(stream)), "ffb_eig")
         return ev, U
 
+    def svd(self, coef, device="cuda", stream=None):
+        """Eigenpairs by the SVD route (ffb_svd): (evals [P], evecs packed)."""
+        ev = torch.empty(self.P, dtype=torch.float64, device=device)
+        U = torch.empty(self.cov_total, dtype=torch.float64, device=device)
+        _check(load().ffb_svd(self._h, _ptr(coef, torch.float32, "coef"), coef.shape[0], _ptr(ev, torch.float64, "ev"),
+                              _ptr(U, torch.float64, "U"), _stream(stream)), "ffb_svd")
+        return ev, U
+
+    def invariants(self, coef, pairs=(), triples=(), stream=None):
+        """Rotation-invariant features (ffb_invariants): power [n, len(pairs)]
+        and bispectrum [n, len(triples), 2]."""
+        n = coef.shape[0]
+        pw = torch.empty((n, len(pairs)), dtype=torch.float32, device=coef.device)
+        bs = torch.empty((n, len(triples), 2), dtype=torch.float32, device=coef.device)
+        hp = (ctypes.c_int * max(1, 2 * len(pairs)))(*[v for pr in pairs for v in pr])
+        ht = (ctypes.c_int * max(1, 5 * len(triples)))(*[v for tr in triples for v in tr])
+        _check(load().ffb_invariants(self._h, _ptr(coef, torch.float32, "coef"), n, len(pairs), hp,
+                                     ctypes.c_void_p(pw.data_ptr()), len(triples), ht,
+                                     ctypes.c_void_p(bs.data_ptr()), _stream(stream)), "ffb_invariants")
+        return pw, bs
+
     def eig_blocks(self, C, stream=None):
         """Synchronising: Jacobi eigenpairs of caller-supplied packed blocks."""
         ev = torch.empty(self.P, device=C.device, dtype=torch.float64)
@@ -328,6 +352,23 @@ class Plan:
 
     def sync(self, stream=None):
         _check(load().ffb_sync(self._h, _stream(stream)), "ffb_sync")
+
+    def estimate_support(self, images, frac=0.999, sigma2=None, stream=None):
+        """R, c and the noise variance of a stack (see ffb_estimate_support);
+        returns a dict with the radial variance and radial power profiles."""
+        import numpy as np
+        n = images.shape[0]
+        if tuple(images.shape[1:]) != (self.L, self.L):
+            raise ValueError("images must be [n, L, L]")
+        out = np.zeros(4)
+        rv = np.zeros(self.L // 2)
+        rp = np.zeros(self.n_xi)
+        _check(load().ffb_estimate_support(self._h, _ptr(images, torch.float32, "images"), n, float(frac),
+                                           -1.0 if sigma2 is None else float(sigma2),
+                                           out.ctypes.data_as(_pd), rv.ctypes.data_as(_pd),
+                                           rp.ctypes.data_as(_pd), _stream(stream)), "ffb_estimate_support")
+        return {"R": out[0], "c": out[1], "sigma2": out[2], "c_index": int(out[3]),
+                "radial_variance": rv, "radial_power": rp}
 
     # -- helpers for packed outputs ----------------------------------------
     def unpack_blocks(self, packed):

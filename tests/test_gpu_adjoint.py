@@ -107,13 +107,14 @@ def test_denoise_topk_matches_oracle(dev):
     assert np.linalg.norm(out - c) < 0.7 * np.linalg.norm(x - c)
 
 
-def test_denoise_mp_wiener_matches_oracle(dev):
+@pytest.mark.parametrize("mode", ["mp_wiener", "mp_hard"])
+def test_denoise_mp_matches_oracle(dev, mode):
     spec = data.TINY
     imgs, _, sigma2 = data.blob_stack(spec)
     gp, op = gplan(spec.L), fb.make_plan(spec.L, spec.c, spec.R)
     x = imgs.double().numpy()
-    out = gp.denoise(imgs.to(dev), mode="mp_wiener", sigma2=sigma2).double().cpu().numpy()
-    ref = fb.denoise(op, x, "mp_wiener", sigma2=sigma2)
+    out = gp.denoise(imgs.to(dev), mode=mode, sigma2=sigma2).double().cpu().numpy()
+    ref = fb.denoise(op, x, mode, sigma2=sigma2)
     assert rel(out, ref) <= TOL
 
 

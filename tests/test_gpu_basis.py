@@ -78,3 +78,58 @@ def test_eigenimages_reject_bad_pairs(setup):
         gp.eigenimages([(gp.k_max + 1, 0)])
     with pytest.raises(FFBError):
         gp.eigenimages([(0, gp.p[0])])
+
+
+def _rotate90(x):
+    """I'(i1, i2) = I(i2, -i1) on the grid i = a - L/2 (as in the oracle
+    pins): row a1 >= 1 of the result is column L - a1 of the input, row 0
+    (i1 = -L/2, whose image -i1 = L/2 is off the grid) is zero."""
+    L = x.shape[-1]
+    out = torch.zeros_like(x)
+    cols = L - torch.arange(1, L, device=x.device)
+    out[:, 1:, :] = x[:, :, cols].transpose(1, 2)
+    return out
+
+
+PAIRS = [(0, 0), (1, 0), (2, 0), (3, 0), (1, 1)]
+TRIPLES = [(1, 0, 1, 0, 0), (1, 0, 2, 0, 0), (1, 0, 0, 0, 0), (2, 0, 1, 0, 0)]
+
+
+def test_invariant_features_match_oracle(setup):
+    gp, op, _, _ = setup
+    spec = data.TINY
+    imgs, _, _ = data.blob_stack(spec)
+    coef = gp.expand(imgs.to("cuda:0"))
+    pw, bs = gp.invariants(coef, PAIRS, TRIPLES)
+    a = fb.expand(op, imgs.double().numpy())
+    mean0, blocks = fb.covariance(op, a)
+    _, vecs = fb.eig_blocks(blocks)
+    rp, rb = fb.invariant_features(op, a, mean0, vecs, PAIRS, TRIPLES)
+    gb = bs.cpu().double().numpy()
+    gb = gb[..., 0] + 1j * gb[..., 1]
+    ep = np.linalg.norm(pw.cpu().double().numpy() - rp) / np.linalg.norm(rp)
+    eb = np.linalg.norm(gb - rb) / np.linalg.norm(rb)
+    print("invariant features vs oracle: power %.2e, bispectrum %.2e" % (ep, eb))
+    assert ep <= 1e-4 and eb <= 1e-4
+
+
+def test_invariant_features_are_rotation_invariant_on_gpu(setup):
+    gp, _, _, _ = setup
+    spec = data.TINY
+    imgs, _, _ = data.blob_stack(spec, n=64)
+    # a 90-degree rotation is exact on the grid for images that vanish for
+    # r >= R (Eqs. rot, refl); the stack's noise covers every pixel
+    x = (imgs * data.support_mask(spec.L, spec.R)).to("cuda:0").contiguous()
+    pw, bs = gp.invariants(gp.expand(x), PAIRS, TRIPLES)
+    pr, br = gp.invariants(gp.expand(_rotate90(x)), PAIRS, TRIPLES)
+    assert float((pr - pw).norm() / pw.norm()) <= 1e-5
+    assert float((br - bs).norm() / bs.norm()) <= 1e-5
+
+
+def test_invariant_features_reject_bad_indices(setup):
+    gp, _, _, _ = setup
+    coef = torch.zeros((2, gp.P, 2), device="cuda:0")
+    with pytest.raises(FFBError):
+        gp.invariants(coef, [(gp.k_max + 1, 0)])
+    with pytest.raises(FFBError):
+        gp.invariants(coef, [], [(gp.k_max, 0, 1, 0, 0)])

@@ -401,3 +401,49 @@ def test_denoise_all_components_is_projection():
     out = fb.denoise(p, I, "all")
     ref = fb.synthesize(p, fb.expand(p, I))
     assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_svd_route_equals_covariance_eigenpairs():
+    """Sec. III: the left singular vectors of A^(k) are the eigenvectors of
+    C^(k) and s^2/n its eigenvalues.  The oracle's SVD route (LAPACK SVD of the
+    stacked real matrix) against its covariance route (two-pass covariance,
+    LAPACK symmetric eigensolver): two different algorithms on the same data."""
+    plan = fb.make_plan(24, 0.5, 12.0)
+    rng = np.random.default_rng(8)
+    n = 90
+    a = rng.standard_normal((n, plan.P)) + 1j * rng.standard_normal((n, plan.P))
+    a *= np.linspace(2.0, 0.5, plan.P)[None, :]
+    a[:, :plan.p[0]] = a[:, :plan.p[0]].real + 0.3
+    _, blocks = fb.covariance(plan, a)
+    lc, uc = fb.eig_blocks(blocks)
+    ls, us = fb.svd_route(plan, a)
+    for k in range(len(plan.p)):
+        assert np.max(np.abs(lc[k] - ls[k])) <= 1e-12 * max(1.0, lc[k].max())
+        # compare the spectral projectors (robust to near-degenerate pairs)
+        Pc = uc[k] @ np.diag(lc[k]) @ uc[k].T
+        Ps = us[k] @ np.diag(ls[k]) @ us[k].T
+        assert np.max(np.abs(Pc - Ps)) <= 1e-12 * max(1.0, lc[k].max())
+
+
+def test_invariant_features_under_rotation_and_reflection():
+    """Exact 90-degree rotations and the reflection of the grid (Eqs. rot, refl)
+    leave the power spectrum of the steerable coefficients unchanged and
+    leave (rotation) or conjugate (reflection) the bispectrum -- checked on the
+    images themselves, through the whole expansion."""
+    L = 24
+    plan = fb.make_plan(L, 0.5, L / 2)
+    I = _masked_noise(L, L // 2, 40, 21)
+    a = fb.expand(plan, I)
+    mean0, blocks = fb.covariance(plan, a)
+    _, vecs = fb.eig_blocks(blocks)
+    pairs = [(0, 0), (1, 0), (2, 1), (5, 0)]
+    triples = [(1, 0, 1, 0, 0), (1, 0, 2, 1, 0), (2, 0, 3, 0, 1), (0, 1, 4, 0, 0)]
+    pw, bs = fb.invariant_features(plan, a, mean0, vecs, pairs, triples)
+    ar = fb.expand(plan, _rotate90(I))                     # exact on the pixel grid
+    pwr, bsr = fb.invariant_features(plan, ar, mean0, vecs, pairs, triples)
+    assert np.max(np.abs(pwr - pw)) <= 1e-10 * np.max(np.abs(pw))
+    assert np.max(np.abs(bsr - bs)) <= 1e-10 * np.max(np.abs(bs))
+    af = fb.expand(plan, _reflect(I))
+    pwf, bsf = fb.invariant_features(plan, af, mean0, vecs, pairs, triples)
+    assert np.max(np.abs(pwf - pw)) <= 1e-10 * np.max(np.abs(pw))
+    assert np.max(np.abs(bsf - np.conj(bs))) <= 1e-10 * np.max(np.abs(bs))
