@@ -40,8 +40,8 @@
 
 #include "ffb_internal.cuh"
 
-#define FUS_WARPS 16                 // warps with FFT buffers (phases 1-2)
-#define FUS_NT 1024                  // threads per CTA; all of them interpolate (phase 3)
+#define FUS_WARPS 32                 // warps per CTA, each with an N-entry FFT buffer
+#define FUS_NT (32 * FUS_WARPS)      // threads per CTA
 #define RFFT_RB 32   // rings per ring-FFT CTA (one warp each)
 #define FUS_GB 2048   // nodes per regrouped block (phase 3)
 
@@ -50,108 +50,155 @@ __host__ __device__ constexpr int fus_mh(int N, int W) { return N / 2 + 1 + 2 * 
 __host__ __device__ constexpr int fus_sld(int N, int W) { return (fus_mh(N, W) > N / 2) ? fus_mh(N, W) : N / 2; }
 
 // ---------------------------------------------------------------------------
-// Stockham FFT of compile-time power-of-two length by one warp (radix 4,
-// then one radix-2 stage when log2(N) is odd).  Same pass structure as
-// smem_fft, with every division and modulo by a power of two.
-//
-// The buffers are addressed through swz(i) = i ^ (5 ((i >> 4) & 3)): with
-// t = bits 4-5 of the complex index, the low nibble is XORed with (t, t).
-// A radix-4 stage with Ns = 1 stores a half warp's outputs at i = 4j + r
-// (j = lane, bits 2-5) and one with Ns = 4 at i = 16(j/4) + j%4 + 4r; without
-// the swizzle four lanes share each 8-byte bank slot (i mod 16); with it the
-// 16 lanes of every store land on 16 distinct slots, and runs of consecutive
-// indices (all loads, the Ns >= 16 stores) stay distinct as well.  Every
-// access to a buffer handed to warp_fft_pow2 goes through swz().
-__device__ __forceinline__ int swz(int i) { return i ^ (5 * ((i >> 4) & 3)); }
-
-template <int N, bool INV, int FIRST = 0>
-__device__ __forceinline__ float2 *warp_fft_pow2(float2 *a, float2 *b, const float2 *__restrict__ tw, int lane) {
-    constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9 : (N == 1024) ? 10 : -1;
-    static_assert(LOG > 0, "power-of-two length 64..1024");
-    constexpr int N4 = LOG / 2;           // radix-4 stages
-    constexpr bool TAIL2 = (LOG & 1);     // one radix-2 stage
-#pragma unroll
-    for (int s = FIRST; s < N4; ++s) {
-        const int Ns = 1 << (2 * s);
-        constexpr int nb = N / 4;
-        const int tshift = LOG - 2 * s - 2;   // tstep = N / (Ns * 4)
-#pragma unroll
-        for (int jj = 0; jj < nb / 32; ++jj) {
-            const int j = lane + 32 * jj;
-            const int k = j & (Ns - 1);
-            float2 v[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) v[r] = a[swz(j + r * nb)];
-#pragma unroll
-            for (int r = 1; r < 4; ++r) {
-                float2 wv = __ldg(&tw[((r * k) << tshift) & (N - 1)]);
-                if (INV) wv.y = -wv.y;
-                v[r] = cmul(v[r], wv);
-            }
-            dft4<INV>(v);
-            const int base = ((j >> (2 * s)) << (2 * s + 2)) + k;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) b[swz(base + r * Ns)] = v[r];
-        }
-        __syncwarp();
-        float2 *t = a;
-        a = b;
-        b = t;
-    }
-    if (TAIL2) {
-        constexpr int Ns = 1 << (2 * N4);
-        constexpr int nb = N / 2;
-#pragma unroll
-        for (int jj = 0; jj < nb / 32; ++jj) {
-            const int j = lane + 32 * jj;
-            const int k = j & (Ns - 1);
-            float2 v[2];
-            v[0] = a[swz(j)];
-            v[1] = a[swz(j + nb)];
-            float2 wv = __ldg(&tw[k & (N - 1)]);  // tstep = 1
-            if (INV) wv.y = -wv.y;
-            v[1] = cmul(v[1], wv);
-            dft2<INV>(v);
-            const int base = ((j / Ns) * Ns * 2) + k;
-            b[swz(base)] = v[0];
-            b[swz(base + Ns)] = v[1];
-        }
-        __syncwarp();
-        float2 *t = a;
-        a = b;
-        b = t;
-    }
-    return a;
+// Register FFTs.  dft_reg<M>: a length-M DFT held in one thread's registers
+// (M = 4, 8, 16; radix 4 with constant twiddles).
+// ---------------------------------------------------------------------------
+template <int M>
+__host__ __device__ constexpr int bitrev_c(int i) {
+    int r = 0;
+    for (int b = 1; b < M; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
 }
 
-// true when warp_fft_pow2<N> leaves its result in the second buffer
-template <int N>
-__host__ __device__ constexpr bool fft_pow2_result_in_b() {
-    return (((N == 64) ? 3 : (N == 128) ? 4 : (N == 256) ? 4 : (N == 512) ? 5 : 5) & 1) != 0;
+// W_16^e = exp(-2 pi i e / 16) for the e a radix-4 x 4 DFT needs
+#define FFB_C1 0.92387953251128676f    // cos(pi/8)
+#define FFB_S1 0.38268343236508977f    // sin(pi/8)
+#define FFB_R2 0.70710678118654752f    // sqrt(1/2)
+__device__ __forceinline__ float2 w16(int e) {
+    switch (e & 15) {
+        case 1: return make_float2(FFB_C1, -FFB_S1);
+        case 2: return make_float2(FFB_R2, -FFB_R2);
+        case 3: return make_float2(FFB_S1, -FFB_C1);
+        case 4: return make_float2(0.f, -1.f);
+        case 6: return make_float2(-FFB_R2, -FFB_R2);
+        case 9: return make_float2(-FFB_C1, FFB_S1);
+        default: return make_float2(1.f, 0.f);
+    }
 }
 
+// in-register length-M DFT, natural order in and out (forward)
+template <int M>
+__device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
+    if constexpr (M == 4) {
+        dft4<false>(x);
+    } else if constexpr (M == 8) {
+        float2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
+        dft4<false>(e);
+        dft4<false>(o);
+        const float2 w[4] = {make_float2(1.f, 0.f), make_float2(FFB_R2, -FFB_R2), make_float2(0.f, -1.f),
+                             make_float2(-FFB_R2, -FFB_R2)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 t = (k == 0) ? o[0] : cmul(o[k], w[k]);
+            x[k] = cadd(e[k], t);
+            x[k + 4] = csub(e[k], t);
+        }
+    } else {
+        static_assert(M == 16, "M in {4, 8, 16}");
+        float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 v[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+            dft4<false>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 * k1 == 0) ? v[k1] : cmul(v[k1], w16(n2 * k1));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 v[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            dft4<false>(v);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Length-N forward DFT of a sequence whose only nonzeros are the L = N/2
-// values placed at (a - L/2) mod N, a = lane + 32 q (q < N/64), given in z[q]:
-// they occupy [0, N/4) and [3N/4, N).  Every radix-4 butterfly of the first
-// Stockham stage (Ns = 1, inputs j, j + N/4, j + N/2, j + 3N/4) then has two
-// zero inputs and its two nonzero ones in the same lane (z[N/128 + jj] at j,
-// z[jj] at j + 3N/4 for j = lane + 32 jj), so that stage runs from registers
-// and the remaining stages continue in shared memory.
+// values placed at (a - L/2) mod N, a = lane + 32 q, given in z[q] (N = 128,
+// 256), by one warp as a four-step FFT.  With N = 32 M, index l = 32 m + j
+// (lane j) and k = k1 + M k2:
+//   X_k = sum_j W^{j k1} [sum_m s_{32m+j} W_M^{m k1}] W_32^{j k2},  W = e^{-2 pi i/N}.
+// The nonzeros sit at m in {0, 1, M-2, M-1} (N = 256) or {0, M-1} (N = 128),
+// so the length-M DFT over m starts from two half-zero length-4 DFTs
+// (a + d i^k for inputs (a, 0, 0, d)).  After the twiddle W^{j k1}, one
+// transpose through the warp's buffer (row k1, column rotated by k1 R,
+// R = 32/M: conflict-free) gives lane (g = k1, r) the values j = r + R i;
+// a length-M DFT over i, the twiddle W_32^{r k2'} and a length-R DFT across
+// the group's lanes (radix-2 decimation in frequency by XOR shuffles, lane r
+// ends with t = bitreverse(r)) give X_k, k = g + M (k2' + M t).  X is left in
+// the buffer in natural order at position fswz<N>(k): the XOR with the bits
+// above M^2 spreads the lanes of one write over 16 bank slots, and runs of
+// consecutive k stay contiguous for the readers.
+// ---------------------------------------------------------------------------
 template <int N>
-__device__ __forceinline__ float2 *warp_fft_halfzero(const float2 *z, float2 *a, float2 *b,
-                                                     const float2 *__restrict__ tw, int lane) {
+__device__ __forceinline__ int fswz(int k) {
+    return (N == 256) ? (k ^ ((k >> 6) << 2)) : (k ^ ((k >> 4) << 1));
+}
+
+template <int N>
+__device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, const float2 *__restrict__ tw,
+                                                  int lane) {
+    static_assert(N == 128 || N == 256, "N in {128, 256}");
+    constexpr int M = N / 32, R = 32 / M;
+    float2 x[M];
+    if constexpr (N == 256) {
+        // z[2], z[3] at m = 0, 1; z[0], z[1] at m = 6, 7: even-m DFT4 of
+        // (z2, 0, 0, z0) in x[0..3], odd-m DFT4 of (z3, 0, 0, z1) in x[4..7]
+        {
+            const float2 a = z[2], d = z[0];
+            x[0] = cadd(a, d); x[1] = make_float2(a.x - d.y, a.y + d.x);
+            x[2] = csub(a, d); x[3] = make_float2(a.x + d.y, a.y - d.x);
+        }
+        {
+            const float2 b = z[3], e = z[1];
+            x[4] = cadd(b, e); x[5] = make_float2(b.x - e.y, b.y + e.x);
+            x[6] = csub(b, e); x[7] = make_float2(b.x + e.y, b.y - e.x);
+        }
 #pragma unroll
-    for (int jj = 0; jj < N / 128; ++jj) {
-        const int j = lane + 32 * jj;
-        const float2 v0 = z[N / 128 + jj], v3 = z[jj];
-        // dft4 of (v0, 0, 0, v3), forward: (v0 + v3, v0 + i v3, v0 - v3, v0 - i v3)
-        a[swz(4 * j + 0)] = cadd(v0, v3);
-        a[swz(4 * j + 1)] = make_float2(v0.x - v3.y, v0.y + v3.x);
-        a[swz(4 * j + 2)] = csub(v0, v3);
-        a[swz(4 * j + 3)] = make_float2(v0.x + v3.y, v0.y - v3.x);
+        for (int k = 0; k < 4; ++k) {   // radix-2 combination with W8^k
+            float2 t = x[k + 4];
+            if (k == 1) t = make_float2(FFB_R2 * (t.x + t.y), FFB_R2 * (t.y - t.x));
+            if (k == 2) t = make_float2(t.y, -t.x);
+            if (k == 3) t = make_float2(FFB_R2 * (t.y - t.x), -FFB_R2 * (t.x + t.y));
+            const float2 e0 = x[k];
+            x[k] = cadd(e0, t);
+            x[k + 4] = csub(e0, t);
+        }
+    } else {
+        // z[1] at m = 0, z[0] at m = 3
+        const float2 a = z[1], d = z[0];
+        x[0] = cadd(a, d); x[1] = make_float2(a.x - d.y, a.y + d.x);
+        x[2] = csub(a, d); x[3] = make_float2(a.x + d.y, a.y - d.x);
     }
+#pragma unroll
+    for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&tw[(lane * k1) & (N - 1)]));
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) buf[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
     __syncwarp();
-    return warp_fft_pow2<N, false, 1>(a, b, tw, lane);
+    const int g = lane / R, r = lane % R;
+#pragma unroll
+    for (int i = 0; i < M; ++i) x[i] = buf[g * 32 + ((r + R * i + g * R) & 31)];
+    __syncwarp();
+    dft_reg<M>(x);
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) x[k2] = cmul(x[k2], __ldg(&tw[(r * k2 * (N / 32)) & (N - 1)]));
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+        const bool up = (r & h) != 0;
+        const float2 w = __ldg(&tw[(r & (h - 1)) * (N / (2 * h))]);
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, x[k2].x, h),
+                                          __shfl_xor_sync(0xffffffffu, x[k2].y, h));
+            x[k2] = up ? cmul(csub(pv, x[k2]), w) : cadd(x[k2], pv);
+        }
+    }
+    int t = 0;
+    for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) buf[fswz<N>(g + M * (k2 + M * t))] = x[k2];
+    __syncwarp();
 }
 
 template <int N, int W>
@@ -164,19 +211,18 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
     constexpr int SLD = fus_sld(N, W);            // row length of S
-    static_assert(2 * FUS_GB <= FUS_WARPS * 2 * N, "phase-3 staging must fit in the warp buffers");
+    static_assert(2 * FUS_GB <= FUS_WARPS * N, "phase-3 staging must fit in the warp buffers");
     extern __shared__ float2 smz[];
     float2 *S = smz;                               // [MH][SLD]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *bufA = smz + MH * SLD + (warp < FUS_WARPS ? warp : 0) * 2 * N;   // FFT warps only
-    float2 *bufB = bufA + N;
+    float2 *buf = smz + MH * SLD + warp * N;   // this warp's FFT buffer
     const int half = blockIdx.x;
     const int img = blockIdx.y;
     const float *im = images + (size_t)img * L * L;
 
     // ---- phase 1: row transforms (two pixel rows per complex FFT) --------
     bool bad = false;
-    for (int rp = warp; warp < FUS_WARPS && rp < L / 2; rp += FUS_WARPS) {
+    for (int rp = warp; rp < L / 2; rp += FUS_WARPS) {
         const int a1 = 2 * rp;
         float x[L / 32], y[L / 32];
 #pragma unroll
@@ -193,11 +239,11 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             const float ca = corr[a2];
             z[q] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
         }
-        const float2 *X = warp_fft_halfzero<N>(z, bufA, bufB, tw, lane);
+        warp_fft_halfzero<N>(z, buf, tw, lane);
         for (int e = lane; e < MH; e += 32) {
             const int m = (e - H) & (N - 1);
-            const float2 Z = X[swz(m)];
-            const float2 Zc = cconj(X[swz((N - m) & (N - 1))]);
+            const float2 Z = buf[fswz<N>(m)];
+            const float2 Zc = cconj(buf[fswz<N>((N - m) & (N - 1))]);
             const float2 D = csub(Z, Zc);
             S[e * SLD + a1] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
             S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
@@ -209,13 +255,13 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 
     // ---- phase 2: column transforms, in place per row of S ---------------
     const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-    for (int e = warp; warp < FUS_WARPS && e < MH; e += FUS_WARPS) {
+    for (int e = warp; e < MH; e += FUS_WARPS) {
         float2 *row = S + e * SLD;
         float2 z[L / 32];
 #pragma unroll
         for (int q = 0; q < L / 32; ++q) z[q] = row[lane + 32 * q];
-        const float2 *X = warp_fft_halfzero<N>(z, bufA, bufB, tw, lane);
-        for (int c = lane; c < MH; c += 32) row[c] = X[swz((c + m1lo) & (N - 1))];
+        warp_fft_halfzero<N>(z, buf, tw, lane);
+        for (int c = lane; c < MH; c += 32) row[c] = buf[fswz<N>((c + m1lo) & (N - 1))];
         __syncwarp();
     }
     __syncthreads();
@@ -328,66 +374,6 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 // RFFT_RB consecutive rings per (k, re/im) in the quadrature's operand format.
 // grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
 // ---------------------------------------------------------------------------
-template <int M>
-__host__ __device__ constexpr int bitrev_c(int i) {
-    int r = 0;
-    for (int b = 1; b < M; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
-    return r;
-}
-
-// W_16^e = exp(-2 pi i e / 16) for the e a radix-4 x 4 DFT needs
-#define FFB_C1 0.92387953251128676f    // cos(pi/8)
-#define FFB_S1 0.38268343236508977f    // sin(pi/8)
-#define FFB_R2 0.70710678118654752f    // sqrt(1/2)
-__device__ __forceinline__ float2 w16(int e) {
-    switch (e & 15) {
-        case 1: return make_float2(FFB_C1, -FFB_S1);
-        case 2: return make_float2(FFB_R2, -FFB_R2);
-        case 3: return make_float2(FFB_S1, -FFB_C1);
-        case 4: return make_float2(0.f, -1.f);
-        case 6: return make_float2(-FFB_R2, -FFB_R2);
-        case 9: return make_float2(-FFB_C1, FFB_S1);
-        default: return make_float2(1.f, 0.f);
-    }
-}
-
-// in-register length-M DFT, natural order in and out (forward)
-template <int M>
-__device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
-    if constexpr (M == 4) {
-        dft4<false>(x);
-    } else if constexpr (M == 8) {
-        float2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
-        dft4<false>(e);
-        dft4<false>(o);
-        const float2 w[4] = {make_float2(1.f, 0.f), make_float2(FFB_R2, -FFB_R2), make_float2(0.f, -1.f),
-                             make_float2(-FFB_R2, -FFB_R2)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 t = (k == 0) ? o[0] : cmul(o[k], w[k]);
-            x[k] = cadd(e[k], t);
-            x[k + 4] = csub(e[k], t);
-        }
-    } else {
-        static_assert(M == 16, "M in {4, 8, 16}");
-        float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) {
-            float2 v[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
-            dft4<false>(v);
-#pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 * k1 == 0) ? v[k1] : cmul(v[k1], w16(n2 * k1));
-        }
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            float2 v[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-            dft4<false>(v);
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
-        }
-    }
-}
-
 template <int NTH, int FMT>
 __global__ void __launch_bounds__(32 * RFFT_RB, 1)
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
@@ -483,7 +469,7 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
 // ---------------------------------------------------------------------------
 template <int N, int W>
 static size_t fused_smem() {
-    return sizeof(float2) * ((size_t)fus_mh(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * 2 * N);
+    return sizeof(float2) * ((size_t)fus_mh(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * N);
 }
 
 template <int N, int W>
