@@ -158,6 +158,22 @@ def ncu_traffic(kernel, images_per_launch):
     return rec["bytes_per_launch"] * images_per_launch / rec["images_per_launch"]
 
 
+def measured_tensor_peak(precision):
+    """Sustained dense tensor-core peak for the contraction's input type, from
+    MEASURED_PEAKS.json (bf16 measured; tf32 by the nominal 1.1 / 2.25 ratio);
+    the recipe's 1.7 PFLOP/s sustained figure when the file is absent."""
+    if precision not in ("bf16", "bf16x3", "tf32", "tf32x3"):
+        return None, None
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16, src = float(pk["bf16_tflops_sustained"]), "of measured sustained bf16"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1700.0, "of fallback sustained bf16"
+    if precision.startswith("tf32"):
+        return bf16 * 1.1 / 2.25, src + " x 1.1/2.25 (tf32)"
+    return bf16, src
+
+
 def fp32_peak_tflops(sm_mhz):
     """152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -361,6 +377,25 @@ def run_ours(args):
                "sample": "%d images of the n=100000 L=128 stack (%.1f s), FP64 direct NDFT + ring DFT + "
                          "quadrature + covariance; numpy BLAS threads" % (m, dt)}
 
+    # every stage against its own roof: the FFT / NUFFT stages against the FP32
+    # FFMA peak, the contractions against the tensor-core peak of their input
+    # type (measured sustained bf16; tf32 = bf16 x 1.1/2.25, the nominal ratio)
+    stages = {}
+    tc_peak, tc_note = measured_tensor_peak(head)
+    for c, (ms_c, calls_c) in prof.items():
+        if c not in flops or ms_c <= 0:
+            continue
+        rate = flops[c] * n * args.steps / (ms_c / 1e3) / 1e12
+        contraction = c in ("bessel", "covariance")
+        if contraction and tc_peak:
+            products = 3 if head in ("bf16x3", "tf32x3") else 1
+            stages[c] = {"bound": "tensor", "achieved": rate, "executed": rate * products, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": rate * products / tc_peak, "peak_note": tc_note,
+                         "ms_per_step": ms_c / args.steps}
+        else:
+            stages[c] = {"bound": "alu", "achieved": rate, "peak": peak, "unit": "TFLOP/s", "frac": rate / peak,
+                         "ms_per_step": ms_c / args.steps}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
@@ -373,7 +408,8 @@ def run_ours(args):
                 "precisions": {p: {"images_per_s": world * n / (v["ms"] / args.steps / 1e3),
                                    "kernel_ms": {c: round(t[0] / args.steps, 4) for c, t in v["prof"].items()}}
                                for p, v in results.items()},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
+                "roofline": roofline, "stages": stages, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": r["launches"],
                 "clocks": r["clocks"]}
         print(json.dumps(line))
     if world > 1:

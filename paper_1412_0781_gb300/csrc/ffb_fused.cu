@@ -186,12 +186,14 @@ __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, 
 #pragma unroll
     for (int h = R / 2; h >= 1; h >>= 1) {
         const bool up = (r & h) != 0;
-        const float2 w = __ldg(&tw[(r & (h - 1)) * (N / (2 * h))]);
+        // the last stage (h = 1) has the twiddle W^0 = 1
+        const float2 w = (h > 1) ? __ldg(&tw[(r & (h - 1)) * (N / (2 * h))]) : make_float2(1.f, 0.f);
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) {
             const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, x[k2].x, h),
                                           __shfl_xor_sync(0xffffffffu, x[k2].y, h));
-            x[k2] = up ? cmul(csub(pv, x[k2]), w) : cadd(x[k2], pv);
+            const float2 d = csub(pv, x[k2]);
+            x[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(x[k2], pv);
         }
     }
     int t = 0;
@@ -278,7 +280,8 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     constexpr float two_over_w = 2.0f / W;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
     float2 *stage0 = smz + MH * SLD;
-    // t / nl as a multiply-high: exact for t < 2^32 / nl
+    // t / nl as a multiply-high: exact for t < 2^32 / nl (nl >= 31 on this
+    // path, so the multiplier does not overflow)
     const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;
     for (int b = 0; b * FUS_GB < npts; ++b) {
         const int t0 = b * FUS_GB;
@@ -415,12 +418,14 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
 #pragma unroll
         for (int h = R / 2; h >= 1; h >>= 1) {           // pass B, part 2: across the R lanes
             const bool up = (r & h) != 0;
-            const float2 w = __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]);
+            // the last stage (h = 1) has the twiddle W^0 = 1
+            const float2 w = (h > 1) ? __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]) : make_float2(1.f, 0.f);
 #pragma unroll
             for (int k2 = 0; k2 < M; ++k2) {
                 const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
                                               __shfl_xor_sync(0xffffffffu, y[k2].y, h));
-                y[k2] = up ? cmul(csub(pv, y[k2]), w) : cadd(y[k2], pv);
+                const float2 d = csub(pv, y[k2]);
+                y[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(y[k2], pv);
             }
         }
         int t = 0;

@@ -76,12 +76,24 @@ __global__ void k_split_planes(const float *__restrict__ src, int64_t total, int
 // ---------------------------------------------------------------------------
 // the contraction
 // ---------------------------------------------------------------------------
+#define TCB_WARPS 6   // warp 0: TMA, warp 1: MMA and TMEM, warps 2-5: epilogue
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Persistent: CTA b takes items b, b + gridDim.x, ... of the (k, M tile)
+// list (item = k nM + m; M tile m = images 64 m .. 64 m + 63, rows image x
+// re/im).  For every item the producer streams the K chunks of A and B
+// (hi/lo planes) through a ring of nst stages (full/empty mbarriers); the MMA
+// thread accumulates each item into one of two TMEM accumulators and commits
+// it to the epilogue (accf), which drains it with tcgen05.ld into a padded
+// [64 images][BN q][re, im] stage, releases the accumulator (acce) and
+// writes the coefficients as contiguous runs per image.
 template <int KIND, int NPA, int NPB, int NPROD>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(32 * TCB_WARPS)
 k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
             const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int ld,
             int nimg, const int *__restrict__ pk_, const int *__restrict__ off_, int P, float *__restrict__ coef,
-            int BNmax, int tmem_cols, int nst, int *status) {
+            int BNmax, int acc_cols, int nst, int nM, int nitems, int *status) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     constexpr int ES = (KIND == 0) ? 4 : 2;
@@ -90,24 +102,27 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     const uint32_t a_bytes = 128u * 128u;       // one plane, one K chunk, 128 rows
     const uint32_t b_bytes = (uint32_t)BNmax * 128u;
     const uint32_t st_bytes = NPA * a_bytes + NPB * b_bytes;   // one stage: every plane of one K chunk
-    const size_t ring = (size_t)nst * st_bytes;
-    const size_t stage_bytes = (size_t)64 * (2 * BNmax + 2) * 4;      // epilogue reuse of the ring
-    uint64_t *bars = (uint64_t *)(sm + (ring > stage_bytes ? ring : stage_bytes));
-    uint64_t *full = bars, *empty = bars + nst, *done = bars + 2 * nst;
-    uint32_t *slot = (uint32_t *)(done + 1);
+    const int ldst = 2 * BNmax + 2;             // floats per image row of the epilogue stage
+    float *stage = (float *)(sm + (size_t)nst * st_bytes);
+    const size_t stage_bytes = ((size_t)64 * ldst * 4 + 15) & ~(size_t)15;
+    uint64_t *bars = (uint64_t *)(sm + (size_t)nst * st_bytes + stage_bytes);
+    uint64_t *full = bars, *empty = bars + nst, *accf = bars + 2 * nst, *acce = bars + 2 * nst + 2;
+    uint32_t *slot = (uint32_t *)(bars + 2 * nst + 4);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x, k = blockIdx.y;
-    const int pk = pk_[k], o = off_[k];
-    const int BN = max(16, (pk + 15) & ~15);
+    const int myitems = (blockIdx.x < nitems) ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2 * nst + 1; ++i) tc::mbar_init(&bars[i], 1);
+        for (int i = 0; i < 2 * nst; ++i) tc::mbar_init(&bars[i], 1);
+        tc::mbar_init(&accf[0], 1);
+        tc::mbar_init(&accf[1], 1);
+        tc::mbar_init(&acce[0], 4);   // one arrival per epilogue warp
+        tc::mbar_init(&acce[1], 4);
         tc::fence_mbar_init();
         *okflag = 1;
     }
-    if (warp == 0) {
-        tc::tmem_alloc(slot, (uint32_t)tmem_cols);
+    if (warp == 1) {
+        tc::tmem_alloc(slot, (uint32_t)(2 * acc_cols));
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -115,105 +130,139 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     tc::fence_after_sync();
     const uint32_t tbase = *slot;
 
-    if (threadIdx.x == 0) {
-        // K chunk ch lives in stage ch % nst; its load arrives on full[stage].
-        // The stage of chunk ch - 1 is refilled with chunk ch - 1 + nst right
-        // after the MMAs of chunk ch are queued, so the tensor pipe always has
-        // work while the copy runs.
-        auto load = [&](int ch) {
-            uint8_t *st = sm + (size_t)(ch % nst) * st_bytes;
-            uint64_t *bar = &full[ch % nst];
-            tc::mbar_arrive_expect_tx(bar, st_bytes);
-            tc::tma_load_3d(st, &mapA0, bar, ch * KCH, 128 * m, k);
-            if (NPA > 1) tc::tma_load_3d(st + a_bytes, &mapA1, bar, ch * KCH, 128 * m, k);
-            tc::tma_load_3d(st + NPA * a_bytes, &mapB0, bar, ch * KCH, 0, k);
-            if (NPB > 1) tc::tma_load_3d(st + NPA * a_bytes + b_bytes, &mapB1, bar, ch * KCH, 0, k);
-        };
-        const int npre = min(nst, NCH);
-        for (int ch = 0; ch < npre; ++ch) load(ch);
-        int issued = npre;        // chunks whose load has been issued
-        int waited = 0;           // chunks whose load has been waited for
-        bool ok = true;
-        const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
-        uint32_t acc = 0;
-        for (int ch = 0; ch < NCH && ok; ++ch) {
-            const int si = ch % nst;
-            if (!tc::mbar_wait(&full[si], (uint32_t)((ch / nst) & 1), TC_BUDGET)) {
-                ok = false;
-                break;
-            }
-            waited = ch + 1;
-            tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(sm + (size_t)si * st_bytes);
-#pragma unroll
-            for (int pr = 0; pr < NPROD; ++pr) {
-                const int pa = (pr == 2) ? 1 : 0;   // products (0,0), (0,1), (1,0)
-                const int pb = (pr == 1) ? 1 : 0;
-                const uint32_t a0 = sa + pa * a_bytes;
-                const uint32_t b0 = sa + NPA * a_bytes + pb * b_bytes;
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
-                    const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
-                    if (KIND == 0) tc::mma_tf32(tbase, ad, bd, id, acc);
-                    else tc::mma_bf16(tbase, ad, bd, id, acc);
-                    acc = 1;
+    if (warp == 0) {
+        if (lane == 0) {                                  // ---- TMA producer
+            int64_t g = 0;
+            bool ok = true;
+            for (int it = 0; it < myitems && ok; ++it) {
+                const int item = blockIdx.x + it * gridDim.x;
+                const int k = item / nM, m = item - k * nM;
+                for (int ch = 0; ch < NCH; ++ch, ++g) {
+                    const int si = (int)(g % nst);
+                    if (g >= nst && !tc::mbar_wait(&empty[si], (uint32_t)(((g / nst) - 1) & 1), TC_BUDGET)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = sm + (size_t)si * st_bytes;
+                    tc::mbar_arrive_expect_tx(&full[si], st_bytes);
+                    tc::tma_load_3d(st, &mapA0, &full[si], ch * KCH, 128 * m, k);
+                    if (NPA > 1) tc::tma_load_3d(st + a_bytes, &mapA1, &full[si], ch * KCH, 128 * m, k);
+                    tc::tma_load_3d(st + NPA * a_bytes, &mapB0, &full[si], ch * KCH, 0, k);
+                    if (NPB > 1) tc::tma_load_3d(st + NPA * a_bytes + b_bytes, &mapB1, &full[si], ch * KCH, 0, k);
                 }
             }
-            tc::mma_commit(&empty[si]);
-            const int prev = ch - 1;
-            if (prev >= 0 && issued < NCH) {
-                // the MMAs of chunk prev are done reading their stage
-                if (!tc::mbar_wait(&empty[prev % nst], (uint32_t)((prev / nst) & 1), TC_BUDGET)) {
+            if (!ok) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+            // every issued copy lands before the CTA may leave
+            for (int64_t h = (g > nst ? g - nst : 0); h < g; ++h)
+                tc::mbar_wait(&full[h % nst], (uint32_t)((h / nst) & 1), TC_BUDGET);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                  // ---- MMA issue
+            int64_t g = 0;
+            bool ok = true;
+            int it = 0;
+            for (; it < myitems && ok; ++it) {
+                const int item = blockIdx.x + it * gridDim.x;
+                const int k = item / nM;
+                const int pk = pk_[k];
+                const int BN = max(16, (pk + 15) & ~15);
+                const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
+                const int a = it & 1;
+                if (it >= 2 && !tc::mbar_wait(&acce[a], (uint32_t)(((it >> 1) - 1) & 1), TC_BUDGET)) {
                     ok = false;
                     break;
                 }
-                load(issued++);
+                tc::fence_after_sync();
+                const uint32_t dt = tbase + (uint32_t)(a * acc_cols);
+                for (int ch = 0; ch < NCH; ++ch, ++g) {
+                    const int si = (int)(g % nst);
+                    if (!tc::mbar_wait(&full[si], (uint32_t)((g / nst) & 1), TC_BUDGET)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(sm + (size_t)si * st_bytes);
+#pragma unroll
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int pa = (pr == 2) ? 1 : 0;   // products (0,0), (0,1), (1,0)
+                        const int pb = (pr == 1) ? 1 : 0;
+                        const uint32_t a0 = sa + pa * a_bytes;
+                        const uint32_t b0 = sa + NPA * a_bytes + pb * b_bytes;
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
+                            const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
+                            const uint32_t accf_ = (ch > 0 || pr > 0 || ks > 0) ? 1u : 0u;
+                            if (KIND == 0) tc::mma_tf32(dt, ad, bd, id, accf_);
+                            else tc::mma_bf16(dt, ad, bd, id, accf_);
+                        }
+                    }
+                    tc::mma_commit(&empty[si]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[a]);
+            }
+            if (!ok) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+                tc::mma_commit(&accf[it & 1]);   // tracks every MMA issued so far
+                tc::mbar_wait(&accf[it & 1], (uint32_t)((it >> 1) & 1), TC_BUDGET);
             }
         }
-        // the last commit covers every MMA issued before it
-        tc::mma_commit(done);
-        if (!ok) {
-            ffb_flag(status, FFB_ERR_TIMEOUT);
-            *okflag = 0;
-            for (int ch = waited; ch < issued; ++ch)   // let in-flight copies land
-                tc::mbar_wait(&full[ch % nst], (uint32_t)((ch / nst) & 1), TC_BUDGET);
-        }
-    }
-    __syncthreads();
-    if (!tc::mbar_wait(done, 0, TC_BUDGET)) {
-        ffb_flag(status, FFB_ERR_TIMEOUT);
-        atomicExch(okflag, 0);
-    }
-    tc::fence_after_sync();
-    __syncthreads();
-    if (*okflag) {
-        // drain TMEM into a padded [64 images][BN q][re, im] stage (the operand
-        // ring is no longer needed), then write each image's p_k complex
-        // coefficients as one contiguous run
-        float *stage = (float *)sm;
-        const int ldst = 2 * BN + 2;               // floats per image row, +2 breaks bank aliasing
-        const int r = 32 * warp + lane;            // accumulator row = TMEM lane
-        for (int c16 = 0; c16 < BN; c16 += 16) {
-            float v[16];
-            tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c16, v);
+    } else {                                              // ---- epilogue, warps 2-5
+        const int q4 = warp & 3;                          // TMEM lanes 32 q4 .. 32 q4 + 31
+        const int r = 32 * q4 + lane;                     // accumulator row: image r/2, part r%2
+        const int et = threadIdx.x - 64;                  // 0 .. 127
+        for (int it = 0; it < myitems; ++it) {
+            const int item = blockIdx.x + it * gridDim.x;
+            const int k = item / nM, m = item - k * nM;
+            const int pk = pk_[k], o = off_[k];
+            const int BN = max(16, (pk + 15) & ~15);
+            const int a = it & 1;
+            // after a failure elsewhere, stop waiting long (the loop count stays
+            // the same for all four warps: they meet at named barriers)
+            const long long budget = (*(volatile int *)okflag) ? TC_BUDGET : 0;
+            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), budget);
+            if (!ok && budget) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+            tc::fence_after_sync();
+            if (ok) {
+                for (int c16 = 0; c16 < BN; c16 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * acc_cols + c16), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) stage[(r >> 1) * ldst + 2 * (c16 + i) + (r & 1)] = v[i];
-        }
-        __syncthreads();
-        const int i0 = 64 * m;
-        const int nimg_t = min(64, nimg - i0);
-        float2 *out = (float2 *)coef;
-        for (int t = threadIdx.x; t < nimg_t * pk; t += 128) {
-            const int ii = t / pk, q = t - ii * pk;
-            float2 val = make_float2(stage[ii * ldst + 2 * q], stage[ii * ldst + 2 * q + 1]);
-            if (k == 0) val.y = 0.f;
-            out[(size_t)(i0 + ii) * P + o + q] = val;
+                    for (int i = 0; i < 16; ++i) stage[(r >> 1) * ldst + 2 * (c16 + i) + (r & 1)] = v[i];
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[a]);
+            epi_bar();                                    // the stage holds the item
+            if (ok) {
+                const int i0 = 64 * m;
+                const int nimg_t = min(64, nimg - i0);
+                float2 *out = (float2 *)coef;
+                // t / pk as a multiply-high (exact for t < 2^32 / pk); pk = 1
+                // would overflow the multiplier and is taken as is
+                const unsigned magic = (pk > 1) ? 0xFFFFFFFFu / (unsigned)pk + 1u : 0u;
+                for (int t = et; t < nimg_t * pk; t += 128) {
+                    const int ii = (pk > 1) ? (int)__umulhi((unsigned)t, magic) : t, q = t - ii * pk;
+                    float2 val = make_float2(stage[ii * ldst + 2 * q], stage[ii * ldst + 2 * q + 1]);
+                    if (k == 0) val.y = 0.f;
+                    out[(size_t)(i0 + ii) * P + o + q] = val;
+                }
+            }
+            epi_bar();                                    // the stage may be refilled
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, (uint32_t)tmem_cols);
+    if (warp == 1) tc::tmem_dealloc(tbase, (uint32_t)(2 * acc_cols));
 }
 
 // ---------------------------------------------------------------------------
@@ -284,19 +333,18 @@ static size_t tc_stage_bytes(int prec, int BN) {
 
 static size_t tc_smem_bytes(int prec, int BN, int nst) {
     const size_t ring = (size_t)nst * tc_stage_bytes(prec, BN);
-    const size_t stage = (size_t)64 * (2 * BN + 2) * 4;
-    return 1024 + (ring > stage ? ring : stage) + 8 * (2 * nst + 1) + 16;
+    const size_t stage = ((size_t)64 * (2 * BN + 2) * 4 + 15) & ~(size_t)15;
+    return 1024 + ring + stage + 8 * (2 * (size_t)nst + 4) + 16;
 }
 
-// stages of the K pipeline: as many as fit in one CTA's shared memory, at
-// most the number of K chunks and at most 4; 0 when not even one fits
+// stages of the K pipeline: as many as fit in one CTA's shared memory next to
+// the epilogue stage, at most 4; 0 when not even one fits
 static int tc_stages(int prec, int ld, int BN) {
-    const int es = is_bf16(prec) ? 2 : 4;
-    const int nch = ld / (128 / es);
+    (void)ld;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int nst = nch < 4 ? nch : 4;
+    int nst = 4;
     while (nst > 0 && tc_smem_bytes(prec, BN, nst) > (size_t)optin) --nst;
     return nst;
 }
@@ -368,8 +416,19 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
 
 template <int KIND, int NPA, int NPB, int NPROD>
 static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    const int nst = tc_stages(p->precision, t->ld, t->BN);
+    // two CTAs per SM when a two-stage ring fits in half the shared memory
+    // (their epilogues then overlap each other's loads), else one with the
+    // deepest ring that fits
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int per_sm = 1, nst = tc_stages(p->precision, t->ld, t->BN);
     if (nst <= 0) return FFB_ERR_UNSUPPORTED;
+    if (2 * tc_smem_bytes(p->precision, t->BN, 2) + 2048 <= (size_t)optin) {
+        per_sm = 2;
+        nst = 2;
+    }
     const size_t smem = tc_smem_bytes(p->precision, t->BN, nst);
     static int attr = 0;
     if (attr < (int)smem) {
@@ -378,11 +437,13 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
         if (e) return e;
         attr = (int)smem;
     }
-    dim3 g((2 * nimg + 127) / 128, p->k_max + 1);
+    const int nM = (2 * nimg + 127) / 128;
+    const int nitems = nM * (p->k_max + 1);
+    const int grid = nitems < per_sm * sms ? nitems : per_sm * sms;   // persistent CTAs
     ProfScope ps(p, FFB_KC_BESSEL, s);
-    k_tc_bessel<KIND, NPA, NPB, NPROD><<<g, 128, smem, s>>>(t->mA0, t->mA1, t->mB0, t->mB1, t->ld, nimg, p->d_p,
-                                                           p->d_off, p->P, d_coef_chunk, t->BN, t->tmem_cols,
-                                                           nst, p->d_status);
+    k_tc_bessel<KIND, NPA, NPB, NPROD><<<grid, 32 * TCB_WARPS, smem, s>>>(
+        t->mA0, t->mA1, t->mB0, t->mB1, t->ld, nimg, p->d_p, p->d_off, p->P, d_coef_chunk, t->BN, t->tmem_cols, nst,
+        nM, nitems, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -430,10 +491,11 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 // q >= p_k of the staging buffer may hold another item's values, which only
 // reach accumulator entries that are never read.
 // ---------------------------------------------------------------------------
-#define COV_PF 16   // coefficient values per thread per tile held in registers
+#define COV_NT 512   // threads of a covariance CTA
+#define COV_PF 4     // coefficient values per thread per tile held in registers
 
 template <int KIND, int NP>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(COV_NT, 1)
 k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per chunk
@@ -448,7 +510,7 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (uint32_t i = threadIdx.x; i < 2 * BUF_BYTES / 16; i += 128)
+    for (uint32_t i = threadIdx.x; i < 2 * BUF_BYTES / 16; i += COV_NT)
         ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) {
         tc::mbar_init(&bars[0], 1);
@@ -474,11 +536,17 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
         const int64_t ie = min(S.n, ib + (int64_t)S.per);
         const int p = S.pk[k], o = S.off[k];
         const int BN = max(16, (p + 15) & ~15);
-        const int TI = (g.tile_imgs >= 32 && 32 * p <= 128 * COV_PF) ? 32 : 16;
-        const int items = TI * p;                   // (image, q) pairs per tile
+        // (image, q) slots of a tile: each warp covers 8 rows q x 4 images,
+        // so that its stores into the swizzled K-major tile fall on distinct
+        // banks; QBP 8-row blocks (a power of two >= p/8) index by shifts
+        int lgQ = 0;
+        while ((8 << lgQ) < p) ++lgQ;
+        const int QBP = 1 << lgQ;
+        const int TI = (g.tile_imgs >= 32 && 8 * QBP * 32 <= COV_NT * COV_PF) ? 32 : 16;
+        const int items = 8 * QBP * TI;
         const int kent = 2 * TI;                    // K entries per tile
         const int ntiles = (ie > ib) ? (int)((ie - ib + TI - 1) / TI) : 0;
-        if (items > 128 * COV_PF || BN > acc_cols) {   // uniform across the CTA
+        if (items > COV_NT * COV_PF || BN > acc_cols) {   // uniform across the CTA
             if (threadIdx.x == 0) ffb_flag(status, FFB_ERR_UNSUPPORTED);
             continue;
         }
@@ -491,11 +559,11 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
             const int64_t i0 = ib + (int64_t)t * TI;
 #pragma unroll
             for (int u = 0; u < COV_PF; ++u) {
-                const int it = threadIdx.x + 128 * u;
+                const int it = threadIdx.x + COV_NT * u;
                 float2 v = make_float2(0.f, 0.f);
                 if (it < items) {
-                    const int ii = it / p, q = it - ii * p;
-                    if (i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
+                    const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7), ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
+                    if (q < p && i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
                 }
                 pre[u] = v;
             }
@@ -516,9 +584,10 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
             if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
 #pragma unroll
             for (int u = 0; u < COV_PF; ++u) {
-                const int it = threadIdx.x + 128 * u;
+                const int it = threadIdx.x + COV_NT * u;
                 if (it >= items) break;
-                const int ii = it / p, q = it - ii * p;
+                const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7), ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
+                if (q >= p) continue;   // rows past p_k of the last 8-row block
                 float re = cur[u].x, im = cur[u].y;
                 if (k == 0) {   // shifted real part; images past the range stay zero
                     re = (ib + (int64_t)t * TI + ii < ie) ? re - S.shift[q] : 0.f;
@@ -578,16 +647,18 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
         tc::fence_after_sync();
         __syncthreads();
         if (ntiles > 0 && *okflag) {
-            const int q = 32 * warp + lane;
+            // warp w reads TMEM lanes 32 (w mod 4) .. + 31 and every fourth
+            // group of 16 columns
+            const int q = 32 * (warp & 3) + lane;
             const int used = min(nacc, ntiles);
             double *blk = S.acc + S.cov_off[k];
-            for (int c16 = 0; c16 < BN; c16 += 16) {
+            for (int c16 = 16 * (warp >> 2); c16 < BN; c16 += 16 * (COV_NT / 128)) {
                 double sum[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) sum[i] = 0.0;
                 for (int a = 0; a < used; ++a) {
                     float v[16];
-                    tc::tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * acc_cols + c16), v);
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(a * acc_cols + c16), v);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) sum[i] += (double)v[i];
                 }
@@ -633,7 +704,9 @@ static size_t tc_cov_smem(int prec) {
 bool ffb_tc_cov_supported(ffb_plan_t p) {
     if (p->precision == FFB_FP32) return false;
     if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
-    if (16 * p->pmax > 128 * COV_PF) return false;    // a 16-image tile fits the register prefetch
+    int qbp = 1;
+    while (8 * qbp < p->pmax) qbp <<= 1;
+    if (8 * qbp * 16 > COV_NT * COV_PF) return false;   // a 16-image tile fits the prefetch
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -656,7 +729,7 @@ static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t 
     while (cols < ((pmax + 15) & ~15)) cols <<= 1;
     if (cols > 128) return FFB_ERR_UNSUPPORTED;
     const int nacc = 512 / cols > 8 ? 8 : 512 / cols;   // rotating float32 accumulators in TMEM
-    k_tc_cov<KIND, NP><<<grid, 128, smem, s>>>(g, cols, nacc, status);
+    k_tc_cov<KIND, NP><<<grid, COV_NT, smem, s>>>(g, cols, nacc, status);
     return ffb_check_cuda(cudaGetLastError());
 }
 
