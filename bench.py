@@ -127,15 +127,16 @@ def algorithmic_flops(plan):
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the
     # dominant kernel, valid while the source it was captured from is unchanged
-    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_fused.cu:k_grid_interp_half",
+    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_fused.cu",
                                 "paper_1412_0781_gb300/csrc/ffb_internal.cuh"],
-                    "sha256": "db46cb94189b8aab20c2b3072fbada93b80d5bbb3171aadcfce666462a51a0de",
-                    "bytes_per_launch": 10081024 + 8448, "images_per_launch": 152},
+                    "sha256": "bb52721b2ecbf8d999a4f3ace6927e05886bfe9b0a9348af0dac14ff2b24fbec",
+                    "bytes_per_launch": 10086912 + 337152, "images_per_launch": 152},
 }
 
 
 def _source_digest(sources):
-    """sha256 over the listed files; "file:kernel" hashes only the text from the
+    """sha256 over the listed files (the kernel's file and the header its
+    inlined helpers come from); "file:kernel" hashes only the text from the
     kernel's template line to the next section banner."""
     import hashlib
     h = hashlib.sha256()
