@@ -11,6 +11,28 @@
 // the p_k rows of B^(k); K = n_xi.  Each thread owns 2 images x 4 q.
 // ---------------------------------------------------------------------------
 #define BES_IMG 32
+// NC: 16-column groups of q computed per 64-column tile (ceil(p_k / 16),
+// at most 4), so that blocks with small p_k skip the padding columns
+template <int NC>
+__device__ __forceinline__ void bessel_fp32_tile(const float *As, const float *Bs, int ld, int n_xi, int tx, int ty,
+                                                 float (&acc)[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int j = 0; j < n_xi; ++j) {
+        float a[4], b[NC];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[(ty * 4 + r) * ld + j];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) b[c] = Bs[(tx + 16 * c) * ld + j];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_bessel_fp32(const float *__restrict__ Fhat, const float *__restrict__ Bf, const int *__restrict__ pk_,
               const int *__restrict__ off_, int n_xi, int chunk, int nimg, int P, float2 *__restrict__ coef) {
@@ -36,21 +58,11 @@ k_bessel_fp32(const float *__restrict__ Fhat, const float *__restrict__ Bf, cons
         }
         __syncthreads();
         float acc[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-        for (int j = 0; j < n_xi; ++j) {
-            float a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[(ty * 4 + r) * ld + j];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[(tx + 16 * c) * ld + j];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-        }
+        const int nc = min(4, (pk - q0 + 15) >> 4);   // uniform over the CTA
+        if (nc == 1) bessel_fp32_tile<1>(As, Bs, ld, n_xi, tx, ty, acc);
+        else if (nc == 2) bessel_fp32_tile<2>(As, Bs, ld, n_xi, tx, ty, acc);
+        else if (nc == 3) bessel_fp32_tile<3>(As, Bs, ld, n_xi, tx, ty, acc);
+        else bessel_fp32_tile<4>(As, Bs, ld, n_xi, tx, ty, acc);
 #pragma unroll
         for (int ii = 0; ii < 2; ++ii) {
             const int img = i0 + ty * 2 + ii;
@@ -104,7 +116,12 @@ __global__ void __launch_bounds__(256)
 k_cov_fp32(const __grid_constant__ CovGroup g) {
     __shared__ float2 Xa[COV_TI][64];
     __shared__ float2 Xb[COV_TI][64];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // warp w owns rows 16 (w % 4) .. + 15 and columns 32 (w / 4) .. + 31 of the
+    // 64 x 64 tile, 4 x 4 per thread; a warp whose sub-block lies past p_k skips
+    // the products (uniformly), so small blocks cost less than a full tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0w = 16 * (warp & 3) + 4 * (lane >> 3);
+    const int c0w = 32 * (warp >> 2) + 4 * (lane & 7);
     for (int64_t item = blockIdx.x; item < g.nitems; item += gridDim.x) {
         const CovStack &S = g.st[cov_stack_of(g, item)];
         const int64_t local = item - S.item0;
@@ -147,17 +164,20 @@ k_cov_fp32(const __grid_constant__ CovGroup g) {
                 Xb[ii][qq] = vb;
             }
             __syncthreads();
+            if (16 * (warp & 3) < pk - q0 && 32 * (warp >> 2) < pk - q1) {
 #pragma unroll 4
-            for (int ii = 0; ii < COV_TI; ++ii) {
-                float2 a[4], b[4];
+                for (int ii = 0; ii < COV_TI; ++ii) {
+                    float2 a[4], b[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = Xa[ii][ty * 4 + r];
+                    for (int r = 0; r < 4; ++r) a[r] = Xa[ii][r0w + r];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) b[c] = Xb[ii][tx * 4 + c];
+                    for (int c = 0; c < 4; ++c) b[c] = Xb[ii][c0w + c];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
+                        for (int c = 0; c < 4; ++c)
+                            accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
+                }
             }
             if (do_sum && threadIdx.x < 64) {
                 for (int ii = 0; ii < COV_TI; ++ii) sf += Xa[ii][threadIdx.x].x;
@@ -180,7 +200,7 @@ k_cov_fp32(const __grid_constant__ CovGroup g) {
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int qa = q0 + ty * 4 + r, qb = q1 + tx * 4 + c;
+                const int qa = q0 + r0w + r, qb = q1 + c0w + c;
                 if (qa < pk && qb < pk) {
                     double v = accd[r][c] + (double)accf[r][c];
                     atomicAdd(&blk[(size_t)qa * pk + qb], v);
