@@ -349,7 +349,7 @@ struct CovStack {
 };
 struct CovGroup {
     int S;
-    int tile_imgs;          // tensor cores: images per MMA tile, 16 or 32
+    int tile_imgs;          // tensor cores: largest images per MMA tile (64, 32 or 16)
     int64_t nitems;
     CovStack st[FFB_GROUP_MAX];
 };

@@ -76,9 +76,10 @@ __global__ void k_split_planes(const float *__restrict__ src, int64_t total, int
 // ---------------------------------------------------------------------------
 // the contraction
 // ---------------------------------------------------------------------------
-#define TCB_WARPS 6   // warp 0: TMA, warp 1: MMA and TMEM, warps 2-5: epilogue
+#define TCB_EPI 8     // epilogue warps: two per TMEM lane quarter
+#define TCB_WARPS (2 + TCB_EPI)   // warp 0: TMA, warp 1: MMA and TMEM, the rest: epilogue
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TCB_EPI) : "memory"); }
 
 // Persistent: CTA b takes items b, b + gridDim.x, ... of the (k, M tile)
 // list (item = k nM + m; M tile m = images 64 m .. 64 m + 63, rows image x
@@ -116,8 +117,8 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
         for (int i = 0; i < 2 * nst; ++i) tc::mbar_init(&bars[i], 1);
         tc::mbar_init(&accf[0], 1);
         tc::mbar_init(&accf[1], 1);
-        tc::mbar_init(&acce[0], 4);   // one arrival per epilogue warp
-        tc::mbar_init(&acce[1], 4);
+        tc::mbar_init(&acce[0], TCB_EPI);   // one arrival per epilogue warp
+        tc::mbar_init(&acce[1], TCB_EPI);
         tc::fence_mbar_init();
         *okflag = 1;
     }
@@ -164,10 +165,11 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             int64_t g = 0;
             bool ok = true;
             int it = 0;
+            // p_k of the next item is loaded one item ahead, off the MMA stream
+            int pk_next = (myitems > 0) ? __ldg(&pk_[blockIdx.x / nM]) : 0;
             for (; it < myitems && ok; ++it) {
-                const int item = blockIdx.x + it * gridDim.x;
-                const int k = item / nM;
-                const int pk = pk_[k];
+                const int pk = pk_next;
+                if (it + 1 < myitems) pk_next = __ldg(&pk_[(blockIdx.x + (it + 1) * gridDim.x) / nM]);
                 const int BN = max(16, (pk + 15) & ~15);
                 const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
                 const int a = it & 1;
@@ -212,10 +214,11 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                 tc::mbar_wait(&accf[it & 1], (uint32_t)((it >> 1) & 1), TC_BUDGET);
             }
         }
-    } else {                                              // ---- epilogue, warps 2-5
+    } else {                                              // ---- epilogue warps
         const int q4 = warp & 3;                          // TMEM lanes 32 q4 .. 32 q4 + 31
+        const int cg = (warp - 2) >> 2;                   // which column groups of 16
         const int r = 32 * q4 + lane;                     // accumulator row: image r/2, part r%2
-        const int et = threadIdx.x - 64;                  // 0 .. 127
+        const int et = threadIdx.x - 64;                  // 0 .. 32 TCB_EPI - 1
         for (int it = 0; it < myitems; ++it) {
             const int item = blockIdx.x + it * gridDim.x;
             const int k = item / nM, m = item - k * nM;
@@ -223,7 +226,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             const int BN = max(16, (pk + 15) & ~15);
             const int a = it & 1;
             // after a failure elsewhere, stop waiting long (the loop count stays
-            // the same for all four warps: they meet at named barriers)
+            // the same for all epilogue warps: they meet at named barriers)
             const long long budget = (*(volatile int *)okflag) ? TC_BUDGET : 0;
             const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), budget);
             if (!ok && budget) {
@@ -232,7 +235,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             }
             tc::fence_after_sync();
             if (ok) {
-                for (int c16 = 0; c16 < BN; c16 += 16) {
+                for (int c16 = 16 * cg; c16 < BN; c16 += 16 * (TCB_EPI / 4)) {
                     float v[16];
                     tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * acc_cols + c16), v);
 #pragma unroll
@@ -250,7 +253,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                 // t / pk as a multiply-high (exact for t < 2^32 / pk); pk = 1
                 // would overflow the multiplier and is taken as is
                 const unsigned magic = (pk > 1) ? 0xFFFFFFFFu / (unsigned)pk + 1u : 0u;
-                for (int t = et; t < nimg_t * pk; t += 128) {
+                for (int t = et; t < nimg_t * pk; t += 32 * TCB_EPI) {
                     const int ii = (pk > 1) ? (int)__umulhi((unsigned)t, magic) : t, q = t - ii * pk;
                     float2 val = make_float2(stage[ii * ldst + 2 * q], stage[ii * ldst + 2 * q + 1]);
                     if (k == 0) val.y = 0.f;
@@ -492,14 +495,18 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 // reach accumulator entries that are never read.
 // ---------------------------------------------------------------------------
 #define COV_NT 512   // threads of a covariance CTA
-#define COV_PF 4     // coefficient values per thread per tile held in registers
+// coefficient values per thread per tile held in registers: 8 for bf16
+// (64-image tiles), 4 for tf32 (32-image tiles)
+template <int KIND>
+__host__ __device__ constexpr int cov_pf() { return (KIND == 0) ? 4 : 8; }
 
 template <int KIND, int NP>
 __global__ void __launch_bounds__(COV_NT, 1)
 k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per chunk
-    constexpr int NCHT = (KIND == 0) ? 2 : 1;   // chunks per tile of 32 images
+    constexpr int NCHT = 2;                     // 128-byte K chunks per tile buffer
+    constexpr int PF = cov_pf<KIND>();
     constexpr int KINST = (KIND == 0) ? 8 : 16; // K per MMA instruction
     constexpr uint32_t CH_BYTES = 128u * 128u;  // one chunk of 128 rows
     constexpr uint32_t BUF_BYTES = NP * NCHT * CH_BYTES;
@@ -542,11 +549,16 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
         int lgQ = 0;
         while ((8 << lgQ) < p) ++lgQ;
         const int QBP = 1 << lgQ;
-        const int TI = (g.tile_imgs >= 32 && 8 * QBP * 32 <= COV_NT * COV_PF) ? 32 : 16;
+        // images per tile: 64 (bf16: two K chunks), 32 or 16, as the staging
+        // slots and the buffer's two K chunks allow
+        const int ti_max = (KIND == 0) ? 32 : 64;
+        int TI = 16;
+        if (g.tile_imgs >= 32 && 8 * QBP * 32 <= COV_NT * PF) TI = 32;
+        if (ti_max >= 64 && g.tile_imgs >= 64 && 8 * QBP * 64 <= COV_NT * PF) TI = 64;
         const int items = 8 * QBP * TI;
         const int kent = 2 * TI;                    // K entries per tile
         const int ntiles = (ie > ib) ? (int)((ie - ib + TI - 1) / TI) : 0;
-        if (items > COV_NT * COV_PF || BN > acc_cols) {   // uniform across the CTA
+        if (items > COV_NT * PF || BN > acc_cols) {   // uniform across the CTA
             if (threadIdx.x == 0) ffb_flag(status, FFB_ERR_UNSUPPORTED);
             continue;
         }
@@ -554,11 +566,11 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
         const float2 *coef = S.coef;
         const int P = S.P;
 
-        float2 pre[COV_PF];
+        float2 pre[PF];
         auto load_tile = [&](int t) {
             const int64_t i0 = ib + (int64_t)t * TI;
 #pragma unroll
-            for (int u = 0; u < COV_PF; ++u) {
+            for (int u = 0; u < PF; ++u) {
                 const int it = threadIdx.x + COV_NT * u;
                 float2 v = make_float2(0.f, 0.f);
                 if (it < items) {
@@ -578,12 +590,12 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
                     atomicExch(okflag, 0);
                 }
             }
-            float2 cur[COV_PF];
+            float2 cur[PF];
 #pragma unroll
-            for (int u = 0; u < COV_PF; ++u) cur[u] = pre[u];
+            for (int u = 0; u < PF; ++u) cur[u] = pre[u];
             if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
 #pragma unroll
-            for (int u = 0; u < COV_PF; ++u) {
+            for (int u = 0; u < PF; ++u) {
                 const int it = threadIdx.x + COV_NT * u;
                 if (it >= items) break;
                 const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7), ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
@@ -706,7 +718,7 @@ bool ffb_tc_cov_supported(ffb_plan_t p) {
     if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
     int qbp = 1;
     while (8 * qbp < p->pmax) qbp <<= 1;
-    if (8 * qbp * 16 > COV_NT * COV_PF) return false;   // a 16-image tile fits the prefetch
+    if (8 * qbp * 16 > COV_NT * cov_pf<0>()) return false;   // a 16-image tile fits the prefetch
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -757,7 +769,7 @@ int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *sta
 int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
     CovGroup g;          // copied into the launch's parameters
     g.S = 1;
-    g.tile_imgs = 32;
+    g.tile_imgs = 64;
     ffb_cov_stack(p, d_coef, n, true, &g.st[0]);
     g.st[0].item0 = 0;
     g.st[0].per = 1024;
