@@ -32,10 +32,16 @@
 // consecutive nodes, the nodes into half warps with distinct slots (built on
 // the host from the node geometry, ffb_fused_prepare), and the kernel stages
 // each block's results in shared memory to store them in natural order.
+// The window origin and the 8 + 8 kernel weights of a node depend on the
+// geometry alone: the plan computes them once in float64 and stores them with
+// the node's slot (80 bytes per node, about 3 MB at N = 256 and less below,
+// read from L2 by every CTA), so phase 3 spends its issue slots on the 2 W^2
+// gather FMAs instead of 2 W kernel evaluations and the node's coordinates.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ffb_internal.cuh"
@@ -206,9 +212,8 @@ __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, 
 template <int N, int W>
 __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
-                   const float2 *__restrict__ tw, float beta, const float2 *__restrict__ rad,
-                   const float4 *__restrict__ ang, int n_xi, int n_theta, int nq0,
-                   const unsigned short *__restrict__ gperm, int nblk, float2 *__restrict__ Fpol, int *status) {
+                   const float2 *__restrict__ tw, int n_xi, int n_theta, int nq0,
+                   const float4 *__restrict__ nodes, int nblk, float2 *__restrict__ Fpol, int *status) {
     constexpr int L = N / 2;
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
@@ -270,14 +275,16 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
     // node t = j * nl + (l - lbeg); block b holds t in [b FUS_GB, (b + 1) FUS_GB),
-    // visited in the plan's regrouped order and staged in the (now idle) warp
-    // buffers, two blocks deep so that one barrier per block suffices.
+    // visited in the plan's regrouped order: record s of the block carries the
+    // node's window origin (r0, c0) in S, its 8 + 8 kernel weights and its slot
+    // in the block (the plan computes them once, in float64).  Results are
+    // staged in the (now idle) warp buffers, two blocks deep so that one
+    // barrier per block suffices, and stored in natural order.
+    static_assert(W == 8, "node records hold 8 + 8 weights");
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
     const int nl = (half == 0) ? nq0 : nh - nq0;
     const int npts = n_xi * nl;
-    constexpr float halfw = 0.5f * W;
-    constexpr float two_over_w = 2.0f / W;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
     float2 *stage0 = smz + MH * SLD;
     // t / nl as a multiply-high: exact for t < 2^32 / nl (nl >= 31 on this
@@ -287,61 +294,49 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
         const int t0 = b * FUS_GB;
         const int cnt = min(FUS_GB, npts - t0);
         float2 *stage = stage0 + (b & 1) * FUS_GB;
-        const unsigned short *pm = gperm + ((size_t)half * nblk + b) * FUS_GB;
+        // record fields: [0], [1] row weights, [2], [3] column weights, [4] (origin, slot)
+        const float4 *rec = nodes + ((size_t)half * nblk + b) * 5 * FUS_GB;
         for (int s = threadIdx.x; s < FUS_GB; s += FUS_NT) {
-            const int loc = pm[s];
+            // all five loads issued together (every slot's record is valid)
+            const float4 meta = __ldg(&rec[4 * FUS_GB + s]);
+            const float4 y0 = __ldg(&rec[s]), y1 = __ldg(&rec[FUS_GB + s]);
+            const float4 x0 = __ldg(&rec[2 * FUS_GB + s]), x1 = __ldg(&rec[3 * FUS_GB + s]);
+            const int loc = __float_as_int(meta.y);
             if (loc >= cnt) continue;
-            const int t = t0 + loc;
-            const int j = (int)__umulhi((unsigned)t, nl_magic);
-            const int l = lbeg + (t - j * nl);
-            const float2 r = __ldg(&rad[j]);
-            const float4 a = __ldg(&ang[l]);
-            const float p1 = r.x * a.x;
-            const float e1 = fmaf(r.x, a.x, -p1) + fmaf(r.x, a.y, r.y * a.x);
-            const float p2 = r.x * a.z;
-            const float e2 = fmaf(r.x, a.z, -p2) + fmaf(r.x, a.w, r.y * a.z);
-            const float m1f = ceilf(p1 - halfw), m2f = ceilf(p2 - halfw);
-            const float f1 = (p1 - m1f) + e1, f2 = (p2 - m2f) + e2;
-            const int c0 = (int)m1f - m1lo;     // column of the first tap in S
-            const int r0 = (int)m2f + H;        // row of the first tap in S
+            const int rc = __float_as_int(meta.x);
+            const int r0 = rc & 0xFFFF, c0 = rc >> 16;
             float2 acc = make_float2(0.f, 0.f);
-            if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) {
+            if (r0 + W > MH || c0 + W > MH) {
                 ffb_flag(status, FFB_ERR_ARG);
             } else {
+                const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
                 // column sums over the W rows first: every row issues 2 W
                 // independent FMAs; the column weights are applied at the end
                 const float2 *base = S + r0 * SLD + c0;
                 float2 cs[W];
-                {
-                    const float wy = es_kernel(f2, two_over_w, beta);
 #pragma unroll
-                    for (int q = 0; q < W; ++q) {
-                        const float2 g = base[q];
-                        cs[q] = make_float2(wy * g.x, wy * g.y);
-                    }
+                for (int q = 0; q < W; ++q) {
+                    const float2 g = base[q];
+                    cs[q] = make_float2(wy[0] * g.x, wy[0] * g.y);
                 }
 #pragma unroll
                 for (int bq = 1; bq < W; ++bq) {
-                    const float wy = es_kernel(f2 - (float)bq, two_over_w, beta);
                     const float2 *row = base + bq * SLD;
 #pragma unroll
                     for (int q = 0; q < W; ++q) {
                         const float2 g = row[q];
-                        cs[q].x = fmaf(wy, g.x, cs[q].x);
-                        cs[q].y = fmaf(wy, g.y, cs[q].y);
+                        cs[q].x = fmaf(wy[bq], g.x, cs[q].x);
+                        cs[q].y = fmaf(wy[bq], g.y, cs[q].y);
                     }
                 }
+                const float wx[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
                 float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < W; q += 2) {
-                    const float w0 = es_kernel(f1 - (float)q, two_over_w, beta);
-                    ax0 = fmaf(w0, cs[q].x, ax0);
-                    ay0 = fmaf(w0, cs[q].y, ay0);
-                    if (q + 1 < W) {
-                        const float w1v = es_kernel(f1 - (float)(q + 1), two_over_w, beta);
-                        ax1 = fmaf(w1v, cs[q + 1].x, ax1);
-                        ay1 = fmaf(w1v, cs[q + 1].y, ay1);
-                    }
+                    ax0 = fmaf(wx[q], cs[q].x, ax0);
+                    ay0 = fmaf(wx[q], cs[q].y, ay0);
+                    ax1 = fmaf(wx[q + 1], cs[q + 1].x, ax1);
+                    ay1 = fmaf(wx[q + 1], cs[q + 1].y, ay1);
                 }
                 acc = make_float2(ax0 + ax1, ay0 + ay1);
             }
@@ -490,9 +485,8 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
     dim3 g(2, m);
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
     k_grid_interp_half<N, W><<<g, FUS_NT, smem, s>>>(d_images + (size_t)i0 * p->L * p->L, p->off, p->d_corr,
-                                                     p->d_twN, (float)p->beta, p->d_rad, p->d_ang, p->n_xi,
-                                                     p->n_theta, p->nq0, p->d_gperm, p->gperm_nblk, Fpol,
-                                                     p->d_status);
+                                                     p->d_twN, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
+                                                     p->node_nblk, Fpol, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -510,36 +504,73 @@ bool ffb_fused_supported(ffb_plan_t p) {
     return smem <= (size_t)optin;
 }
 
-// Regrouped node order of phase 3 (see the file header): for each half and
-// block of FUS_GB nodes, block-local node indices in lane order; entries past
-// the block's node count hold 0xFFFF.  Greedy per half warp: one node from
-// every nonempty bank slot, fullest slot first, then fill from the fullest.
+// Node records of phase 3 (see the file header): for each half and block of
+// FUS_GB nodes, FUS_GB records in the regrouped lane order, stored as five
+// float4 planes [block][field][slot] so that every field is one coalesced
+// 16-byte load per lane:
+//   fields 0, 1  row weights phi(f2 - b), b = 0..7, f2 = p2 - m2 (rows of S)
+//   field  2, 3  column weights phi(f1 - q), q = 0..7, f1 = p1 - m1
+//   field  4     (r0 | c0 << 16, slot in the block, 0, 0) as int bits
+// with p = N xi_j (cos theta_l, sin theta_l) the node in grid units,
+// m = ceil(p - W/2) the first tap, phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1))
+// the ES kernel (Sec. III, type-2 NUFFT), all in float64.  Slots past the
+// block's node count hold slot 0xFFFF.  Lane order: greedy per half warp, one
+// node from every nonempty bank slot (r0 SLD + c0) mod 16, fullest slot first,
+// then fill from the fullest.
 int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
-    const int N = p->N, W = p->w, H = (W + 1) / 2, SLD = fus_sld(N, W);
+    const int N = p->N, W = p->w, H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W);
+    if (W != 8) return FFB_ERR_UNSUPPORTED;
     const int nh = p->n_theta / 2;
     const int nblk = (p->n_xi * p->nq0 + FUS_GB - 1) / FUS_GB;   // half 0 has the most nodes
     std::vector<double> xi(p->n_xi);
     int e = ffb_check_cuda(cudaMemcpyAsync(xi.data(), p->d_xi, sizeof(double) * p->n_xi, cudaMemcpyDeviceToHost, s));
     if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
     if (e) return e;
-    std::vector<unsigned short> perm((size_t)2 * nblk * FUS_GB, 0xFFFF);
+    auto phi = [&](double x) {
+        const double z = 2.0 * x / W, u = 1.0 - z * z;
+        return (u > 0.0) ? std::exp(p->beta * (std::sqrt(u) - 1.0)) : 0.0;
+    };
+    auto bits = [](int v) {
+        float f;
+        std::memcpy(&f, &v, sizeof f);
+        return f;
+    };
+    std::vector<float4> rec((size_t)2 * nblk * 5 * FUS_GB, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int half = 0; half < 2; ++half) {
         const int lbeg = (half == 0) ? 0 : p->nq0;
         const int nl = (half == 0) ? p->nq0 : nh - p->nq0;
         const int npts = p->n_xi * nl;
         const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-        for (int b = 0; b * FUS_GB < npts; ++b) {
-            const int t0 = b * FUS_GB, cnt = std::min(FUS_GB, npts - t0);
+        for (int b = 0; b < nblk; ++b) {
+            float4 *R = rec.data() + ((size_t)half * nblk + b) * 5 * FUS_GB;
+            for (int sl = 0; sl < FUS_GB; ++sl) R[4 * FUS_GB + sl] = make_float4(0.f, bits(0xFFFF), 0.f, 0.f);
+            const int t0 = b * FUS_GB, cnt = std::max(0, std::min(FUS_GB, npts - t0));
             std::vector<int> bucket[16];
+            std::vector<double> f1(cnt), f2(cnt);
+            std::vector<int> rc(cnt);
             for (int i = cnt - 1; i >= 0; --i) {
                 const int t = t0 + i, j = t / nl, l = lbeg + t % nl;
                 const double th = 2.0 * M_PI * (double)l / (double)p->n_theta;
-                const double p1 = N * xi[j] * cos(th), p2 = N * xi[j] * sin(th);
-                const long c0 = (long)ceil(p1 - 0.5 * W) - m1lo, r0 = (long)ceil(p2 - 0.5 * W) + H;
+                const double p1 = N * xi[j] * std::cos(th), p2 = N * xi[j] * std::sin(th);
+                const double m1 = std::ceil(p1 - 0.5 * W), m2 = std::ceil(p2 - 0.5 * W);
+                const long c0 = (long)m1 - m1lo, r0 = (long)m2 + H;
+                if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) return FFB_ERR_UNSUPPORTED;
+                f1[i] = p1 - m1;
+                f2[i] = p2 - m2;
+                rc[i] = (int)(r0 | (c0 << 16));
                 bucket[(r0 * SLD + c0) & 15].push_back(i);
             }
-            unsigned short *out = perm.data() + ((size_t)half * nblk + b) * FUS_GB;
             int pos = 0;
+            auto put = [&](int i) {
+                float w[16];
+                for (int q = 0; q < W; ++q) {
+                    w[q] = (float)phi(f2[i] - q);
+                    w[8 + q] = (float)phi(f1[i] - q);
+                }
+                for (int f = 0; f < 4; ++f) R[f * FUS_GB + pos] = make_float4(w[4 * f], w[4 * f + 1], w[4 * f + 2], w[4 * f + 3]);
+                R[4 * FUS_GB + pos] = make_float4(bits(rc[i]), bits(i), 0.f, 0.f);
+                ++pos;
+            };
             while (pos < cnt) {
                 int order[16];
                 for (int r = 0; r < 16; ++r) order[r] = r;
@@ -547,7 +578,7 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
                 int taken = 0;
                 for (int r : order) {
                     if (bucket[r].empty()) continue;
-                    out[pos++] = (unsigned short)bucket[r].back();
+                    put(bucket[r].back());
                     bucket[r].pop_back();
                     ++taken;
                 }
@@ -555,20 +586,20 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
                     int rb = 0;
                     for (int r = 1; r < 16; ++r)
                         if (bucket[r].size() > bucket[rb].size()) rb = r;
-                    out[pos++] = (unsigned short)bucket[rb].back();
+                    put(bucket[rb].back());
                     bucket[rb].pop_back();
                     ++taken;
                 }
             }
         }
     }
-    if (p->d_gperm) cudaFree(p->d_gperm);
-    p->d_gperm = nullptr;
-    e = ffb_check_cuda(cudaMalloc((void **)&p->d_gperm, sizeof(unsigned short) * perm.size()));
-    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_gperm, perm.data(), sizeof(unsigned short) * perm.size(),
+    if (p->d_nodes) cudaFree(p->d_nodes);
+    p->d_nodes = nullptr;
+    e = ffb_check_cuda(cudaMalloc((void **)&p->d_nodes, sizeof(float4) * rec.size()));
+    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_nodes, rec.data(), sizeof(float4) * rec.size(),
                                                cudaMemcpyHostToDevice, s));
     if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
-    p->gperm_nblk = nblk;
+    p->node_nblk = nblk;
     return e;
 }
 
