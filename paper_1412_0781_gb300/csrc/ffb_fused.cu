@@ -23,20 +23,20 @@
 // Both halves compute the same row transforms (phase 1); the columns and the
 // nodes are split.
 //
-// Node order in phase 3.  Each node gathers a W x W window of S starting at
-// S[r0][c0]; one 8-byte load of a half warp is served in a single shared-
-// memory wavefront when the 16 window origins r0 * SLD + c0 fall in distinct
-// 8-byte bank slots (the origin mod 16) or coincide.  Lanes that take
-// consecutive angles of one ring do not: about half of the gather loads
-// replay.  The plan therefore regroups, within every block of FUS_GB
-// consecutive nodes, the nodes into half warps with distinct slots (built on
-// the host from the node geometry, ffb_fused_prepare), and the kernel stages
-// each block's results in shared memory to store them in natural order.
-// The window origin and the 8 + 8 kernel weights of a node depend on the
-// geometry alone: the plan computes them once in float64 and stores them with
-// the node's slot (80 bytes per node, about 3 MB at N = 256 and less below,
-// read from L2 by every CTA), so phase 3 spends its issue slots on the 2 W^2
-// gather FMAs instead of 2 W kernel evaluations and the node's coordinates.
+// Node order in phase 3.  A node gathers the W x W window of S at
+// S[r0][c0] (W = 8).  Two nodes with the same r0 and window origins c0, c0 + d
+// (d in {0, 1}) form a unit: one thread reads the 8 x 9 union of their
+// windows once and forms both results, 36 gathers per node instead of 64
+// (phase 3 is bound by the shared-memory pipe).  One 8-byte load of a half
+// warp takes a single wavefront when the 16 unit origins r0 * SLD + c0 fall in
+// distinct 8-byte bank slots (the origin mod 16) or coincide, so the units are
+// ordered into half warps with distinct slots.  Everything here depends on
+// the geometry alone and is built by the plan in float64
+// (ffb_fused_prepare): blocks of whole rings (consecutive nodes t = j nl + l),
+// at most FUS_GU units and FUS_GN nodes each, and per unit the origin, both
+// nodes' 8 row weights and 9 column weights over the union (144 bytes, about
+// 2.6 MB at N = 256, read from L2 by every CTA).  The kernel stages a block's
+// results in shared memory and stores them in natural order.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -49,11 +49,14 @@
 #define FUS_WARPS 32                 // warps per CTA, each with an N-entry FFT buffer
 #define FUS_NT (32 * FUS_WARPS)      // threads per CTA
 #define RFFT_RB 32   // rings per ring-FFT CTA (one warp each)
-#define FUS_GB 2048   // nodes per regrouped block (phase 3)
+#define FUS_GU 2048   // units per phase-3 block (at most; two per thread)
+#define FUS_REC 9     // float4 fields of a unit record
 
-// rows of the shared-memory grid block and its row pitch (complex entries)
+// rows of the shared-memory grid block and its row pitch (complex entries):
+// MH (odd) columns hold the half plane, two more zero columns let a unit's
+// 9-column union start at the last window origin; the pitch stays odd
 __host__ __device__ constexpr int fus_mh(int N, int W) { return N / 2 + 1 + 2 * ((W + 1) / 2); }
-__host__ __device__ constexpr int fus_sld(int N, int W) { return (fus_mh(N, W) > N / 2) ? fus_mh(N, W) : N / 2; }
+__host__ __device__ constexpr int fus_sld(int N, int W) { return fus_mh(N, W) + 2; }
 
 // ---------------------------------------------------------------------------
 // Register FFTs.  dft_reg<M>: a length-M DFT held in one thread's registers
@@ -213,12 +216,13 @@ template <int N, int W>
 __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
                    const float2 *__restrict__ tw, int n_xi, int n_theta, int nq0,
-                   const float4 *__restrict__ nodes, int nblk, float2 *__restrict__ Fpol, int *status) {
+                   const float4 *__restrict__ units, const int2 *__restrict__ blocks, int nblk0, int nblk1,
+                   float2 *__restrict__ Fpol, int *status) {
     constexpr int L = N / 2;
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
     constexpr int SLD = fus_sld(N, W);            // row length of S
-    static_assert(2 * FUS_GB <= FUS_WARPS * N, "phase-3 staging must fit in the warp buffers");
+    constexpr int GN = FUS_WARPS * N / 2;         // nodes per block at most (two staged blocks)
     extern __shared__ float2 smz[];
     float2 *S = smz;                               // [MH][SLD]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,78 +273,89 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
         for (int q = 0; q < L / 32; ++q) z[q] = row[lane + 32 * q];
         warp_fft_halfzero<N>(z, buf, tw, lane);
         for (int c = lane; c < MH; c += 32) row[c] = buf[fswz<N>((c + m1lo) & (N - 1))];
+        if (lane < SLD - MH) row[MH + lane] = make_float2(0.f, 0.f);
         __syncwarp();
     }
     __syncthreads();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
-    // node t = j * nl + (l - lbeg); block b holds t in [b FUS_GB, (b + 1) FUS_GB),
-    // visited in the plan's regrouped order: record s of the block carries the
-    // node's window origin (r0, c0) in S, its 8 + 8 kernel weights and its slot
-    // in the block (the plan computes them once, in float64).  Results are
-    // staged in the (now idle) warp buffers, two blocks deep so that one
-    // barrier per block suffices, and stored in natural order.
-    static_assert(W == 8, "node records hold 8 + 8 weights");
+    // block b of the half covers the nodes t in [t0, t0 + cnt) (whole rings);
+    // unit record s holds, as FUS_REC planes of FUS_GU float4,
+    //   0, 1  row weights of node A    2, 3  row weights of node B
+    //   4, 5  column weights of A (columns 0..7 of the union)
+    //   6, 7  column weights of B, columns 0..7; 8.x: column 8
+    //   8.y   r0 | c0 << 16 (union origin in S)   8.z  slotA | slotB << 16
+    // slots index the block's nodes (0xFFFF: none; node B of a single unit
+    // carries zero weights).  Results are staged in the (now idle) warp
+    // buffers, two blocks deep so that one barrier per block suffices.
+    static_assert(W == 8, "unit records hold 8 + 8 row and 8 + 9 column weights");
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
     const int nl = (half == 0) ? nq0 : nh - nq0;
-    const int npts = n_xi * nl;
+    const int nblk = (half == 0) ? nblk0 : nblk1;
+    const int gb0 = (half == 0) ? 0 : nblk0;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
     float2 *stage0 = smz + MH * SLD;
     // t / nl as a multiply-high: exact for t < 2^32 / nl (nl >= 31 on this
     // path, so the multiplier does not overflow)
     const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;
-    for (int b = 0; b * FUS_GB < npts; ++b) {
-        const int t0 = b * FUS_GB;
-        const int cnt = min(FUS_GB, npts - t0);
-        float2 *stage = stage0 + (b & 1) * FUS_GB;
-        // record fields: [0], [1] row weights, [2], [3] column weights, [4] (origin, slot)
-        const float4 *rec = nodes + ((size_t)half * nblk + b) * 5 * FUS_GB;
-        for (int s = threadIdx.x; s < FUS_GB; s += FUS_NT) {
-            // all five loads issued together (every slot's record is valid)
-            const float4 meta = __ldg(&rec[4 * FUS_GB + s]);
-            const float4 y0 = __ldg(&rec[s]), y1 = __ldg(&rec[FUS_GB + s]);
-            const float4 x0 = __ldg(&rec[2 * FUS_GB + s]), x1 = __ldg(&rec[3 * FUS_GB + s]);
-            const int loc = __float_as_int(meta.y);
-            if (loc >= cnt) continue;
-            const int rc = __float_as_int(meta.x);
+    constexpr int GU = (FUS_GU < GN / 2) ? FUS_GU : GN / 2;   // units per block
+    for (int b = 0; b < nblk; ++b) {
+        const int2 tb = __ldg(&blocks[gb0 + b]);
+        const int t0 = tb.x, cnt = tb.y;
+        float2 *stage = stage0 + (b & 1) * GN;
+        const float4 *rec = units + (size_t)(gb0 + b) * FUS_REC * GU;
+#pragma unroll 1
+        for (int s = threadIdx.x; s < GU; s += FUS_NT) {
+            const float4 meta = __ldg(&rec[8 * GU + s]);
+            const int locs = __float_as_int(meta.z);
+            const int la = locs & 0xFFFF, lb = locs >> 16;
+            if (la >= cnt) continue;
+            const int rc = __float_as_int(meta.y);
             const int r0 = rc & 0xFFFF, c0 = rc >> 16;
-            float2 acc = make_float2(0.f, 0.f);
-            if (r0 + W > MH || c0 + W > MH) {
+            const float4 xa0 = __ldg(&rec[4 * GU + s]), xa1 = __ldg(&rec[5 * GU + s]);
+            const float4 xb0 = __ldg(&rec[6 * GU + s]), xb1 = __ldg(&rec[7 * GU + s]);
+            if (r0 + W > MH || c0 + W + 1 > SLD) {
                 ffb_flag(status, FFB_ERR_ARG);
-            } else {
-                const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-                // column sums over the W rows first: every row issues 2 W
-                // independent FMAs; the column weights are applied at the end
-                const float2 *base = S + r0 * SLD + c0;
-                float2 cs[W];
-#pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    const float2 g = base[q];
-                    cs[q] = make_float2(wy[0] * g.x, wy[0] * g.y);
-                }
-#pragma unroll
-                for (int bq = 1; bq < W; ++bq) {
-                    const float2 *row = base + bq * SLD;
-#pragma unroll
-                    for (int q = 0; q < W; ++q) {
-                        const float2 g = row[q];
-                        cs[q].x = fmaf(wy[bq], g.x, cs[q].x);
-                        cs[q].y = fmaf(wy[bq], g.y, cs[q].y);
-                    }
-                }
-                const float wx[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < W; q += 2) {
-                    ax0 = fmaf(wx[q], cs[q].x, ax0);
-                    ay0 = fmaf(wx[q], cs[q].y, ay0);
-                    ax1 = fmaf(wx[q + 1], cs[q + 1].x, ax1);
-                    ay1 = fmaf(wx[q + 1], cs[q + 1].y, ay1);
-                }
-                acc = make_float2(ax0 + ax1, ay0 + ay1);
+                stage[la] = make_float2(0.f, 0.f);
+                if (lb < cnt) stage[lb] = make_float2(0.f, 0.f);
+                continue;
             }
-            stage[loc] = acc;
+            const float wxa[8] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w};
+            const float wxb[9] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w, meta.x};
+            // row by row: the 9 values of the union row, interpolated along
+            // the row with each node's column weights, then weighted by the
+            // node's row weight (rows 0..3, then 4..7, four row weights of
+            // each node at a time)
+            const float2 *base = S + r0 * SLD + c0;
+            float2 aa = make_float2(0.f, 0.f), ab = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int h4 = 0; h4 < 2; ++h4) {
+                const float4 ya = __ldg(&rec[h4 * GU + s]), yb = __ldg(&rec[(2 + h4) * GU + s]);
+                const float wya[4] = {ya.x, ya.y, ya.z, ya.w};
+                const float wyb[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+                for (int b4 = 0; b4 < 4; ++b4) {
+                    const float2 *row = base + (4 * h4 + b4) * SLD;
+                    float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q <= W; ++q) {
+                        const float2 g = row[q];
+                        if (q < W) {
+                            ra.x = fmaf(wxa[q], g.x, ra.x);
+                            ra.y = fmaf(wxa[q], g.y, ra.y);
+                        }
+                        rb.x = fmaf(wxb[q], g.x, rb.x);
+                        rb.y = fmaf(wxb[q], g.y, rb.y);
+                    }
+                    aa.x = fmaf(wya[b4], ra.x, aa.x);
+                    aa.y = fmaf(wya[b4], ra.y, aa.y);
+                    ab.x = fmaf(wyb[b4], rb.x, ab.x);
+                    ab.y = fmaf(wyb[b4], rb.y, ab.y);
+                }
+            }
+            stage[la] = aa;
+            if (lb < cnt) stage[lb] = ab;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += FUS_NT) {
@@ -486,7 +501,8 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
     k_grid_interp_half<N, W><<<g, FUS_NT, smem, s>>>(d_images + (size_t)i0 * p->L * p->L, p->off, p->d_corr,
                                                      p->d_twN, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
-                                                     p->node_nblk, Fpol, p->d_status);
+                                                     p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
+                                                     p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -504,24 +520,22 @@ bool ffb_fused_supported(ffb_plan_t p) {
     return smem <= (size_t)optin;
 }
 
-// Node records of phase 3 (see the file header): for each half and block of
-// FUS_GB nodes, FUS_GB records in the regrouped lane order, stored as five
-// float4 planes [block][field][slot] so that every field is one coalesced
-// 16-byte load per lane:
-//   fields 0, 1  row weights phi(f2 - b), b = 0..7, f2 = p2 - m2 (rows of S)
-//   field  2, 3  column weights phi(f1 - q), q = 0..7, f1 = p1 - m1
-//   field  4     (r0 | c0 << 16, slot in the block, 0, 0) as int bits
-// with p = N xi_j (cos theta_l, sin theta_l) the node in grid units,
-// m = ceil(p - W/2) the first tap, phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1))
-// the ES kernel (Sec. III, type-2 NUFFT), all in float64.  Slots past the
-// block's node count hold slot 0xFFFF.  Lane order: greedy per half warp, one
-// node from every nonempty bank slot (r0 SLD + c0) mod 16, fullest slot first,
-// then fill from the fullest.
+// Units and blocks of phase 3 (see the file header).  For node t = j nl + l'
+// of a half, p = N xi_j (cos theta_l, sin theta_l) in grid units, the window
+// starts at m = ceil(p - W/2) and the weights are phi(f - b), f = p - m,
+// b = 0..7, phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) the ES kernel
+// (Sec. III, type-2 NUFFT), in float64.  A block takes whole rings while its
+// nodes pair into at most GU units and number at most GN.  Pairing within a
+// block: nodes sorted by (r0, c0), each joined with the next when that has the
+// same r0 and c0 at most one larger (left to right, a maximum matching of
+// this interval structure); the rest are single units.  Units are ordered per
+// half warp with distinct bank slots (r0 SLD + c0) mod 16: one unit from every
+// nonempty slot, fullest slot first, then fill from the fullest.
 int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
     const int N = p->N, W = p->w, H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W);
     if (W != 8) return FFB_ERR_UNSUPPORTED;
+    const int GN = FUS_WARPS * N / 2, GU = std::min(FUS_GU, GN / 2);
     const int nh = p->n_theta / 2;
-    const int nblk = (p->n_xi * p->nq0 + FUS_GB - 1) / FUS_GB;   // half 0 has the most nodes
     std::vector<double> xi(p->n_xi);
     int e = ffb_check_cuda(cudaMemcpyAsync(xi.data(), p->d_xi, sizeof(double) * p->n_xi, cudaMemcpyDeviceToHost, s));
     if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
@@ -535,43 +549,101 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
         std::memcpy(&f, &v, sizeof f);
         return f;
     };
-    std::vector<float4> rec((size_t)2 * nblk * 5 * FUS_GB, make_float4(0.f, 0.f, 0.f, 0.f));
+    struct Node {
+        int r0, c0;
+        double f1, f2;
+    };
+    std::vector<float4> rec;
+    std::vector<int2> blk;
+    int nb[2] = {0, 0};
     for (int half = 0; half < 2; ++half) {
         const int lbeg = (half == 0) ? 0 : p->nq0;
         const int nl = (half == 0) ? p->nq0 : nh - p->nq0;
         const int npts = p->n_xi * nl;
         const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-        for (int b = 0; b < nblk; ++b) {
-            float4 *R = rec.data() + ((size_t)half * nblk + b) * 5 * FUS_GB;
-            for (int sl = 0; sl < FUS_GB; ++sl) R[4 * FUS_GB + sl] = make_float4(0.f, bits(0xFFFF), 0.f, 0.f);
-            const int t0 = b * FUS_GB, cnt = std::max(0, std::min(FUS_GB, npts - t0));
+        if (nl > GN) return FFB_ERR_UNSUPPORTED;
+        std::vector<Node> nd(npts);
+        for (int t = 0; t < npts; ++t) {
+            const int j = t / nl, l = lbeg + t % nl;
+            const double th = 2.0 * M_PI * (double)l / (double)p->n_theta;
+            const double p1 = N * xi[j] * std::cos(th), p2 = N * xi[j] * std::sin(th);
+            const double m1 = std::ceil(p1 - 0.5 * W), m2 = std::ceil(p2 - 0.5 * W);
+            const int c0 = (int)m1 - m1lo, r0 = (int)m2 + H;
+            if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) return FFB_ERR_UNSUPPORTED;
+            nd[t] = {r0, c0, p1 - m1, p2 - m2};
+        }
+        // units of the nodes [t0, t1): (A, B) block-local, B = -1 for a single
+        auto pair_up = [&](int t0, int t1) {
+            std::vector<int> ord(t1 - t0);
+            for (int i = 0; i < t1 - t0; ++i) ord[i] = i;
+            std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+                const Node &u = nd[t0 + x], &v = nd[t0 + y];
+                return (u.r0 != v.r0) ? u.r0 < v.r0 : (u.c0 != v.c0) ? u.c0 < v.c0 : x < y;
+            });
+            std::vector<std::pair<int, int>> un;
+            for (size_t i = 0; i < ord.size();) {
+                if (i + 1 < ord.size()) {
+                    const Node &u = nd[t0 + ord[i]], &v = nd[t0 + ord[i + 1]];
+                    if (u.r0 == v.r0 && v.c0 - u.c0 <= 1) {
+                        un.push_back({ord[i], ord[i + 1]});
+                        i += 2;
+                        continue;
+                    }
+                }
+                un.push_back({ord[i], -1});
+                ++i;
+            }
+            return un;
+        };
+        for (int t0 = 0; t0 < npts;) {
+            // grow by whole rings while the block fits
+            int t1 = std::min(npts, t0 + nl);
+            std::vector<std::pair<int, int>> un = pair_up(t0, t1);
+            if ((int)un.size() > GU) return FFB_ERR_UNSUPPORTED;
+            while (t1 < npts) {
+                const int t2 = std::min(npts, t1 + nl);
+                if (t2 - t0 > GN) break;
+                std::vector<std::pair<int, int>> u2 = pair_up(t0, t2);
+                if ((int)u2.size() > GU) break;
+                un.swap(u2);
+                t1 = t2;
+            }
+            const int cnt = t1 - t0;
+            blk.push_back(make_int2(t0, cnt));
+            const size_t base = rec.size();
+            rec.resize(base + (size_t)FUS_REC * GU, make_float4(0.f, 0.f, 0.f, 0.f));
+            float4 *R = rec.data() + base;
+            for (int sl = 0; sl < GU; ++sl) R[8 * GU + sl] = make_float4(0.f, 0.f, bits(0xFFFF | (0xFFFF << 16)), 0.f);
             std::vector<int> bucket[16];
-            std::vector<double> f1(cnt), f2(cnt);
-            std::vector<int> rc(cnt);
-            for (int i = cnt - 1; i >= 0; --i) {
-                const int t = t0 + i, j = t / nl, l = lbeg + t % nl;
-                const double th = 2.0 * M_PI * (double)l / (double)p->n_theta;
-                const double p1 = N * xi[j] * std::cos(th), p2 = N * xi[j] * std::sin(th);
-                const double m1 = std::ceil(p1 - 0.5 * W), m2 = std::ceil(p2 - 0.5 * W);
-                const long c0 = (long)m1 - m1lo, r0 = (long)m2 + H;
-                if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) return FFB_ERR_UNSUPPORTED;
-                f1[i] = p1 - m1;
-                f2[i] = p2 - m2;
-                rc[i] = (int)(r0 | (c0 << 16));
-                bucket[(r0 * SLD + c0) & 15].push_back(i);
+            for (int u = (int)un.size() - 1; u >= 0; --u) {
+                const Node &a = nd[t0 + un[u].first];
+                bucket[(a.r0 * SLD + a.c0) & 15].push_back(u);
             }
             int pos = 0;
-            auto put = [&](int i) {
-                float w[16];
+            auto put = [&](int u) {
+                const int ia = un[u].first, ib = un[u].second;
+                const Node &a = nd[t0 + ia];
+                float w[34] = {};   // row A, row B, column A (8), column B (9)
                 for (int q = 0; q < W; ++q) {
-                    w[q] = (float)phi(f2[i] - q);
-                    w[8 + q] = (float)phi(f1[i] - q);
+                    w[q] = (float)phi(a.f2 - q);
+                    w[16 + q] = (float)phi(a.f1 - q);
                 }
-                for (int f = 0; f < 4; ++f) R[f * FUS_GB + pos] = make_float4(w[4 * f], w[4 * f + 1], w[4 * f + 2], w[4 * f + 3]);
-                R[4 * FUS_GB + pos] = make_float4(bits(rc[i]), bits(i), 0.f, 0.f);
+                if (ib >= 0) {
+                    const Node &bn = nd[t0 + ib];
+                    const int d = bn.c0 - a.c0;   // 0 or 1
+                    for (int q = 0; q < W; ++q) {
+                        w[8 + q] = (float)phi(bn.f2 - q);
+                        w[24 + d + q] = (float)phi(bn.f1 - q);
+                    }
+                }
+                for (int f = 0; f < 8; ++f)
+                    R[f * GU + pos] = make_float4(w[4 * f], w[4 * f + 1], w[4 * f + 2], w[4 * f + 3]);
+                const int locs = ia | ((ib >= 0 ? ib : 0xFFFF) << 16);
+                R[8 * GU + pos] = make_float4(w[32], bits(a.r0 | (a.c0 << 16)), bits(locs), 0.f);
                 ++pos;
             };
-            while (pos < cnt) {
+            const int nu = (int)un.size();
+            while (pos < nu) {
                 int order[16];
                 for (int r = 0; r < 16; ++r) order[r] = r;
                 std::stable_sort(order, order + 16, [&](int x, int y) { return bucket[x].size() > bucket[y].size(); });
@@ -582,7 +654,7 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
                     bucket[r].pop_back();
                     ++taken;
                 }
-                while (taken < 16 && pos < cnt) {
+                while (taken < 16 && pos < nu) {
                     int rb = 0;
                     for (int r = 1; r < 16; ++r)
                         if (bucket[r].size() > bucket[rb].size()) rb = r;
@@ -591,15 +663,23 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
                     ++taken;
                 }
             }
+            ++nb[half];
+            t0 = t1;
         }
     }
     if (p->d_nodes) cudaFree(p->d_nodes);
+    if (p->d_node_blk) cudaFree(p->d_node_blk);
     p->d_nodes = nullptr;
+    p->d_node_blk = nullptr;
     e = ffb_check_cuda(cudaMalloc((void **)&p->d_nodes, sizeof(float4) * rec.size()));
+    if (!e) e = ffb_check_cuda(cudaMalloc((void **)&p->d_node_blk, sizeof(int2) * blk.size()));
     if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_nodes, rec.data(), sizeof(float4) * rec.size(),
                                                cudaMemcpyHostToDevice, s));
+    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_node_blk, blk.data(), sizeof(int2) * blk.size(),
+                                               cudaMemcpyHostToDevice, s));
     if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
-    p->node_nblk = nblk;
+    p->node_nblk[0] = nb[0];
+    p->node_nblk[1] = nb[1];
     return e;
 }
 

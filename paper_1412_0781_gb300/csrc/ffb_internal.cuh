@@ -69,8 +69,9 @@ struct ffb_plan_s {
     float2 *d_G = nullptr;       // [chunk][Mh][N]
     float *d_Fhat = nullptr;     // [k_max+1][chunk][2][n_xi]
     float2 *d_Fpol = nullptr;    // [chunk][n_xi][n_theta/2] (fused path)
-    float4 *d_nodes = nullptr;   // [2][node_nblk][5][2048] phase-3 node records (fused path)
-    int node_nblk = 0;
+    float4 *d_nodes = nullptr;   // [blocks][9][units] phase-3 unit records (fused path)
+    int2 *d_node_blk = nullptr;  // [blocks] (first node, node count), half 0 then half 1
+    int node_nblk[2] = {0, 0};   // blocks per half
     // covariance state
     double *d_acc = nullptr;     // [cov_total] sum Re(a a^*), k = 0 shifted
     double *d_sum0 = nullptr;    // [p0] sum (a0 - shift)
