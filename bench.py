@@ -405,7 +405,9 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": "precision stack: n=100000 Gaussian-blob images L=128 R=64 c=0.5 "
                                        "SNR=1/10, eps=1e-6", "L": L_, "n_per_gpu": n, "precision": head,
-                           "l2": "inputs (6.55 GB) larger than L2, no flush"},
+                           "l2": "inputs (6.55 GB) larger than L2, no flush",
+                           "polar_variant": {0: "separate grid and interpolation kernels", 1: "grid in shared memory",
+                                             2: "grid in shared memory, CTA-pair clusters"}[r["plan"].polar_variant]},
                 "precisions": {p: {"images_per_s": world * n / (v["ms"] / args.steps / 1e3),
                                    "kernel_ms": {c: round(t[0] / args.steps, 4) for c, t in v["prof"].items()}}
                                for p, v in results.items()},

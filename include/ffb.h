@@ -86,10 +86,14 @@ int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
 /* Releases everything the plan owns.  NULL is accepted. */
 int ffb_plan_destroy(ffb_plan_t plan);
 
-/* Sizes of the plan, written to h_info[0..9]:
+/* Sizes of the plan, written to h_info[0..10]:
  *   0 L, 1 k_max, 2 P (= sum_{k>=0} p_k), 3 n_xi, 4 n_theta,
  *   5 N (oversampled grid), 6 kernel width w, 7 precision,
- *   8 max_k p_k, 9 images per internal chunk. */
+ *   8 max_k p_k, 9 images per internal chunk, 10 polar transform variant
+ *   (0 separate grid / interpolation kernels, 1 grid in shared memory,
+ *   2 as 1 with the two CTAs of an image in a cluster sharing the FFTs;
+ *   2 is chosen when such clusters fill every SM, unless the environment
+ *   variable FFB_FUSED_CLUSTER is "0" when the plan is created). */
 int ffb_plan_info(ffb_plan_t plan, int *h_info);
 
 /* p_k and offset[k] (k = 0..k_max), host arrays of k_max+1 ints. */

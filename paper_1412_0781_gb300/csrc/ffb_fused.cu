@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -212,7 +213,20 @@ __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, 
     __syncwarp();
 }
 
-template <int N, int W>
+// distributed shared memory of a thread-block cluster: a float2 store into the
+// peer CTA's shared memory (cluster-space address from mapa), and the
+// cluster-wide barrier with release / acquire ordering of shared memory
+__device__ __forceinline__ void st_peer(unsigned addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CL: the two CTAs of an image form a cluster and split the row and column
+// transforms, which are the same for both halves: each computes half of them
+// and writes the results into its own and its peer's grid block.
+template <int N, int W, bool CL>
 __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
                    const float2 *__restrict__ tw, int n_xi, int n_theta, int nq0,
@@ -230,10 +244,23 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     const int half = blockIdx.x;
     const int img = blockIdx.y;
     const float *im = images + (size_t)img * L * L;
+    // cluster: the peer's S in the cluster window, this CTA's share of the
+    // transforms (every second one)
+    unsigned peerS = 0;
+    int part = 0, nparts = 1;
+    if constexpr (CL) {
+        unsigned rank;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+        const unsigned own = (unsigned)__cvta_generic_to_shared(smz);
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(peerS) : "r"(own), "r"(rank ^ 1u));
+        part = (int)rank;
+        nparts = 2;
+    }
 
     // ---- phase 1: row transforms (two pixel rows per complex FFT) --------
+    // (cluster: this CTA's pixel rows are a1 in [part L/2, (part + 1) L/2))
     bool bad = false;
-    for (int rp = warp; rp < L / 2; rp += FUS_WARPS) {
+    for (int rp = part * (L / 2 / nparts) + warp; rp < (part + 1) * (L / 2 / nparts); rp += FUS_WARPS) {
         const int a1 = 2 * rp;
         float x[L / 32], y[L / 32];
 #pragma unroll
@@ -263,10 +290,21 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     }
     if (bad) ffb_flag(status, FFB_ERR_NONFINITE);
     __syncthreads();
+    if constexpr (CL) {
+        // the peer transforms the rows e = 1 - part (mod 2) of S: send it this
+        // CTA's half of each, as contiguous row segments
+        for (int e = (part ^ 1) + 2 * warp; e < MH; e += 2 * FUS_WARPS) {
+            const int i0 = e * SLD + part * (L / 2);
+            for (int a = lane; a < L / 2; a += 32) st_peer(peerS + 8u * (unsigned)(i0 + a), S[i0 + a]);
+        }
+        cluster_sync_all();
+    }
 
     // ---- phase 2: column transforms, in place per row of S ---------------
+    // (cluster: a row is transformed once and both halves' columns written)
     const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-    for (int e = warp; e < MH; e += FUS_WARPS) {
+    const int m1lo_peer = (half == 0) ? -(N / 2) - H : -H;
+    for (int e = part + nparts * warp; e < MH; e += nparts * FUS_WARPS) {
         float2 *row = S + e * SLD;
         float2 z[L / 32];
 #pragma unroll
@@ -274,9 +312,17 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
         warp_fft_halfzero<N>(z, buf, tw, lane);
         for (int c = lane; c < MH; c += 32) row[c] = buf[fswz<N>((c + m1lo) & (N - 1))];
         if (lane < SLD - MH) row[MH + lane] = make_float2(0.f, 0.f);
+        if constexpr (CL) {
+            const unsigned prow = peerS + 8u * (unsigned)(e * SLD);
+            for (int c = lane; c < MH; c += 32) st_peer(prow + 8u * c, buf[fswz<N>((c + m1lo_peer) & (N - 1))]);
+            if (lane < SLD - MH) st_peer(prow + 8u * (MH + lane), make_float2(0.f, 0.f));
+        }
         __syncwarp();
     }
-    __syncthreads();
+    // (cluster: the peer's writes into this block are complete and visible,
+    // and no CTA touches its peer's shared memory after this barrier)
+    if constexpr (CL) cluster_sync_all();
+    else __syncthreads();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
     // block b of the half covers the nodes t in [t0, t0 + cnt) (whole rings);
@@ -487,24 +533,86 @@ static size_t fused_smem() {
     return sizeof(float2) * ((size_t)fus_mh(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * N);
 }
 
+// 1 when the cluster variant keeps every SM busy: clusters of two CTAs (one
+// per SM) can occupy all SMs at once; FFB_FUSED_CLUSTER=0 in the environment
+// at plan creation selects the plain variant
+template <int N, int W>
+static int fused_cluster_ok() {
+    const char *ev = std::getenv("FFB_FUSED_CLUSTER");
+    if (ev && ev[0] == '0') return 0;
+    const size_t smem = fused_smem<N, W>();
+    if (cudaFuncSetAttribute(k_grid_interp_half<N, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0, sms = 0, ncl = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1024);
+    cfg.blockDim = dim3(FUS_NT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_grid_interp_half<N, W, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (2 * ncl >= sms) ? 1 : 0;
+}
+
 template <int N, int W>
 static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {
-    static int attr = 0;
+    static int attr = 0, attr_cl = 0;
     const size_t smem = fused_smem<N, W>();
-    if (attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_grid_interp_half<N, W>,
+    const bool cl = p->fused == 2;
+    int &done = cl ? attr_cl : attr;
+    if (done < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(cl ? k_grid_interp_half<N, W, true> : k_grid_interp_half<N, W, false>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
-        attr = (int)smem;
+        done = (int)smem;
     }
-    dim3 g(2, m);
+    const float *img = d_images + (size_t)i0 * p->L * p->L;
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
-    k_grid_interp_half<N, W><<<g, FUS_NT, smem, s>>>(d_images + (size_t)i0 * p->L * p->L, p->off, p->d_corr,
-                                                     p->d_twN, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
-                                                     p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
-                                                     p->d_status);
+    if (cl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2, m);
+        cfg.blockDim = dim3(FUS_NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_grid_interp_half<N, W, true>, img, p->off,
+                                                  (const float *)p->d_corr, (const float2 *)p->d_twN, p->n_xi,
+                                                  p->n_theta, p->nq0, (const float4 *)p->d_nodes,
+                                                  (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1],
+                                                  Fpol, p->d_status));
+        p->launches++;
+        return e;
+    }
+    k_grid_interp_half<N, W, false><<<dim3(2, m), FUS_NT, smem, s>>>(
+        img, p->off, p->d_corr, p->d_twN, p->n_xi, p->n_theta, p->nq0, p->d_nodes, p->d_node_blk,
+        p->node_nblk[0], p->node_nblk[1], Fpol, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
+}
+
+int ffb_fused_mode(ffb_plan_t p) {
+    if (p->N == 256) return 1 + fused_cluster_ok<256, 8>();
+    if (p->N == 128) return 1 + fused_cluster_ok<128, 8>();
+    return 1;
 }
 
 bool ffb_fused_supported(ffb_plan_t p) {

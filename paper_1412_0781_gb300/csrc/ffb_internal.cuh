@@ -46,7 +46,7 @@ struct ffb_plan_s {
     FftPlanDev fftN, fftT;
     int chunk;           // images per internal chunk
     int nq0;             // half-ring angles with cos(theta) >= 0 (fused path split)
-    int fused;           // 1: grid held in shared memory (ffb_fused.cu)
+    int fused;           // 1: grid held in shared memory (ffb_fused.cu); 2: as 1, in CTA-pair clusters
     // device tables (float64 setup results)
     double *d_zeros = nullptr;   // [P]
     double *d_xi = nullptr;      // [n_xi]
@@ -304,6 +304,7 @@ int ffb_ensure_scratch(ffb_plan_t plan);
 int ffb_ensure_scratch_grid(ffb_plan_t plan);
 bool ffb_fused_supported(ffb_plan_t plan);
 int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
+int ffb_fused_mode(ffb_plan_t plan);   // 1 plain, 2 cluster variant of the fused kernel
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
                            cudaStream_t s);
 struct RingOut {

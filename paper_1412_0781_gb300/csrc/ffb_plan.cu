@@ -413,7 +413,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
     if (st == FFB_OK) st = build_plan(p, s);
     if (st == FFB_OK && p->precision != FFB_FP32 && !ffb_tc_supported(p)) st = FFB_ERR_UNSUPPORTED;
     if (st == FFB_OK && ffb_fused_supported(p)) {
-        p->fused = 1;
+        p->fused = ffb_fused_mode(p);
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
         st = ffb_fused_prepare(p, s);
     }
@@ -445,6 +445,7 @@ extern "C" int ffb_plan_info(ffb_plan_t p, int *info) {
     info[7] = p->precision;
     info[8] = p->pmax;
     info[9] = p->chunk;
+    info[10] = p->fused;
     return FFB_OK;
 }
 

@@ -134,10 +134,10 @@ class Plan:
         _check(lib.ffb_plan(ctypes.byref(h), int(L), float(c), R, float(eps), prec, _stream(stream)),
                "ffb_plan")
         self._h = h
-        info = (ctypes.c_int * 10)()
+        info = (ctypes.c_int * 11)()
         _check(lib.ffb_plan_info(h, info), "ffb_plan_info")
         (self.L, self.k_max, self.P, self.n_xi, self.n_theta, self.N, self.w,
-         self.precision, self.pmax, self.chunk) = list(info)
+         self.precision, self.pmax, self.chunk, self.polar_variant) = list(info)
         self.c, self.R, self.eps = float(c), R, float(eps)
         pk = (ctypes.c_int * (self.k_max + 1))()
         off = (ctypes.c_int * (self.k_max + 1))()

@@ -133,6 +133,24 @@ def test_rotation_reflection_on_gpu(dev):
     assert rel(af, a.conj()) <= TOL
 
 
+@pytest.mark.parametrize("L", [64, 128])
+def test_fused_cluster_variant_equals_plain(dev, L, monkeypatch):
+    """The grid kernel's two variants (the CTA pair of an image in a cluster
+    sharing the row and column FFTs through distributed shared memory, or each
+    CTA computing them alone) run the same arithmetic on the same values: the
+    polar samples and the coefficients agree bit for bit."""
+    gp = gplan(L)
+    monkeypatch.setenv("FFB_FUSED_CLUSTER", "0")
+    plain = Plan(L, 0.5, L / 2, eps=1e-6)
+    monkeypatch.delenv("FFB_FUSED_CLUSTER")
+    assert plain.polar_variant == 1 and gp.polar_variant in (1, 2)
+    n = 2 * gp.chunk + 5      # two full launches and a ragged one
+    imgs, _, _ = data.blob_stack(data.StackSpec(n, L, L / 2, 8, (1.5, 6.0), 0.2, 4242), device=dev)
+    assert torch.equal(gp.polar(imgs[:7]), plain.polar(imgs[:7]))
+    assert torch.equal(gp.expand(imgs), plain.expand(imgs))
+    plain.close()
+
+
 @pytest.mark.parametrize("which,samples", [("fp32", (0, 9999, 19999)), ("precision", (0, 50000, 99999))])
 def test_expand_full_size_l128_sampled(dev, which, samples):
     """Full-size L = 128 stacks (n = 20000 and n = 100000, the benchmark's
