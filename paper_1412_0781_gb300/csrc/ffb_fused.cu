@@ -32,8 +32,8 @@
 // distinct 8-byte bank slots (the origin mod 16) or coincide, so the units are
 // ordered into half warps with distinct slots.  Everything here depends on
 // the geometry alone and is built by the plan in float64
-// (ffb_fused_prepare): blocks of whole rings (consecutive nodes t = j nl + l),
-// at most FUS_GU units and FUS_GN nodes each, and per unit the origin, both
+// (ffb_fused_prepare): blocks of consecutive nodes t = j nl + l, at most
+// FUS_GU units each, and per unit the origin, both
 // nodes' 8 row weights and 9 column weights over the union (144 bytes, about
 // 2.6 MB at N = 256, read from L2 by every CTA).  The kernel stages a block's
 // results in shared memory and stores them in natural order.
@@ -325,7 +325,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     else __syncthreads();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
-    // block b of the half covers the nodes t in [t0, t0 + cnt) (whole rings);
+    // block b of the half covers the nodes t in [t0, t0 + cnt);
     // unit record s holds, as FUS_REC planes of FUS_GU float4,
     //   0, 1  row weights of node A    2, 3  row weights of node B
     //   4, 5  column weights of A (columns 0..7 of the union)
@@ -632,8 +632,8 @@ bool ffb_fused_supported(ffb_plan_t p) {
 // of a half, p = N xi_j (cos theta_l, sin theta_l) in grid units, the window
 // starts at m = ceil(p - W/2) and the weights are phi(f - b), f = p - m,
 // b = 0..7, phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) the ES kernel
-// (Sec. III, type-2 NUFFT), in float64.  A block takes whole rings while its
-// nodes pair into at most GU units and number at most GN.  Pairing within a
+// (Sec. III, type-2 NUFFT), in float64.  A block takes the longest run of
+// consecutive nodes, at most GN, that pairs into at most GU units.  Pairing within a
 // block: nodes sorted by (r0, c0), each joined with the next when that has the
 // same r0 and c0 at most one larger (left to right, a maximum matching of
 // this interval structure); the rest are single units.  Units are ordered per
@@ -704,18 +704,16 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             return un;
         };
         for (int t0 = 0; t0 < npts;) {
-            // grow by whole rings while the block fits
-            int t1 = std::min(npts, t0 + nl);
-            std::vector<std::pair<int, int>> un = pair_up(t0, t1);
-            if ((int)un.size() > GU) return FFB_ERR_UNSUPPORTED;
-            while (t1 < npts) {
-                const int t2 = std::min(npts, t1 + nl);
-                if (t2 - t0 > GN) break;
-                std::vector<std::pair<int, int>> u2 = pair_up(t0, t2);
-                if ((int)u2.size() > GU) break;
-                un.swap(u2);
-                t1 = t2;
+            // the longest node range whose units fit (the unit count of a
+            // range never decreases as it grows): full blocks of GU units
+            int lo = t0 + 1, hi = std::min(npts, t0 + GN);
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if ((int)pair_up(t0, mid).size() <= GU) lo = mid;
+                else hi = mid - 1;
             }
+            const int t1 = lo;
+            std::vector<std::pair<int, int>> un = pair_up(t0, t1);
             const int cnt = t1 - t0;
             blk.push_back(make_int2(t0, cnt));
             const size_t base = rec.size();
@@ -809,7 +807,7 @@ static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOu
     }
     dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
     ProfScope ps(p, FFB_KC_RING_FFT, s);
-    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, p->chunk, p->d_twT, o.p0, o.p1, o.ld);
+    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, o.lead, p->d_twT, o.p0, o.p1, o.ld);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }

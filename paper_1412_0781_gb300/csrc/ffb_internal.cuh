@@ -309,11 +309,15 @@ int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, i
                            cudaStream_t s);
 struct RingOut {
     int fmt;           // FFB_FMT_*
-    void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra)
+    void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra), at the launch's first image
     int ld;            // row length of the planes (>= n_xi)
+    int lead;          // images per k in the planes
 };
 int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, const RingOut &out, cudaStream_t s);
 int ffb_tc_prepare(ffb_plan_t plan, cudaStream_t s, RingOut *out);
+// chunks whose ring spectra one tensor-core quadrature launch takes (>= 1;
+// valid after ffb_tc_prepare)
+int ffb_tc_group(ffb_plan_t plan);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);

@@ -20,6 +20,7 @@
 // Every wait is bounded by a clock budget; a timeout latches FFB_ERR_TIMEOUT,
 // waits (bounded) for in-flight copies, frees TMEM and returns.
 #include <cudaTypedefs.h>
+#include <algorithm>
 #include <cuda_bf16.h>
 
 #include "ffb_internal.cuh"
@@ -304,8 +305,9 @@ static int make_map(CUtensorMap *map, void *base, bool bf16, uint64_t d0, uint64
 struct TcState {
     int prepared = -1;       // precision the tables were built for
     int BN = 0, tmem_cols = 0, ld = 0;
+    int grp = 1;                           // chunks per quadrature launch
     void *bhi = nullptr, *blo = nullptr;   // padded radial tables [k][BN][ld]
-    void *ahi = nullptr, *alo = nullptr;   // ring spectra planes [k][2 chunk][ld]
+    void *ahi = nullptr, *alo = nullptr;   // ring spectra planes [k][2 grp chunk][ld]
     CUtensorMap mA0, mA1, mB0, mB1;
 };
 
@@ -378,7 +380,14 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
                 *q = nullptr;
             }
         const size_t nb = (size_t)(p->k_max + 1) * t->BN * t->ld;
-        const size_t na = (size_t)(p->k_max + 1) * p->chunk * 2 * t->ld;
+        // the fused path's ring FFT writes the planes of several chunks before
+        // one quadrature launch takes them all (fewer, fuller launches), as
+        // many as keep the planes within 64 MiB, so that they stay in L2 next
+        // to the polar buffer; the separate-kernel path converts one chunk
+        const int np = (p->precision == FFB_TF32X3 || p->precision == FFB_BF16X3) ? 2 : 1;
+        const size_t per_chunk = (size_t)(p->k_max + 1) * p->chunk * 2 * t->ld * es * np;
+        t->grp = p->fused ? (int)std::max<size_t>(1, std::min<size_t>(4, ((size_t)64 << 20) / per_chunk)) : 1;
+        const size_t na = (size_t)(p->k_max + 1) * t->grp * p->chunk * 2 * t->ld;
         int e;
         if ((e = ffb_check_cuda(cudaMalloc(&t->bhi, nb * es)))) return e;
         if ((e = ffb_check_cuda(cudaMalloc(&t->blo, nb * es)))) return e;
@@ -396,7 +405,7 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
                                                  t->bhi, t->blo);
         p->launches++;
         if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
-        const uint64_t rows = 2ull * p->chunk;
+        const uint64_t rows = 2ull * t->grp * p->chunk;
         if ((e = make_map(&t->mA0, t->ahi, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
         if ((e = make_map(&t->mA1, t->alo, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
         if ((e = make_map(&t->mB0, t->bhi, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
@@ -413,9 +422,12 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
         out->p0 = t->ahi;
         out->p1 = t->alo;
         out->ld = t->ld;
+        out->lead = t->grp * p->chunk;
     }
     return FFB_OK;
 }
+
+int ffb_tc_group(ffb_plan_t p) { return p->tc ? ((TcState *)p->tc)->grp : 1; }
 
 template <int KIND, int NPA, int NPB, int NPROD>
 static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {

@@ -56,6 +56,28 @@ def test_tc_quadrature_matches_oracle(dev, L, n, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("L,prec", [(64, "bf16x3"), (128, "bf16x3"), (128, "tf32x3")])
+def test_tc_grouped_quadrature_ragged_and_independent(dev, L, prec):
+    """One quadrature launch takes the ring spectra of several chunks (up to
+    four, as many as fit the plane budget): a stack of two full groups and a
+    ragged one gives every image the coefficients it gets alone, and sampled
+    images at the chunk and group seams match the oracle."""
+    plan = Plan(L, 0.5, L / 2, eps=1e-6, precision=prec)
+    per = 4 * plan.chunk                       # at least one group
+    n = 2 * per + 37
+    spec = data.StackSpec(n, L, L / 2, 12, (2.0 * L / 128, 8.0 * L / 128), 0.1, 4711 + L)
+    imgs, _, _ = data.blob_stack(spec, device=dev)
+    coef = plan.expand(imgs)
+    sel = [0, plan.chunk - 1, plan.chunk, 2 * plan.chunk, per - 1, per, 2 * per - 1, 2 * per, n - 1]
+    alone = plan.expand(imgs[sel].contiguous())
+    assert torch.equal(coef[sel], alone)
+    op = fb.make_plan(L, 0.5, L / 2)
+    ref = fb.expand(op, imgs[sel].double().cpu().numpy())
+    a = torch.view_as_complex(coef[sel].cpu()).numpy().astype(np.complex128)
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= GATES[prec]
+    plan.close()
+
+
 @pytest.mark.parametrize("L,n", [(32, 200), (128, 3000)])
 def test_tc_covariance_matches_oracle(dev, L, n):
     """Covariance blocks (Eqs. ck, ck_0) from the tensor-core SYRK, fed the
