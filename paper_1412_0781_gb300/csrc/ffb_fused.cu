@@ -89,7 +89,11 @@ __device__ __forceinline__ float2 w16(int e) {
 // in-register length-M DFT, natural order in and out (forward)
 template <int M>
 __device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
-    if constexpr (M == 4) {
+    if constexpr (M == 2) {
+        const float2 a = x[0];
+        x[0] = cadd(a, x[1]);
+        x[1] = csub(a, x[1]);
+    } else if constexpr (M == 4) {
         dft4<false>(x);
     } else if constexpr (M == 8) {
         float2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
@@ -104,7 +108,7 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
             x[k + 4] = csub(e[k], t);
         }
     } else {
-        static_assert(M == 16, "M in {4, 8, 16}");
+        static_assert(M == 16, "M in {2, 4, 8, 16}");
         float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) {
@@ -122,6 +126,55 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
         }
     }
 }
+
+// length-H DFT of a real sequence u (H = 2, 4, 8), E[H - j] = conj E[j]
+template <int H>
+__device__ __forceinline__ void dft_real(const float (&u)[H], float2 (&E)[H]) {
+    if constexpr (H == 2) {
+        E[0] = make_float2(u[0] + u[1], 0.f);
+        E[1] = make_float2(u[0] - u[1], 0.f);
+    } else if constexpr (H == 4) {
+        const float t0 = u[0] + u[2], t1 = u[0] - u[2], t2 = u[1] + u[3], t3 = u[1] - u[3];
+        E[0] = make_float2(t0 + t2, 0.f);
+        E[1] = make_float2(t1, -t3);
+        E[2] = make_float2(t0 - t2, 0.f);
+        E[3] = make_float2(t1, t3);
+    } else {
+        static_assert(H == 8, "H in {2, 4, 8}");
+        // even / odd samples: real length-4 DFTs A, B; E[j] = A[j] + W8^j B[j]
+        const float a0 = u[0] + u[4], a1 = u[0] - u[4], a2 = u[2] + u[6], a3 = u[2] - u[6];
+        const float b0 = u[1] + u[5], b1 = u[1] - u[5], b2 = u[3] + u[7], b3 = u[3] - u[7];
+        const float A0 = a0 + a2, A2 = a0 - a2, B0 = b0 + b2, B2 = b0 - b2;
+        const float2 A1 = make_float2(a1, -a3), B1 = make_float2(b1, -b3);
+        const float2 wb = make_float2(FFB_R2 * (B1.x + B1.y), FFB_R2 * (B1.y - B1.x));   // W8 B1
+        E[0] = make_float2(A0 + B0, 0.f);
+        E[4] = make_float2(A0 - B0, 0.f);
+        E[1] = cadd(A1, wb);
+        E[5] = csub(A1, wb);
+        E[2] = make_float2(A2, -B2);
+        E[6] = make_float2(A2, B2);
+        E[3] = cconj(E[5]);
+        E[7] = cconj(E[1]);
+    }
+}
+
+// cos / sin (2 pi e / 16), e = 0..15
+__device__ __forceinline__ float cos16(int e) {
+    constexpr float c[16] = {1.f, FFB_C1, FFB_R2, FFB_S1, 0.f, -FFB_S1, -FFB_R2, -FFB_C1,
+                             -1.f, -FFB_C1, -FFB_R2, -FFB_S1, 0.f, FFB_S1, FFB_R2, FFB_C1};
+    return c[e & 15];
+}
+__device__ __forceinline__ float sin16(int e) { return cos16(e + 12); }
+// cos / sin (2 pi e / 32), e = 0..31
+__device__ __forceinline__ float cos32(int e) {
+    constexpr float c1 = 0.98078528040323044913f, c3 = 0.83146961230254523708f;
+    constexpr float c5 = 0.55557023301960222474f, c7 = 0.19509032201612826785f;
+    constexpr float c[32] = {1.f, c1, FFB_C1, c3, FFB_R2, c5, FFB_S1, c7, 0.f, -c7, -FFB_S1, -c5, -FFB_R2, -c3,
+                             -FFB_C1, -c1, -1.f, -c1, -FFB_C1, -c3, -FFB_R2, -c5, -FFB_S1, -c7, 0.f, c7,
+                             FFB_S1, c5, FFB_R2, c3, FFB_C1, c1};
+    return c[e & 31];
+}
+__device__ __forceinline__ float sin32(int e) { return cos32(e + 24); }
 
 // ---------------------------------------------------------------------------
 // Length-N forward DFT of a sequence whose only nonzeros are the L = N/2
@@ -420,22 +473,27 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 // One warp per ring, four-step in registers: with n_theta = 32 M, sample
 // l = 32 m + j (lane j) and k = k1 + M k2,
 //   X_k = sum_j W^{j k1} [sum_m s_{32m+j} W_M^{m k1}] W_32^{j k2},  W = e^{-2 pi i / n_theta}.
-// Pass A: each lane loads its M/2 samples (m < M/2) from the polar buffer,
-// completes m >= M/2 with s_{l + n_theta/2} = conj s_l in registers and takes
-// the length-M DFT over m, then the twiddle W^{j k1}.  A transpose through
+// Pass A: each lane loads its M/2 samples x_m (m < M/2) from the polar
+// buffer; with s_{l + n_theta/2} = conj s_l the length-M DFT over m splits
+// into X[2j] = 2 DFT_{M/2}(Re x_m)[j] (a real-input DFT) and X[2j+1] =
+// 2 DFT_{M/2}(i Im(x_m) W_M^m)[j] (the factor 2 goes into the weight); then
+// the twiddle W^{j k1}.  A transpose through
 // shared memory (row k1, column rotated by k1 R, R = 32/M, so that writes and
 // reads touch 16 distinct bank slots per half warp) gives lane (g = k1, r) the
 // values j = r + R i.  Pass B: the length-32 DFT over j for every k1 as a
 // length-M DFT over i in registers, the twiddle W_32^{r k2'} and a length-R
 // DFT across the R lanes of the group (radix-2 decimation in frequency by XOR
-// shuffles; lane r ends with t = bitreverse(r)), k2 = k2' + M t.  The results
-// with k <= k_max go to a ring-major shared stage and leave as rows of
-// RFFT_RB consecutive rings per (k, re/im) in the quadrature's operand format.
+// shuffles; lane r ends with t = bitreverse(r)), k2 = k2' + M t.  For
+// n_theta = 512 (R = 2) the twiddles are constants and, as k_max < n_theta/2,
+// only the t = 0 half of the last step is formed (the pair's sum).  The
+// results with k <= k_max go to a ring-major shared stage and leave as rows
+// of RFFT_RB consecutive rings per (k, re/im) in the quadrature's operand
+// format, two rings per store.
 // grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
 // ---------------------------------------------------------------------------
 template <int NTH, int FMT>
 __global__ void __launch_bounds__(32 * RFFT_RB, 1)
-k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
+k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const float2 *__restrict__ twT,
            void *__restrict__ out0, void *__restrict__ out1, int ld) {
     constexpr int M = NTH / 32;      // samples per lane
     constexpr int R = 32 / M;        // lanes per length-32 DFT of pass B
@@ -449,16 +507,30 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
     const int img = blockIdx.y;
     const int j0 = blockIdx.x * RFFT_RB;
     const int ring = j0 + warp;
-    const float scale = 6.283185307179586f / (float)NTH;
+    // pass A below yields half of each DFT value: the weight 2 pi / n_theta
+    // carries the factor 2
+    const float scale = 2.f * 6.283185307179586f / (float)NTH;
     if (ring < n_xi) {
         const float2 *src = Fpol + ((size_t)img * n_xi + ring) * NH;
-        float2 x[M];
+        // pass A over m with s_{l + n_theta/2} = conj s_l: for the M/2 loaded
+        // samples x_m, X[2j] / 2 is the length-M/2 DFT of Re x_m and
+        // X[2j+1] / 2 that of i Im(x_m) W_M^m
+        float u[M / 2];
+        float2 v[M / 2], E[M / 2];
 #pragma unroll
         for (int m = 0; m < M / 2; ++m) {
-            x[m] = src[32 * m + lane];
-            x[m + M / 2] = cconj(x[m]);
+            const float2 xm = src[32 * m + lane];
+            u[m] = xm.x;
+            v[m] = make_float2(xm.y * sin16((16 / M) * m), xm.y * cos16((16 / M) * m));
         }
-        dft_reg<M>(x);                         // pass A: over m
+        dft_real<M / 2>(u, E);
+        dft_reg<M / 2>(v);
+        float2 x[M];
+#pragma unroll
+        for (int j = 0; j < M / 2; ++j) {
+            x[2 * j] = E[j];
+            x[2 * j + 1] = v[j];
+        }
 #pragma unroll
         for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twT[(lane * k1) & (NTH - 1)]));
 #pragma unroll
@@ -469,57 +541,102 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int chunk, const
 #pragma unroll
         for (int i = 0; i < M; ++i) y[i] = tb[g * 32 + ((r + R * i + g * R) & 31)];
         dft_reg<M>(y);                         // pass B, part 1: over i
+        float *row = ost + warp * ostld;
+        if constexpr (R == 2) {
+            // twiddle W_32^{r k2} (constants), then only the half k < n_theta/2
+            // of the last radix-2 step (k_max < n_theta/2): the pair's sum, of
+            // which lane r keeps the outputs k2 in [r M/2, (r + 1) M/2)
 #pragma unroll
-        for (int k2 = 1; k2 < M; ++k2) y[k2] = cmul(y[k2], __ldg(&twT[(r * k2 * (NTH / 32)) & (NTH - 1)]));
-#pragma unroll
-        for (int h = R / 2; h >= 1; h >>= 1) {           // pass B, part 2: across the R lanes
-            const bool up = (r & h) != 0;
-            // the last stage (h = 1) has the twiddle W^0 = 1
-            const float2 w = (h > 1) ? __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]) : make_float2(1.f, 0.f);
+            for (int k2 = 1; k2 < M; ++k2) {
+                const float2 w = make_float2(cos32(k2), -sin32(k2));
+                const float2 t = cmul(y[k2], w);
+                y[k2] = r ? t : y[k2];
+            }
 #pragma unroll
             for (int k2 = 0; k2 < M; ++k2) {
-                const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
-                                              __shfl_xor_sync(0xffffffffu, y[k2].y, h));
-                const float2 d = csub(pv, y[k2]);
-                y[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(y[k2], pv);
+                y[k2].x += __shfl_xor_sync(0xffffffffu, y[k2].x, 1);
+                y[k2].y += __shfl_xor_sync(0xffffffffu, y[k2].y, 1);
             }
-        }
-        int t = 0;
-        for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
-        float *row = ost + warp * ostld;
 #pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) {
-            const int k = g + M * (k2 + M * t);
-            if (k <= kmax) {
-                row[2 * k] = scale * y[k2].x;
-                row[2 * k + 1] = scale * y[k2].y;
+            for (int h2 = 0; h2 < M / 2; ++h2) {
+                const float2 val = r ? y[M / 2 + h2] : y[h2];
+                const int k = g + M * (r * (M / 2) + h2);
+                if (k <= kmax) {
+                    row[2 * k] = scale * val.x;
+                    row[2 * k + 1] = scale * val.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k2 = 1; k2 < M; ++k2) y[k2] = cmul(y[k2], __ldg(&twT[(r * k2 * (NTH / 32)) & (NTH - 1)]));
+#pragma unroll
+            for (int h = R / 2; h >= 1; h >>= 1) {           // pass B, part 2: across the R lanes
+                const bool up = (r & h) != 0;
+                // the last stage (h = 1) has the twiddle W^0 = 1
+                const float2 w = (h > 1) ? __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]) : make_float2(1.f, 0.f);
+#pragma unroll
+                for (int k2 = 0; k2 < M; ++k2) {
+                    const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
+                                                  __shfl_xor_sync(0xffffffffu, y[k2].y, h));
+                    const float2 d = csub(pv, y[k2]);
+                    y[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(y[k2], pv);
+                }
+            }
+            int t = 0;
+            for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int k = g + M * (k2 + M * t);
+                if (k <= kmax) {
+                    row[2 * k] = scale * y[k2].x;
+                    row[2 * k + 1] = scale * y[k2].y;
+                }
             }
         }
     }
     __syncthreads();
-    // write-out: thread t owns ring jj = t % RFFT_RB and (k, re/im) rows
-    // kc = t / RFFT_RB + (32 RFFT_RB / RFFT_RB) it; consecutive rows of one
-    // thread are 16 k apart, i.e. a fixed stride in the plane
+    // write-out: thread t owns the ring pair jj = 2 (t % (RFFT_RB / 2)), jj + 1
+    // and the (k, re/im) rows kc = t / (RFFT_RB / 2) + KCSTEP it; KCSTEP is
+    // even, so re/im of a row is fixed per thread; the pair leaves as one
+    // 2-element store per plane
     const int nr = min(RFFT_RB, n_xi - j0);
-    const int jj = threadIdx.x % RFFT_RB;
-    constexpr int KCSTEP = (32 * RFFT_RB) / RFFT_RB;     // 32: even, so re/im of a row is fixed per thread
-    const int kc0 = threadIdx.x / RFFT_RB;
+    constexpr int NPR = RFFT_RB / 2;
+    constexpr int KCSTEP = (32 * RFFT_RB) / NPR;
+    static_assert(KCSTEP % 2 == 0, "re/im fixed per thread");
+    const int jj = 2 * (threadIdx.x % NPR);
+    const int kc0 = threadIdx.x / NPR;
     const int kcend = 2 * (kmax + 1);
     if (jj < nr) {
-        size_t idx = (((size_t)(kc0 >> 1) * chunk + img) * 2 + (kc0 & 1)) * ld + j0 + jj;
-        const size_t step = (size_t)(KCSTEP / 2) * chunk * 2 * ld;
+        const bool two = jj + 1 < nr;
+        size_t idx = (((size_t)(kc0 >> 1) * lead + img) * 2 + (kc0 & 1)) * ld + j0 + jj;
+        const size_t step = (size_t)(KCSTEP / 2) * lead * 2 * ld;
         for (int kc = kc0; kc < kcend; kc += KCSTEP, idx += step) {
-            const float x = ost[jj * ostld + kc];
+            const float x0 = ost[jj * ostld + kc];
+            const float x1 = two ? ost[(jj + 1) * ostld + kc] : 0.f;
             if (FMT == FFB_FMT_F32) {
-                ((float *)out0)[idx] = x;
+                if (two) *(float2 *)((float *)out0 + idx) = make_float2(x0, x1);
+                else ((float *)out0)[idx] = x0;
             } else if (FMT == FFB_FMT_TF32 || FMT == FFB_FMT_TF32X2) {
-                const float h = tf32_round(x);
-                ((float *)out0)[idx] = h;
-                if (FMT == FFB_FMT_TF32X2) ((float *)out1)[idx] = x - h;
+                const float h0 = tf32_round(x0), h1 = tf32_round(x1);
+                if (two) {
+                    *(float2 *)((float *)out0 + idx) = make_float2(h0, h1);
+                    if (FMT == FFB_FMT_TF32X2) *(float2 *)((float *)out1 + idx) = make_float2(x0 - h0, x1 - h1);
+                } else {
+                    ((float *)out0)[idx] = h0;
+                    if (FMT == FFB_FMT_TF32X2) ((float *)out1)[idx] = x0 - h0;
+                }
             } else {
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                ((__nv_bfloat16 *)out0)[idx] = h;
-                if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                if (two) {
+                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out0 + idx) = __halves2bfloat162(h0, h1);
+                    if (FMT == FFB_FMT_BF16X2)
+                        *(__nv_bfloat162 *)((__nv_bfloat16 *)out1 + idx) = __halves2bfloat162(l0, l1);
+                } else {
+                    ((__nv_bfloat16 *)out0)[idx] = h0;
+                    if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = l0;
+                }
             }
         }
     }
