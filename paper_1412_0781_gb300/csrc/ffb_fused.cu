@@ -494,6 +494,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 template <int NTH, int FMT>
 __global__ void __launch_bounds__(32 * RFFT_RB, 1)
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const float2 *__restrict__ twT,
+           const float2 *__restrict__ twA,
            void *__restrict__ out0, void *__restrict__ out1, int ld) {
     constexpr int M = NTH / 32;      // samples per lane
     constexpr int R = 32 / M;        // lanes per length-32 DFT of pass B
@@ -531,8 +532,9 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
             x[2 * j] = E[j];
             x[2 * j + 1] = v[j];
         }
+        // twiddles W^{j k1} from the plan's table [k1][j] (coalesced)
 #pragma unroll
-        for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twT[(lane * k1) & (NTH - 1)]));
+        for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twA[k1 * 32 + lane]));
 #pragma unroll
         for (int k1 = 0; k1 < M; ++k1) tb[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
         __syncwarp();
@@ -557,13 +559,15 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
                 y[k2].x += __shfl_xor_sync(0xffffffffu, y[k2].x, 1);
                 y[k2].y += __shfl_xor_sync(0xffffffffu, y[k2].y, 1);
             }
+            // the two lanes of a pair write the same bank slot for their k:
+            // one takes the real part first, the other the imaginary part
 #pragma unroll
             for (int h2 = 0; h2 < M / 2; ++h2) {
                 const float2 val = r ? y[M / 2 + h2] : y[h2];
                 const int k = g + M * (r * (M / 2) + h2);
                 if (k <= kmax) {
-                    row[2 * k] = scale * val.x;
-                    row[2 * k + 1] = scale * val.y;
+                    row[2 * k + r] = scale * (r ? val.y : val.x);
+                    row[2 * k + 1 - r] = scale * (r ? val.x : val.y);
                 }
             }
         } else {
@@ -626,16 +630,15 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
                     if (FMT == FFB_FMT_TF32X2) ((float *)out1)[idx] = x0 - h0;
                 }
             } else {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
                 if (two) {
-                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out0 + idx) = __halves2bfloat162(h0, h1);
-                    if (FMT == FFB_FMT_BF16X2)
-                        *(__nv_bfloat162 *)((__nv_bfloat16 *)out1 + idx) = __halves2bfloat162(l0, l1);
+                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out0 + idx) = h;
+                    if (FMT == FFB_FMT_BF16X2) *(__nv_bfloat162 *)((__nv_bfloat16 *)out1 + idx) = l;
                 } else {
-                    ((__nv_bfloat16 *)out0)[idx] = h0;
-                    if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = l0;
+                    ((__nv_bfloat16 *)out0)[idx] = __low2bfloat16(h);
+                    if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = __low2bfloat16(l);
                 }
             }
         }
@@ -890,6 +893,21 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             t0 = t1;
         }
     }
+    // ring FFT twiddles W^{j k1}, W = e^{-2 pi i / n_theta}, as [k1][j]
+    // (k1 < n_theta / 32, j < 32), from float64
+    const int MA = p->n_theta / 32;
+    std::vector<float2> twa((size_t)MA * 32);
+    for (int k1 = 0; k1 < MA; ++k1)
+        for (int j = 0; j < 32; ++j) {
+            const double a = -2.0 * M_PI * (double)((j * k1) % p->n_theta) / (double)p->n_theta;
+            twa[(size_t)k1 * 32 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    if (p->d_twA) cudaFree(p->d_twA);
+    p->d_twA = nullptr;
+    e = ffb_check_cuda(cudaMalloc((void **)&p->d_twA, sizeof(float2) * twa.size()));
+    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_twA, twa.data(), sizeof(float2) * twa.size(),
+                                               cudaMemcpyHostToDevice, s));
+    if (e) return e;
     if (p->d_nodes) cudaFree(p->d_nodes);
     if (p->d_node_blk) cudaFree(p->d_node_blk);
     p->d_nodes = nullptr;
@@ -924,7 +942,8 @@ static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOu
     }
     dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
     ProfScope ps(p, FFB_KC_RING_FFT, s);
-    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, o.lead, p->d_twT, o.p0, o.p1, o.ld);
+    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, o.lead, p->d_twT, p->d_twA, o.p0,
+                                                        o.p1, o.ld);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
