@@ -123,14 +123,16 @@ def algorithmic_flops(plan):
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (profiles/k_grid_interp_half_L128.md: 152-image launch), valid only
-# while the kernel's source file is byte-identical to the profiled one.
+# while the kernel's sources are byte-identical to the profiled ones (the
+# kernel's file and the register-FFT header; from ffb_internal.cuh it uses
+# only the complex arithmetic and the status flag).  ncu empties L2 before the
+# capture, so the figure includes one read of the plan's 2.6 MB node table,
+# which stays in L2 between launches in a live run.
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one captured launch of the
-    # dominant kernel, valid while the source it was captured from is unchanged
-    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_fused.cu",
-                                "paper_1412_0781_gb300/csrc/ffb_internal.cuh"],
-                    "sha256": "bb52721b2ecbf8d999a4f3ace6927e05886bfe9b0a9348af0dac14ff2b24fbec",
-                    "bytes_per_launch": 10086912 + 337152, "images_per_launch": 152},
+    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu",
+                                "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
+                    "sha256": "adcb0df265a168cfe0a329b56ce0647fe8443f8bb76165fd9e22cd926113e538",
+                    "bytes_per_launch": 12653056 + 97536, "images_per_launch": 152},
 }
 
 

@@ -1,4 +1,5 @@
-// ffb_fused.cu -- steps a1-a4 with the oversampled grid held in shared memory.
+// ffb_grid.cu -- steps a1-a3 with the oversampled grid held in shared memory
+// (the type-2 NUFFT of Eq. nufft onto the polar nodes of Sec. III).
 //
 // One CTA per (image, half).  Half 0 owns the polar nodes with xi1 >= 0
 // (theta in [0, pi/2]), half 1 those with xi1 < 0 (theta in (pi/2, pi)); all
@@ -14,14 +15,17 @@
 //          placed at i1 mod N); the half's m1 range overwrites the row in
 //          place (the row is read completely before it is written).
 // Phase 3  interpolation of the half's nodes from S (w x w taps of the ES
-//          kernel, node coordinates in double-float as in ffb_nufft.cu), the
-//          result written to the polar buffer F[img][j][l], l < n_theta/2.
+//          kernel with weights from the plan), the result written to the
+//          polar buffer F[img][j][l], l < n_theta/2.
+// The ring FFT (ffb_ring.cu) then completes every half ring with
+// F(theta + pi) = conj F(theta) and takes the length-n_theta FFT of Eq. 1DFFT.
 //
-// A second kernel completes every half ring with F(theta + pi) = conj F(theta)
-// and takes the length-n_theta FFT of Eq. 1DFFT.
-//
-// Both halves compute the same row transforms (phase 1); the columns and the
-// nodes are split.
+// Phases 1 and 2 are the same for both halves.  Where clusters of two CTAs
+// fill the GPU, the two CTAs of an image form one and split them: each
+// transforms half of the pixel-row pairs and half of the S rows, and sends
+// the peer what it needs through distributed shared memory (contiguous row
+// segments after phase 1, the peer's column range of every row it
+// transformed in phase 2).
 //
 // Node order in phase 3.  A node gathers the W x W window of S at
 // S[r0][c0] (W = 8).  Two nodes with the same r0 and window origins c0, c0 + d
@@ -37,19 +41,16 @@
 // nodes' 8 row weights and 9 column weights over the union (144 bytes, about
 // 2.6 MB at N = 256, read from L2 by every CTA).  The kernel stages a block's
 // results in shared memory and stores them in natural order.
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
 
-#include "ffb_internal.cuh"
+#include "ffb_fft.cuh"
 
 #define FUS_WARPS 32                 // warps per CTA, each with an N-entry FFT buffer
 #define FUS_NT (32 * FUS_WARPS)      // threads per CTA
-#define RFFT_RB 32   // rings per ring-FFT CTA (one warp each)
 #define FUS_GU 2048   // units per phase-3 block (at most; two per thread)
 #define FUS_REC 9     // float4 fields of a unit record
 
@@ -58,123 +59,6 @@
 // 9-column union start at the last window origin; the pitch stays odd
 __host__ __device__ constexpr int fus_mh(int N, int W) { return N / 2 + 1 + 2 * ((W + 1) / 2); }
 __host__ __device__ constexpr int fus_sld(int N, int W) { return fus_mh(N, W) + 2; }
-
-// ---------------------------------------------------------------------------
-// Register FFTs.  dft_reg<M>: a length-M DFT held in one thread's registers
-// (M = 4, 8, 16; radix 4 with constant twiddles).
-// ---------------------------------------------------------------------------
-template <int M>
-__host__ __device__ constexpr int bitrev_c(int i) {
-    int r = 0;
-    for (int b = 1; b < M; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
-    return r;
-}
-
-// W_16^e = exp(-2 pi i e / 16) for the e a radix-4 x 4 DFT needs
-#define FFB_C1 0.92387953251128676f    // cos(pi/8)
-#define FFB_S1 0.38268343236508977f    // sin(pi/8)
-#define FFB_R2 0.70710678118654752f    // sqrt(1/2)
-__device__ __forceinline__ float2 w16(int e) {
-    switch (e & 15) {
-        case 1: return make_float2(FFB_C1, -FFB_S1);
-        case 2: return make_float2(FFB_R2, -FFB_R2);
-        case 3: return make_float2(FFB_S1, -FFB_C1);
-        case 4: return make_float2(0.f, -1.f);
-        case 6: return make_float2(-FFB_R2, -FFB_R2);
-        case 9: return make_float2(-FFB_C1, FFB_S1);
-        default: return make_float2(1.f, 0.f);
-    }
-}
-
-// in-register length-M DFT, natural order in and out (forward)
-template <int M>
-__device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
-    if constexpr (M == 2) {
-        const float2 a = x[0];
-        x[0] = cadd(a, x[1]);
-        x[1] = csub(a, x[1]);
-    } else if constexpr (M == 4) {
-        dft4<false>(x);
-    } else if constexpr (M == 8) {
-        float2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
-        dft4<false>(e);
-        dft4<false>(o);
-        const float2 w[4] = {make_float2(1.f, 0.f), make_float2(FFB_R2, -FFB_R2), make_float2(0.f, -1.f),
-                             make_float2(-FFB_R2, -FFB_R2)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 t = (k == 0) ? o[0] : cmul(o[k], w[k]);
-            x[k] = cadd(e[k], t);
-            x[k + 4] = csub(e[k], t);
-        }
-    } else {
-        static_assert(M == 16, "M in {2, 4, 8, 16}");
-        float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) {
-            float2 v[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
-            dft4<false>(v);
-#pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 * k1 == 0) ? v[k1] : cmul(v[k1], w16(n2 * k1));
-        }
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            float2 v[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-            dft4<false>(v);
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
-        }
-    }
-}
-
-// length-H DFT of a real sequence u (H = 2, 4, 8), E[H - j] = conj E[j]
-template <int H>
-__device__ __forceinline__ void dft_real(const float (&u)[H], float2 (&E)[H]) {
-    if constexpr (H == 2) {
-        E[0] = make_float2(u[0] + u[1], 0.f);
-        E[1] = make_float2(u[0] - u[1], 0.f);
-    } else if constexpr (H == 4) {
-        const float t0 = u[0] + u[2], t1 = u[0] - u[2], t2 = u[1] + u[3], t3 = u[1] - u[3];
-        E[0] = make_float2(t0 + t2, 0.f);
-        E[1] = make_float2(t1, -t3);
-        E[2] = make_float2(t0 - t2, 0.f);
-        E[3] = make_float2(t1, t3);
-    } else {
-        static_assert(H == 8, "H in {2, 4, 8}");
-        // even / odd samples: real length-4 DFTs A, B; E[j] = A[j] + W8^j B[j]
-        const float a0 = u[0] + u[4], a1 = u[0] - u[4], a2 = u[2] + u[6], a3 = u[2] - u[6];
-        const float b0 = u[1] + u[5], b1 = u[1] - u[5], b2 = u[3] + u[7], b3 = u[3] - u[7];
-        const float A0 = a0 + a2, A2 = a0 - a2, B0 = b0 + b2, B2 = b0 - b2;
-        const float2 A1 = make_float2(a1, -a3), B1 = make_float2(b1, -b3);
-        const float2 wb = make_float2(FFB_R2 * (B1.x + B1.y), FFB_R2 * (B1.y - B1.x));   // W8 B1
-        E[0] = make_float2(A0 + B0, 0.f);
-        E[4] = make_float2(A0 - B0, 0.f);
-        E[1] = cadd(A1, wb);
-        E[5] = csub(A1, wb);
-        E[2] = make_float2(A2, -B2);
-        E[6] = make_float2(A2, B2);
-        E[3] = cconj(E[5]);
-        E[7] = cconj(E[1]);
-    }
-}
-
-// cos / sin (2 pi e / 16), e = 0..15
-__device__ __forceinline__ float cos16(int e) {
-    constexpr float c[16] = {1.f, FFB_C1, FFB_R2, FFB_S1, 0.f, -FFB_S1, -FFB_R2, -FFB_C1,
-                             -1.f, -FFB_C1, -FFB_R2, -FFB_S1, 0.f, FFB_S1, FFB_R2, FFB_C1};
-    return c[e & 15];
-}
-__device__ __forceinline__ float sin16(int e) { return cos16(e + 12); }
-// cos / sin (2 pi e / 32), e = 0..31
-__device__ __forceinline__ float cos32(int e) {
-    constexpr float c1 = 0.98078528040323044913f, c3 = 0.83146961230254523708f;
-    constexpr float c5 = 0.55557023301960222474f, c7 = 0.19509032201612826785f;
-    constexpr float c[32] = {1.f, c1, FFB_C1, c3, FFB_R2, c5, FFB_S1, c7, 0.f, -c7, -FFB_S1, -c5, -FFB_R2, -c3,
-                             -FFB_C1, -c1, -1.f, -c1, -FFB_C1, -c3, -FFB_R2, -c5, -FFB_S1, -c7, 0.f, c7,
-                             FFB_S1, c5, FFB_R2, c3, FFB_C1, c1};
-    return c[e & 31];
-}
-__device__ __forceinline__ float sin32(int e) { return cos32(e + 24); }
 
 // ---------------------------------------------------------------------------
 // Length-N forward DFT of a sequence whose only nonzeros are the L = N/2
@@ -467,185 +351,6 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 }
 
 // ---------------------------------------------------------------------------
-// ring FFT: F[img][j][l] (l < n_theta/2) -> Fhat[k][img][c][j], k <= k_max,
-// with the conjugate completion of the ring and the 2 pi / n_theta weight.
-//
-// One warp per ring, four-step in registers: with n_theta = 32 M, sample
-// l = 32 m + j (lane j) and k = k1 + M k2,
-//   X_k = sum_j W^{j k1} [sum_m s_{32m+j} W_M^{m k1}] W_32^{j k2},  W = e^{-2 pi i / n_theta}.
-// Pass A: each lane loads its M/2 samples x_m (m < M/2) from the polar
-// buffer; with s_{l + n_theta/2} = conj s_l the length-M DFT over m splits
-// into X[2j] = 2 DFT_{M/2}(Re x_m)[j] (a real-input DFT) and X[2j+1] =
-// 2 DFT_{M/2}(i Im(x_m) W_M^m)[j] (the factor 2 goes into the weight); then
-// the twiddle W^{j k1}.  A transpose through
-// shared memory (row k1, column rotated by k1 R, R = 32/M, so that writes and
-// reads touch 16 distinct bank slots per half warp) gives lane (g = k1, r) the
-// values j = r + R i.  Pass B: the length-32 DFT over j for every k1 as a
-// length-M DFT over i in registers, the twiddle W_32^{r k2'} and a length-R
-// DFT across the R lanes of the group (radix-2 decimation in frequency by XOR
-// shuffles; lane r ends with t = bitreverse(r)), k2 = k2' + M t.  For
-// n_theta = 512 (R = 2) the twiddles are constants and, as k_max < n_theta/2,
-// only the t = 0 half of the last step is formed (the pair's sum).  The
-// results with k <= k_max go to a ring-major shared stage and leave as rows
-// of RFFT_RB consecutive rings per (k, re/im) in the quadrature's operand
-// format, two rings per store.
-// grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
-// ---------------------------------------------------------------------------
-template <int NTH, int FMT>
-__global__ void __launch_bounds__(32 * RFFT_RB, 1)
-k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const float2 *__restrict__ twT,
-           const float2 *__restrict__ twA,
-           void *__restrict__ out0, void *__restrict__ out1, int ld) {
-    constexpr int M = NTH / 32;      // samples per lane
-    constexpr int R = 32 / M;        // lanes per length-32 DFT of pass B
-    constexpr int NH = NTH / 2;
-    static_assert(M >= 2 && M <= 16 && M * R == 32, "n_theta in {64, 128, 256, 512}");
-    extern __shared__ float2 smr[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *tb = smr + warp * (M * 32);                  // this warp's transpose buffer [M][32]
-    float *ost = (float *)(smr + RFFT_RB * M * 32);      // [RFFT_RB][ostld]: ring-major stage
-    const int ostld = (2 * (kmax + 1)) | 1;              // odd: the write-out reads conflict-free
-    const int img = blockIdx.y;
-    const int j0 = blockIdx.x * RFFT_RB;
-    const int ring = j0 + warp;
-    // pass A below yields half of each DFT value: the weight 2 pi / n_theta
-    // carries the factor 2
-    const float scale = 2.f * 6.283185307179586f / (float)NTH;
-    if (ring < n_xi) {
-        const float2 *src = Fpol + ((size_t)img * n_xi + ring) * NH;
-        // pass A over m with s_{l + n_theta/2} = conj s_l: for the M/2 loaded
-        // samples x_m, X[2j] / 2 is the length-M/2 DFT of Re x_m and
-        // X[2j+1] / 2 that of i Im(x_m) W_M^m
-        float u[M / 2];
-        float2 v[M / 2], E[M / 2];
-#pragma unroll
-        for (int m = 0; m < M / 2; ++m) {
-            const float2 xm = src[32 * m + lane];
-            u[m] = xm.x;
-            v[m] = make_float2(xm.y * sin16((16 / M) * m), xm.y * cos16((16 / M) * m));
-        }
-        dft_real<M / 2>(u, E);
-        dft_reg<M / 2>(v);
-        float2 x[M];
-#pragma unroll
-        for (int j = 0; j < M / 2; ++j) {
-            x[2 * j] = E[j];
-            x[2 * j + 1] = v[j];
-        }
-        // twiddles W^{j k1} from the plan's table [k1][j] (coalesced)
-#pragma unroll
-        for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twA[k1 * 32 + lane]));
-#pragma unroll
-        for (int k1 = 0; k1 < M; ++k1) tb[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
-        __syncwarp();
-        const int g = lane / R, r = lane % R;
-        float2 y[M];
-#pragma unroll
-        for (int i = 0; i < M; ++i) y[i] = tb[g * 32 + ((r + R * i + g * R) & 31)];
-        dft_reg<M>(y);                         // pass B, part 1: over i
-        float *row = ost + warp * ostld;
-        if constexpr (R == 2) {
-            // twiddle W_32^{r k2} (constants), then only the half k < n_theta/2
-            // of the last radix-2 step (k_max < n_theta/2): the pair's sum, of
-            // which lane r keeps the outputs k2 in [r M/2, (r + 1) M/2)
-#pragma unroll
-            for (int k2 = 1; k2 < M; ++k2) {
-                const float2 w = make_float2(cos32(k2), -sin32(k2));
-                const float2 t = cmul(y[k2], w);
-                y[k2] = r ? t : y[k2];
-            }
-#pragma unroll
-            for (int k2 = 0; k2 < M; ++k2) {
-                y[k2].x += __shfl_xor_sync(0xffffffffu, y[k2].x, 1);
-                y[k2].y += __shfl_xor_sync(0xffffffffu, y[k2].y, 1);
-            }
-            // the two lanes of a pair write the same bank slot for their k:
-            // one takes the real part first, the other the imaginary part
-#pragma unroll
-            for (int h2 = 0; h2 < M / 2; ++h2) {
-                const float2 val = r ? y[M / 2 + h2] : y[h2];
-                const int k = g + M * (r * (M / 2) + h2);
-                if (k <= kmax) {
-                    row[2 * k + r] = scale * (r ? val.y : val.x);
-                    row[2 * k + 1 - r] = scale * (r ? val.x : val.y);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k2 = 1; k2 < M; ++k2) y[k2] = cmul(y[k2], __ldg(&twT[(r * k2 * (NTH / 32)) & (NTH - 1)]));
-#pragma unroll
-            for (int h = R / 2; h >= 1; h >>= 1) {           // pass B, part 2: across the R lanes
-                const bool up = (r & h) != 0;
-                // the last stage (h = 1) has the twiddle W^0 = 1
-                const float2 w = (h > 1) ? __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]) : make_float2(1.f, 0.f);
-#pragma unroll
-                for (int k2 = 0; k2 < M; ++k2) {
-                    const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
-                                                  __shfl_xor_sync(0xffffffffu, y[k2].y, h));
-                    const float2 d = csub(pv, y[k2]);
-                    y[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(y[k2], pv);
-                }
-            }
-            int t = 0;
-            for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
-#pragma unroll
-            for (int k2 = 0; k2 < M; ++k2) {
-                const int k = g + M * (k2 + M * t);
-                if (k <= kmax) {
-                    row[2 * k] = scale * y[k2].x;
-                    row[2 * k + 1] = scale * y[k2].y;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // write-out: thread t owns the ring pair jj = 2 (t % (RFFT_RB / 2)), jj + 1
-    // and the (k, re/im) rows kc = t / (RFFT_RB / 2) + KCSTEP it; KCSTEP is
-    // even, so re/im of a row is fixed per thread; the pair leaves as one
-    // 2-element store per plane
-    const int nr = min(RFFT_RB, n_xi - j0);
-    constexpr int NPR = RFFT_RB / 2;
-    constexpr int KCSTEP = (32 * RFFT_RB) / NPR;
-    static_assert(KCSTEP % 2 == 0, "re/im fixed per thread");
-    const int jj = 2 * (threadIdx.x % NPR);
-    const int kc0 = threadIdx.x / NPR;
-    const int kcend = 2 * (kmax + 1);
-    if (jj < nr) {
-        const bool two = jj + 1 < nr;
-        size_t idx = (((size_t)(kc0 >> 1) * lead + img) * 2 + (kc0 & 1)) * ld + j0 + jj;
-        const size_t step = (size_t)(KCSTEP / 2) * lead * 2 * ld;
-        for (int kc = kc0; kc < kcend; kc += KCSTEP, idx += step) {
-            const float x0 = ost[jj * ostld + kc];
-            const float x1 = two ? ost[(jj + 1) * ostld + kc] : 0.f;
-            if (FMT == FFB_FMT_F32) {
-                if (two) *(float2 *)((float *)out0 + idx) = make_float2(x0, x1);
-                else ((float *)out0)[idx] = x0;
-            } else if (FMT == FFB_FMT_TF32 || FMT == FFB_FMT_TF32X2) {
-                const float h0 = tf32_round(x0), h1 = tf32_round(x1);
-                if (two) {
-                    *(float2 *)((float *)out0 + idx) = make_float2(h0, h1);
-                    if (FMT == FFB_FMT_TF32X2) *(float2 *)((float *)out1 + idx) = make_float2(x0 - h0, x1 - h1);
-                } else {
-                    ((float *)out0)[idx] = h0;
-                    if (FMT == FFB_FMT_TF32X2) ((float *)out1)[idx] = x0 - h0;
-                }
-            } else {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-                const float2 hf = __bfloat1622float2(h);
-                const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-                if (two) {
-                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out0 + idx) = h;
-                    if (FMT == FFB_FMT_BF16X2) *(__nv_bfloat162 *)((__nv_bfloat16 *)out1 + idx) = l;
-                } else {
-                    ((__nv_bfloat16 *)out0)[idx] = __low2bfloat16(h);
-                    if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = __low2bfloat16(l);
-                }
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
 template <int N, int W>
@@ -893,21 +598,6 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             t0 = t1;
         }
     }
-    // ring FFT twiddles W^{j k1}, W = e^{-2 pi i / n_theta}, as [k1][j]
-    // (k1 < n_theta / 32, j < 32), from float64
-    const int MA = p->n_theta / 32;
-    std::vector<float2> twa((size_t)MA * 32);
-    for (int k1 = 0; k1 < MA; ++k1)
-        for (int j = 0; j < 32; ++j) {
-            const double a = -2.0 * M_PI * (double)((j * k1) % p->n_theta) / (double)p->n_theta;
-            twa[(size_t)k1 * 32 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-    if (p->d_twA) cudaFree(p->d_twA);
-    p->d_twA = nullptr;
-    e = ffb_check_cuda(cudaMalloc((void **)&p->d_twA, sizeof(float2) * twa.size()));
-    if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_twA, twa.data(), sizeof(float2) * twa.size(),
-                                               cudaMemcpyHostToDevice, s));
-    if (e) return e;
     if (p->d_nodes) cudaFree(p->d_nodes);
     if (p->d_node_blk) cudaFree(p->d_node_blk);
     p->d_nodes = nullptr;
@@ -928,43 +618,4 @@ int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int 
     if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s);
     if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s);
     return FFB_ERR_UNSUPPORTED;
-}
-
-template <int NTH, int FMT>
-static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
-    static int attr = 0;
-    const size_t smem = sizeof(float2) * RFFT_RB * (size_t)NTH + sizeof(float) * RFFT_RB * ((2 * (p->k_max + 1)) | 1);
-    if (smem > 48 * 1024 && attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_fft<NTH, FMT>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (e) return e;
-        attr = (int)smem;
-    }
-    dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
-    ProfScope ps(p, FFB_KC_RING_FFT, s);
-    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, o.lead, p->d_twT, p->d_twA, o.p0,
-                                                        o.p1, o.ld);
-    p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
-}
-
-template <int NTH>
-static int launch_ring(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
-    switch (o.fmt) {
-        case FFB_FMT_F32: return launch_ring_fmt<NTH, FFB_FMT_F32>(p, m, Fpol, o, s);
-        case FFB_FMT_TF32: return launch_ring_fmt<NTH, FFB_FMT_TF32>(p, m, Fpol, o, s);
-        case FFB_FMT_TF32X2: return launch_ring_fmt<NTH, FFB_FMT_TF32X2>(p, m, Fpol, o, s);
-        case FFB_FMT_BF16: return launch_ring_fmt<NTH, FFB_FMT_BF16>(p, m, Fpol, o, s);
-        case FFB_FMT_BF16X2: return launch_ring_fmt<NTH, FFB_FMT_BF16X2>(p, m, Fpol, o, s);
-        default: return FFB_ERR_ARG;
-    }
-}
-
-int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
-    switch (p->n_theta) {
-        case 128: return launch_ring<128>(p, m, Fpol, o, s);
-        case 256: return launch_ring<256>(p, m, Fpol, o, s);
-        case 512: return launch_ring<512>(p, m, Fpol, o, s);
-        default: return FFB_ERR_UNSUPPORTED;
-    }
 }

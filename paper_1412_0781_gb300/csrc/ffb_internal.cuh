@@ -306,6 +306,7 @@ int ffb_ensure_scratch_grid(ffb_plan_t plan);
 bool ffb_fused_supported(ffb_plan_t plan);
 int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_fused_mode(ffb_plan_t plan);   // 1 plain, 2 cluster variant of the fused kernel
+int ffb_ring_prepare(ffb_plan_t plan, cudaStream_t s);   // ring FFT twiddle table (fused path)
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
                            cudaStream_t s);
 struct RingOut {

@@ -416,6 +416,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
         p->fused = ffb_fused_mode(p);
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
         st = ffb_fused_prepare(p, s);
+        if (st == FFB_OK) st = ffb_ring_prepare(p, s);
     }
     if (st != FFB_OK) {
         cudaStreamSynchronize(s);
