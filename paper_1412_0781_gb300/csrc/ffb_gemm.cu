@@ -219,13 +219,13 @@ void ffb_cov_stack(ffb_plan_t p, const float *d_coef, int64_t n, bool tc, CovSta
     st->pk = p->d_p;
     st->off = p->d_off;
     st->cov_off = p->d_cov_off;
-    st->work = p->d_cov_work;
+    st->work = tc ? p->d_cov_sb : p->d_cov_work;
     st->shift = p->d_shift;
     st->acc = p->d_acc;
     st->sum0 = p->d_sum0;
     st->P = p->P;
-    st->nk = tc ? p->k_max + 1 : p->n_cov_work;
-    st->per = tc ? 1024 : 2048;
+    st->nk = tc ? p->n_cov_sb : p->n_cov_work;
+    st->per = tc ? 512 : 2048;
     st->pmax = p->pmax;
 }
 

@@ -167,8 +167,7 @@ static int tune(ffb_group_t g, const Key &k, cudaStream_t s) {
     std::vector<Cand> cands;
     const int grid0 = ffb_cov_grid_default(g->precision);
     if (tc) {
-        for (int per : {512, 1024, 2048})
-            for (int tile : {64, 32, 16}) cands.push_back({per, tile, grid0, 0.f});
+        for (int per : {128, 256, 512}) cands.push_back({per, 32, grid0, 0.f});
     } else {
         for (int per : {512, 1024, 2048, 4096})
             for (int gm : {1, 2}) cands.push_back({per, 32, grid0 * gm, 0.f});

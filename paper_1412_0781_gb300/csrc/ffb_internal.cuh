@@ -64,6 +64,8 @@ struct ffb_plan_s {
     float4 *d_ang = nullptr;     // [n_theta/2] (cos hi, cos lo, sin hi, sin lo)
     int4 *d_cov_work = nullptr;  // covariance work items (k, q0, q0', 0)
     int n_cov_work = 0;
+    int4 *d_cov_sb = nullptr;    // tensor-core covariance super-blocks (k0, k1, first index, rows)
+    int n_cov_sb = 0;
     // scratch (chunk-sized)
     float2 *d_H = nullptr;       // [chunk][N/2+1][L]
     float2 *d_G = nullptr;       // [chunk][Mh][N]
@@ -347,17 +349,17 @@ struct CovStack {
     int64_t n;              // images
     int64_t item0;          // first item of the stack in the launch
     const int *pk, *off, *cov_off;
-    const int4 *work;       // FP32 kernel: (k, q0, q1) tiles
+    const int4 *work;       // FP32 kernel: (k, q0, q1) tiles; tensor cores: super-blocks
     const float *shift;     // k = 0 pilot mean
     double *acc, *sum0;     // float64 accumulators
     int P;
-    int nk;                 // items per image range: k blocks (tensor cores) or tiles (FP32)
+    int nk;                 // items per image range: super-blocks (tensor cores) or tiles (FP32)
     int per;                // images per item
     int pmax;
 };
 struct CovGroup {
     int S;
-    int tile_imgs;          // tensor cores: largest images per MMA tile (64, 32 or 16)
+    int tile_imgs;          // tensor cores: images per MMA tile (32)
     int64_t nitems;
     CovStack st[FFB_GROUP_MAX];
 };

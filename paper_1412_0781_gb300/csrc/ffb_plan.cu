@@ -180,7 +180,7 @@ static void free_plan(ffb_plan_t p) {
     ffb_tc_release(p);
     void *ptrs[] = {p->d_zeros, p->d_xi, p->d_wq, p->d_B64, p->d_Bf, p->d_p, p->d_off,
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
-                    p->d_cov_work, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
+                    p->d_cov_work, p->d_cov_sb, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
                     p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA};
     for (void *q : ptrs)
@@ -341,6 +341,18 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     p->n_cov_work = (int)work.size();
     CK(dalloc(&p->d_cov_work, work.size()));
     CK(cudaMemcpyAsync(p->d_cov_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, s));
+    // tensor-core covariance super-blocks: runs of consecutive k with
+    // sum p_k <= 128, as (first k, end k, first coefficient index, rows)
+    std::vector<int4> sbs;
+    for (int k = 0; k <= p->k_max;) {
+        int rows = 0, k1 = k;
+        while (k1 <= p->k_max && (k1 == k || rows + p->p[k1] <= 128)) rows += p->p[k1++];
+        sbs.push_back(make_int4(k, k1, p->offset[k], rows));
+        k = k1;
+    }
+    p->n_cov_sb = (int)sbs.size();
+    CK(dalloc(&p->d_cov_sb, sbs.size()));
+    CK(cudaMemcpyAsync(p->d_cov_sb, sbs.data(), sizeof(int4) * sbs.size(), cudaMemcpyHostToDevice, s));
 
     // ---- covariance state and eig outputs ------------------------------
     CK(dalloc(&p->d_acc, p->cov_total));

@@ -491,40 +491,48 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 
 // ---------------------------------------------------------------------------
 // a6/a7 on the tensor cores: C^(k) += X X^T, X = [Re A^(k), Im A^(k)] with rows
-// q (padded to M = 128) and K = (image, re/im).  A persistent CTA walks the
-// items of a stack table (CovGroup: one k and one image range of one stack
-// per item).  For each item it stages tiles of TI images from the interleaved
-// coefficient array into the 128-byte-swizzle K-major layout (hi/lo split in
-// registers, the k = 0 rows shifted by the pilot mean and their imaginary
-// column zero) while the next tile's coefficients are already in flight to
-// registers, and issues the MMA chain (double-buffered tiles, mbarrier per
-// buffer).  Tile t of an item accumulates into TMEM accumulator t mod nacc:
-// the tensor core's float32 accumulation error grows with the number of
-// accumulate steps, so no chain covers more than ~128 images; the nacc
-// accumulators are summed in float64 and added to the float64 accumulator.
-// TI is 32 images when 32 p_k values fit the register prefetch, else 16; rows
-// q >= p_k of the staging buffer may hold another item's values, which only
-// reach accumulator entries that are never read.
+// q and K = (image, re/im).  Consecutive k whose block sizes sum to at most
+// 128 form a super-block (the plan's table: first k, end k, first coefficient
+// index, rows): its rows are the contiguous coefficient range of those k, so
+// one M = 128, N = rows chain of MMAs over the super-block's X computes every
+// C^(k) of it at once as the diagonal blocks of X X^T (the cross terms between
+// different k are formed and never read).  At L = 128 that is 38 chains per
+// image instead of 183 (the MMA issue rate bounded the per-k form).
+//
+// A persistent CTA walks the items (stack, super-block, image range).  For
+// each item it stages tiles of 32 images from the coefficient array (one
+// contiguous run of <= 128 values per image) into the 128-byte-swizzle
+// K-major layout (hi/lo split, the k = 0 rows shifted by the pilot mean and
+// their imaginary column zero); the raw values arrive by cp.async in a ring
+// COV_RS - 1 tiles ahead.  Tile t of an item accumulates into TMEM
+// accumulator t mod nacc (4 x 128 columns): the tensor core's float32
+// accumulation error grows with the number of accumulate steps, so no chain
+// covers more than 128 images (items of at most 512 images); the partial
+// sums are added in float32 and then to the float64 accumulator by atomics.
 // ---------------------------------------------------------------------------
 #define COV_NT 512   // threads of a covariance CTA
-// coefficient values per thread per tile held in registers: 8 for bf16
-// (64-image tiles), 4 for tf32 (32-image tiles)
-template <int KIND>
-__host__ __device__ constexpr int cov_pf() { return (KIND == 0) ? 4 : 8; }
+#define COV_RS 3     // tiles of coefficients in flight (shared-memory ring)
+#define COV_TI 32    // images per tile
+#define COV_PF 8     // slots per thread per tile: 128 rows x 32 images / 512
+#define COV_NACC 4   // rotating accumulators of 128 columns
 
 template <int KIND, int NP>
 __global__ void __launch_bounds__(COV_NT, 1)
-k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status) {
+k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
-    constexpr int KCH = 128 / ES;               // K elements per chunk
-    constexpr int NCHT = 2;                     // 128-byte K chunks per tile buffer
-    constexpr int PF = cov_pf<KIND>();
+    constexpr int KCH = 128 / ES;               // K elements per 128-byte chunk
+    constexpr int KT = 2 * COV_TI;              // K entries per tile
+    constexpr int NCHT = KT / KCH;              // chunks per tile: 1 (bf16) or 2 (tf32)
     constexpr int KINST = (KIND == 0) ? 8 : 16; // K per MMA instruction
     constexpr uint32_t CH_BYTES = 128u * 128u;  // one chunk of 128 rows
     constexpr uint32_t BUF_BYTES = NP * NCHT * CH_BYTES;
+    static_assert(NCHT * KCH == KT, "whole chunks per tile");
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(sm + 2 * BUF_BYTES);   // [0], [1]: buffer free
+    // per-thread ring of raw coefficient slots (each thread reads back only
+    // its own slots)
+    float2 *raw = (float2 *)(sm + 2 * BUF_BYTES);
+    uint64_t *bars = (uint64_t *)(sm + 2 * BUF_BYTES + (size_t)COV_RS * COV_NT * COV_PF * sizeof(float2));
     uint32_t *slot = (uint32_t *)(bars + 4);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,49 +558,49 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
     for (int64_t item = blockIdx.x; item < g.nitems && *okflag; item += gridDim.x) {
         const CovStack &S = g.st[cov_stack_of(g, item)];
         const int64_t local = item - S.item0;
-        const int k = (int)(local % S.nk);
+        const int4 sb = S.work[local % S.nk];       // (first k, end k, first index, rows)
         const int64_t ib = (local / S.nk) * (int64_t)S.per;
         const int64_t ie = min(S.n, ib + (int64_t)S.per);
-        const int p = S.pk[k], o = S.off[k];
-        const int BN = max(16, (p + 15) & ~15);
-        // (image, q) slots of a tile: each warp covers 8 rows q x 4 images,
+        const int rows = sb.w, row0 = sb.z;
+        const int p0 = (sb.x == 0) ? S.pk[0] : 0;   // rows of k = 0 (shifted, real)
+        const int BN = max(16, (rows + 15) & ~15);
+        // (image, row) slots of a tile: each warp covers 8 rows x 4 images,
         // so that its stores into the swizzled K-major tile fall on distinct
-        // banks; QBP 8-row blocks (a power of two >= p/8) index by shifts
+        // banks; QBP 8-row blocks (a power of two >= rows/8) index by shifts
         int lgQ = 0;
-        while ((8 << lgQ) < p) ++lgQ;
+        while ((8 << lgQ) < rows) ++lgQ;
         const int QBP = 1 << lgQ;
-        // images per tile: 64 (bf16: two K chunks), 32 or 16, as the staging
-        // slots and the buffer's two K chunks allow
-        const int ti_max = (KIND == 0) ? 32 : 64;
-        int TI = 16;
-        if (g.tile_imgs >= 32 && 8 * QBP * 32 <= COV_NT * PF) TI = 32;
-        if (ti_max >= 64 && g.tile_imgs >= 64 && 8 * QBP * 64 <= COV_NT * PF) TI = 64;
-        const int items = 8 * QBP * TI;
-        const int kent = 2 * TI;                    // K entries per tile
-        const int ntiles = (ie > ib) ? (int)((ie - ib + TI - 1) / TI) : 0;
-        if (items > COV_NT * PF || BN > acc_cols) {   // uniform across the CTA
+        const int nslots = 8 * QBP * COV_TI;
+        const int ntiles = (ie > ib) ? (int)((ie - ib + COV_TI - 1) / COV_TI) : 0;
+        if (nslots > COV_NT * COV_PF || rows > 128) {   // uniform across the CTA
             if (threadIdx.x == 0) ffb_flag(status, FFB_ERR_UNSUPPORTED);
             continue;
         }
         const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
-        const float2 *coef = S.coef;
+        const float2 *coef = S.coef + row0;
         const int P = S.P;
 
-        float2 pre[PF];
-        auto load_tile = [&](int t) {
-            const int64_t i0 = ib + (int64_t)t * TI;
+        // one commit group per tile (empty past the last one), so that
+        // "all but the newest COV_RS - 1 groups complete" means tile t landed
+        auto issue_tile = [&](int t) {
+            if (t < ntiles) {
+                const int64_t i0 = ib + (int64_t)t * COV_TI;
+                float2 *st = raw + (size_t)(t % COV_RS) * COV_NT * COV_PF;
 #pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int it = threadIdx.x + COV_NT * u;
-                float2 v = make_float2(0.f, 0.f);
-                if (it < items) {
-                    const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7), ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
-                    if (q < p && i0 + ii < ie) v = __ldg(&coef[(i0 + ii) * P + o + q]);
+                for (int u = 0; u < COV_PF; ++u) {
+                    const int it = threadIdx.x + COV_NT * u;
+                    if (it < nslots) {
+                        const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7),
+                                  ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
+                        if (q < rows && i0 + ii < ie) tc::cp_async8(&st[it], &coef[(i0 + ii) * P + q]);
+                        else st[it] = make_float2(0.f, 0.f);
+                    }
                 }
-                pre[u] = v;
             }
+            tc::cp_async_commit();
         };
-        if (ntiles > 0) load_tile(0);
+#pragma unroll
+        for (int t = 0; t < COV_RS - 1; ++t) issue_tile(t);
         for (int t = 0; t < ntiles && *okflag; ++t, ++gt) {
             const int buf = (int)(gt & 1);
             uint8_t *B0 = sm + buf * BUF_BYTES;
@@ -602,19 +610,20 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
                     atomicExch(okflag, 0);
                 }
             }
-            float2 cur[PF];
+            issue_tile(t + COV_RS - 1);               // COV_RS - 1 tiles stay in flight
+            tc::cp_async_wait<COV_RS - 1>();
+            const float2 *st = raw + (size_t)(t % COV_RS) * COV_NT * COV_PF;
+            const bool last = (ib + (int64_t)(t + 1) * COV_TI > ie);
 #pragma unroll
-            for (int u = 0; u < PF; ++u) cur[u] = pre[u];
-            if (t + 1 < ntiles) load_tile(t + 1);     // next tile's loads overlap this staging
-#pragma unroll
-            for (int u = 0; u < PF; ++u) {
+            for (int u = 0; u < COV_PF; ++u) {
                 const int it = threadIdx.x + COV_NT * u;
-                if (it >= items) break;
+                if (it >= nslots) break;
                 const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7), ii = 4 * (pr >> lgQ) + ((it >> 3) & 3);
-                if (q >= p) continue;   // rows past p_k of the last 8-row block
-                float re = cur[u].x, im = cur[u].y;
-                if (k == 0) {   // shifted real part; images past the range stay zero
-                    re = (ib + (int64_t)t * TI + ii < ie) ? re - S.shift[q] : 0.f;
+                if (q >= rows) continue;   // rows past the super-block in the last 8-row block
+                const float2 v = st[it];
+                float re = v.x, im = v.y;
+                if (q < p0) {   // k = 0: shifted real part; images past the range stay zero
+                    re = (!last || ib + (int64_t)t * COV_TI + ii < ie) ? re - S.shift[q] : 0.f;
                     im = 0.f;
                 }
                 const int kidx = 2 * ii;                 // K index of the real part
@@ -627,31 +636,31 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
                     *(float2 *)(B0 + off) = make_float2(rh, ih);
                     if (NP > 1) *(float2 *)(B0 + NCHT * CH_BYTES + off) = make_float2(re - rh, im - ih);
                 } else {
-                    const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
-                    *(__nv_bfloat162 *)(B0 + off) = __halves2bfloat162(rh, ih);
-                    if (NP > 1)
-                        *(__nv_bfloat162 *)(B0 + NCHT * CH_BYTES + off) = __halves2bfloat162(
-                            __float2bfloat16_rn(re - __bfloat162float(rh)),
-                            __float2bfloat16_rn(im - __bfloat162float(ih)));
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+                    *(__nv_bfloat162 *)(B0 + off) = h;
+                    if (NP > 1) {
+                        const float2 hf = __bfloat1622float2(h);
+                        *(__nv_bfloat162 *)(B0 + NCHT * CH_BYTES + off) = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+                    }
                 }
             }
             tc::fence_async_shared();   // generic-proxy writes -> visible to the tensor core
             __syncthreads();
             if (threadIdx.x == 0 && *okflag) {
                 tc::fence_after_sync();
-                const uint32_t dt = tbase + (uint32_t)((t % nacc) * acc_cols);
-                const int nch = (kent + KCH - 1) / KCH;
+                const uint32_t dt = tbase + (uint32_t)((t % COV_NACC) * 128);
 #pragma unroll
                 for (int pr = 0; pr < (NP > 1 ? 3 : 1); ++pr) {
                     const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-                    for (int ch = 0; ch < nch; ++ch) {
+#pragma unroll
+                    for (int ch = 0; ch < NCHT; ++ch) {
                         const uint32_t a0 = tc::smem_u32(B0 + (size_t)(pa * NCHT + ch) * CH_BYTES);
                         const uint32_t b0 = tc::smem_u32(B0 + (size_t)(pb * NCHT + ch) * CH_BYTES);
-                        const int nks = min(KCH, kent - ch * KCH) / KINST;
-                        for (int ks = 0; ks < nks; ++ks) {
+#pragma unroll
+                        for (int ks = 0; ks < KCH / KINST; ++ks) {
                             const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
                             const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
-                            const uint32_t accf = (t >= nacc || pr > 0 || ch > 0 || ks > 0) ? 1u : 0u;
+                            const uint32_t accf = (t >= COV_NACC || pr > 0 || ch > 0 || ks > 0) ? 1u : 0u;
                             if (KIND == 0) tc::mma_tf32(dt, ad, bd, id, accf);
                             else tc::mma_bf16(dt, ad, bd, id, accf);
                         }
@@ -660,6 +669,7 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
                 tc::mma_commit(&bars[buf]);
             }
         }
+        tc::cp_async_wait<0>();   // no copy of this item outstanding (an early exit leaves some)
         __syncthreads();
         // the last commit covers every MMA issued before it
         if (ntiles > 0 && *okflag) {
@@ -671,25 +681,45 @@ k_tc_cov(const __grid_constant__ CovGroup g, int acc_cols, int nacc, int *status
         tc::fence_after_sync();
         __syncthreads();
         if (ntiles > 0 && *okflag) {
-            // warp w reads TMEM lanes 32 (w mod 4) .. + 31 and every fourth
-            // group of 16 columns
+            // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows q); row q of
+            // block k keeps columns [rk, rk + pk) of its own k.  The warp loads
+            // the 16-column groups spanning its lanes' ranges, every fourth
+            // group per column set w / 4
             const int q = 32 * (warp & 3) + lane;
-            const int used = min(nacc, ntiles);
-            double *blk = S.acc + S.cov_off[k];
-            for (int c16 = 16 * (warp >> 2); c16 < BN; c16 += 16 * (COV_NT / 128)) {
-                double sum[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) sum[i] = 0.0;
-                for (int a = 0; a < used; ++a) {
-                    float v[16];
-                    tc::tmem_ld16(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(a * acc_cols + c16), v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) sum[i] += (double)v[i];
+            int kq = -1, rk = 0, pq = 0;
+            if (q < rows) {
+                for (int k = sb.x; k < sb.y; ++k) {
+                    const int r = S.off[k] - row0, pk = S.pk[k];
+                    if (q >= r && q < r + pk) {
+                        kq = k;
+                        rk = r;
+                        pq = pk;
+                        break;
+                    }
                 }
-                if (q < p) {
+            }
+            int lo = (kq >= 0) ? rk : 1 << 20, hi = (kq >= 0) ? rk + pq : 0;
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            const int used = min(COV_NACC, ntiles);
+            double *blk = (kq >= 0) ? S.acc + S.cov_off[kq] : nullptr;
+            for (int c16 = (lo & ~15) + 16 * (warp >> 2); c16 < hi; c16 += 64) {
+                float sum[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c16, sum);
+                for (int a = 1; a < used; ++a) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(a * 128 + c16), v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c16 + i < p) atomicAdd(&blk[(size_t)q * p + c16 + i], sum[i]);
+                    for (int i = 0; i < 16; ++i) sum[i] += v[i];
+                }
+                if (kq >= 0) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int c = c16 + i;
+                        if (c >= rk && c < rk + pq) atomicAdd(&blk[(size_t)(q - rk) * pq + (c - rk)], (double)sum[i]);
+                    }
                 }
             }
         }
@@ -718,19 +748,16 @@ __global__ void k_cov_sum0(const __grid_constant__ CovGroup g, int64_t per0) {
     }
 }
 
-// sized for two planes in every precision: one CTA per SM, so the 512-column
-// TMEM allocation never waits for another CTA
+// one CTA per SM, so the 512-column TMEM allocation never waits for another CTA
 static size_t tc_cov_smem(int prec) {
-    (void)prec;
-    return 1024 + 2 * (size_t)2 * 2 * 128 * 128 + 64;
+    const bool tf = (prec == FFB_TF32 || prec == FFB_TF32X3);
+    const size_t nchunk = tf ? 2 : 1;   // 128-byte K chunks per 32-image tile
+    return 1024 + 2 * (size_t)2 * nchunk * 128 * 128 + (size_t)COV_RS * COV_NT * COV_PF * sizeof(float2) + 64;
 }
 
 bool ffb_tc_cov_supported(ffb_plan_t p) {
     if (p->precision == FFB_FP32) return false;
-    if (((p->pmax + 15) & ~15) > 128) return false;   // rows q live in one M = 128 tile
-    int qbp = 1;
-    while (8 * qbp < p->pmax) qbp <<= 1;
-    if (8 * qbp * 16 > COV_NT * cov_pf<0>()) return false;   // a 16-image tile fits the prefetch
+    if (p->pmax > 128) return false;   // a block's rows live in one M = 128 tile
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -739,7 +766,7 @@ bool ffb_tc_cov_supported(ffb_plan_t p) {
 
 template <int KIND, int NP>
 static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t s) {
-    const size_t smem = tc_cov_smem(0);
+    const size_t smem = tc_cov_smem(KIND == 0 ? FFB_TF32 : FFB_BF16);
     static int attr = 0;
     if (attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_cov<KIND, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -747,13 +774,11 @@ static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t 
         if (e) return e;
         attr = (int)smem;
     }
-    int pmax = 16;
-    for (int i = 0; i < g.S; ++i) pmax = max(pmax, g.st[i].pmax);
-    int cols = 32;
-    while (cols < ((pmax + 15) & ~15)) cols <<= 1;
-    if (cols > 128) return FFB_ERR_UNSUPPORTED;
-    const int nacc = 512 / cols > 8 ? 8 : 512 / cols;   // rotating float32 accumulators in TMEM
-    k_tc_cov<KIND, NP><<<grid, COV_NT, smem, s>>>(g, cols, nacc, status);
+    // accumulator a takes the tiles t = a mod COV_NACC of an item: chains of
+    // at most 128 images
+    for (int i = 0; i < g.S; ++i)
+        if (g.st[i].per > 128 * COV_NACC) return FFB_ERR_ARG;
+    k_tc_cov<KIND, NP><<<grid, COV_NT, smem, s>>>(g, status);
     return ffb_check_cuda(cudaGetLastError());
 }
 
@@ -781,11 +806,10 @@ int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *sta
 int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
     CovGroup g;          // copied into the launch's parameters
     g.S = 1;
-    g.tile_imgs = 64;
+    g.tile_imgs = COV_TI;
     ffb_cov_stack(p, d_coef, n, true, &g.st[0]);
     g.st[0].item0 = 0;
-    g.st[0].per = 1024;
-    g.nitems = (int64_t)g.st[0].nk * ((n + 1023) / 1024);
+    g.nitems = (int64_t)g.st[0].nk * ((n + g.st[0].per - 1) / g.st[0].per);
     ProfScope ps(p, FFB_KC_COV, s);
     const int e = ffb_launch_cov_group_tc(p->precision, g, 0, p->d_status, s);
     p->launches += 2;
