@@ -121,6 +121,9 @@ def algorithmic_flops(plan):
     }
 
 
+PROF_STRIDE = 32   # kernel timing: every 32nd launch of each kernel class
+
+
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (profiles/k_grid_interp_half_L128.md: 152-image launch), valid only
 # while the kernel's sources are byte-identical to the profiled ones (the
@@ -276,7 +279,10 @@ def run_ours(args):
         sampler = ClockSampler(local)
         sampler.start()
         time.sleep(0.3)
-        plan.profile(True)
+        # kernel durations from CUDA events around every PROF_STRIDE-th launch
+        # of each kernel class inside the timed region (events around every
+        # launch would add their own cost to the step)
+        plan.profile(True, stride=PROF_STRIDE)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
@@ -321,6 +327,7 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": ncu_traffic(dom, imgs_per_launch),
                 "peak_note": "FP32 FFMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, max clock)",
                 "kernel_ms_per_launch": dom_ms / dom_calls, "images_per_launch": imgs_per_launch,
+                "kernel_timing": "CUDA events around every %dth launch of each kernel in the timed region" % PROF_STRIDE,
                 "share": share}
 
     # end to end through the public API with host buffers

@@ -243,14 +243,17 @@ int ffb_denoise(ffb_plan_t plan, const float *d_images, int64_t n, int mode,
  * (then clears it). */
 int ffb_sync(ffb_plan_t plan, void *stream);
 
-/* ffb_profile -- enable (1) or disable (0) per-launch timing: every kernel
- * the plan launches is bracketed by two CUDA events on its stream.  Enabling
- * discards earlier records. */
+/* ffb_profile -- per-launch timing: enable = 0 turns it off; enable = s >= 1
+ * brackets every s-th launch of each kernel class (the first included) by two
+ * CUDA events on its stream (s = 1: every launch; a larger stride keeps the
+ * events' own cost out of a timed run).  Enabling discards earlier records.
+ * FFB_ERR_ARG for enable < 0. */
 int ffb_profile(ffb_plan_t plan, int enable);
 
-/* ffb_profile_read -- sums the recorded launch durations per kernel class
- * into h_ms[16] (milliseconds) and h_calls[16] (launches), then discards the
- * records.  Classes: 0 rows FFT, 1 column FFT, 2 interpolation + ring DFT,
+/* ffb_profile_read -- per kernel class: h_ms[16] the launches' total duration
+ * in milliseconds (with a stride s > 1 the mean of the timed launches times
+ * the launch count), h_calls[16] the launches since profiling was enabled;
+ * then discards the records.  Classes: 0 rows FFT, 1 column FFT, 2 interpolation + ring DFT,
  * 3 radial quadrature, 4 covariance, 5 covariance shift/finalise, 6 Jacobi,
  * 7 transposed quadrature, 8 inverse ring DFT + spreading, 9 inverse column
  * FFT, 10 inverse row FFT + deconvolution, 11 steerable filter, 12 setup,

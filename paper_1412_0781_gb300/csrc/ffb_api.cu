@@ -27,9 +27,10 @@ extern "C" int ffb_sync(ffb_plan_t p, void *stream) {
 }
 
 extern "C" int ffb_profile(ffb_plan_t p, int enable) {
-    if (!p) return FFB_ERR_ARG;
-    p->prof_on = enable ? 1 : 0;
+    if (!p || enable < 0) return FFB_ERR_ARG;
+    p->prof_on = enable;
     p->prof_used = 0;
+    for (int c = 0; c < 16; ++c) p->prof_calls[c] = 0;
     return FFB_OK;
 }
 
@@ -39,13 +40,20 @@ extern "C" int ffb_profile_read(ffb_plan_t p, double *h_ms, int64_t *h_calls) {
         h_ms[c] = 0.0;
         h_calls[c] = 0;
     }
+    int64_t timed[FFB_NKC] = {};
     for (size_t i = 0; i < p->prof_used; ++i) {
         const ProfEv &e = p->prof[i];
         if (cudaEventSynchronize(e.b) != cudaSuccess) return FFB_ERR_CUDA;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) return FFB_ERR_CUDA;
         h_ms[e.cls] += ms;
-        h_calls[e.cls] += 1;
+        timed[e.cls] += 1;
+    }
+    // sampled classes: the mean timed duration times the launches
+    for (int c = 0; c < FFB_NKC; ++c) {
+        h_calls[c] = p->prof_calls[c];
+        if (timed[c] > 0) h_ms[c] *= (double)p->prof_calls[c] / (double)timed[c];
+        p->prof_calls[c] = 0;
     }
     p->prof_used = 0;
     return FFB_OK;
@@ -60,7 +68,7 @@ extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, n - i0);
         if (p->fused) {
-            CK(ffb_launch_fused_polar(p, d_images, i0, m, (float2 *)(d_F + (size_t)i0 * per), s));
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, (float2 *)(d_F + (size_t)i0 * per), s, i0 > 0));
         } else {
             CK(ffb_launch_grid(p, d_images, i0, m, s));
             CK(ffb_launch_polar(p, m, d_F + (size_t)i0 * per, s));
@@ -87,7 +95,8 @@ int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef,
         for (int64_t i0 = g0; i0 < g1; i0 += p->chunk) {
             int m = (int)std::min<int64_t>(p->chunk, g1 - i0);
             if (p->fused) {
-                CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s));
+                // chunks after the first follow this call's own kernels
+                CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0));
                 RingOut r = ring;   // this chunk's images in the group's planes
                 const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
                 r.p0 = (char *)ring.p0 + off;

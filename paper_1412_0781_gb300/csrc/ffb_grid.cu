@@ -181,6 +181,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     const int half = blockIdx.x;
     const int img = blockIdx.y;
     const float *im = images + (size_t)img * L * L;
+    pdl_trigger();
     // cluster: the peer's S in the cluster window, this CTA's share of the
     // transforms (every second one)
     unsigned peerS = 0;
@@ -260,6 +261,10 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     // and no CTA touches its peer's shared memory after this barrier)
     if constexpr (CL) cluster_sync_all();
     else __syncthreads();
+
+    // the polar buffer may still be read by the previous kernel (the ring FFT
+    // of the previous chunk) when this launch started early
+    pdl_wait();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
     // block b of the half covers the nodes t in [t0, t0 + cnt);
@@ -392,8 +397,11 @@ static int fused_cluster_ok() {
     return (2 * ncl >= sms) ? 1 : 0;
 }
 
+// pdl: launched with programmatic serialization (the previous kernel in the
+// stream is one of this library's and does not write the images)
 template <int N, int W>
-static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {
+static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
+                        bool pdl) {
     static int attr = 0, attr_cl = 0;
     const size_t smem = fused_smem<N, W>();
     const bool cl = p->fused == 2;
@@ -406,32 +414,30 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
     }
     const float *img = d_images + (size_t)i0 * p->L * p->L;
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, m);
+    cfg.blockDim = dim3(FUS_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    int na = 0;
     if (cl) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2, m);
-        cfg.blockDim = dim3(FUS_NT);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_grid_interp_half<N, W, true>, img, p->off,
-                                                  (const float *)p->d_corr, (const float2 *)p->d_twN, p->n_xi,
-                                                  p->n_theta, p->nq0, (const float4 *)p->d_nodes,
-                                                  (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1],
-                                                  Fpol, p->d_status));
-        p->launches++;
-        return e;
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = 2;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
     }
-    k_grid_interp_half<N, W, false><<<dim3(2, m), FUS_NT, smem, s>>>(
-        img, p->off, p->d_corr, p->d_twN, p->n_xi, p->n_theta, p->nq0, p->d_nodes, p->d_node_blk,
-        p->node_nblk[0], p->node_nblk[1], Fpol, p->d_status);
+    if (pdl) at[na++] = ffb_pdl_attr();
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, cl ? k_grid_interp_half<N, W, true> : k_grid_interp_half<N, W, false>,
+                                              img, p->off, (const float *)p->d_corr, (const float2 *)p->d_twN,
+                                              p->n_xi, p->n_theta, p->nq0, (const float4 *)p->d_nodes,
+                                              (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
+                                              p->d_status));
     p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
+    return e;
 }
 
 int ffb_fused_mode(ffb_plan_t p) {
@@ -614,8 +620,9 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
     return e;
 }
 
-int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s) {
-    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s);
-    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s);
+int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
+                           bool pdl) {
+    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s, pdl);
+    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s, pdl);
     return FFB_ERR_UNSUPPORTED;
 }

@@ -100,9 +100,10 @@ struct ffb_plan_s {
     // tensor-core operand tables and TMA descriptors (ffb_tc.cu)
     void *tc = nullptr;
     // optional per-launch timing
-    int prof_on = 0;
+    int prof_on = 0;                 // 0 off, else the sampling stride
     size_t prof_used = 0;
     std::vector<ProfEv> prof;
+    int64_t prof_calls[16] = {};     // launches per class since profiling was enabled
 };
 
 // Brackets one launch with events when profiling is on (host side).
@@ -112,6 +113,8 @@ struct ProfScope {
     int idx;
     ProfScope(ffb_plan_s *p_, int cls, cudaStream_t s_) : p(p_), s(s_), idx(-1) {
         if (!p->prof_on) return;
+        // every prof_on-th launch of each class is timed (the first included)
+        if (p->prof_calls[cls & 15]++ % p->prof_on != 0) return;
         if (p->prof_used == p->prof.size()) {
             ProfEv e;
             if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
@@ -131,6 +134,23 @@ struct ProfScope {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void ffb_flag(int *status, int code) {
     atomicCAS(status, 0, code);
+}
+
+// Programmatic dependent launch: a kernel launched with the
+// programmatic-serialization attribute may start while the previous kernel
+// in its stream runs; pdl_wait() returns once that kernel has completed and
+// its memory operations are visible (immediately without the attribute);
+// pdl_trigger() lets this kernel's own dependents launch once every CTA of it
+// has executed it or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// the launch attribute for it
+static inline cudaLaunchAttribute ffb_pdl_attr() {
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a.val.programmaticStreamSerializationAllowed = 1;
+    return a;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -310,7 +330,7 @@ int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_fused_mode(ffb_plan_t plan);   // 1 plain, 2 cluster variant of the fused kernel
 int ffb_ring_prepare(ffb_plan_t plan, cudaStream_t s);   // ring FFT twiddle table (fused path)
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
-                           cudaStream_t s);
+                           cudaStream_t s, bool pdl = false);
 struct RingOut {
     int fmt;           // FFB_FMT_*
     void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra), at the launch's first image

@@ -50,6 +50,8 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
     const int ostld = (2 * (kmax + 1)) | 1;              // odd: the write-out reads conflict-free
     const int img = blockIdx.y;
     const int j0 = blockIdx.x * RFFT_RB;
+    pdl_trigger();
+    pdl_wait();   // the polar buffer comes from the previous kernel
     const int ring = j0 + warp;
     // pass A below yields half of each DFT value: the weight 2 pi / n_theta
     // carries the factor 2
@@ -221,10 +223,20 @@ static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOu
     }
     dim3 g((p->n_xi + RFFT_RB - 1) / RFFT_RB, m);
     ProfScope ps(p, FFB_KC_RING_FFT, s);
-    k_ring_fft<NTH, FMT><<<g, 32 * RFFT_RB, smem, s>>>(Fpol, p->n_xi, p->k_max, o.lead, p->d_twT, p->d_twA, o.p0,
-                                                        o.p1, o.ld);
+    // launched with programmatic serialization after the grid kernel
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = dim3(32 * RFFT_RB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_ring_fft<NTH, FMT>, Fpol, p->n_xi, p->k_max, o.lead,
+                                                    (const float2 *)p->d_twT, (const float2 *)p->d_twA, o.p0, o.p1,
+                                                    o.ld));
     p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
+    return e;
 }
 
 template <int NTH>

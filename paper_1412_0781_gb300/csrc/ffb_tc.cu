@@ -113,6 +113,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int myitems = (blockIdx.x < nitems) ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    pdl_trigger();
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * nst; ++i) tc::mbar_init(&bars[i], 1);
@@ -134,6 +135,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
 
     if (warp == 0) {
         if (lane == 0) {                                  // ---- TMA producer
+            pdl_wait();   // the operand planes come from the previous kernels
             int64_t g = 0;
             bool ok = true;
             for (int it = 0; it < myitems && ok; ++it) {
@@ -456,11 +458,22 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     const int nitems = nM * (p->k_max + 1);
     const int grid = nitems < per_sm * sms ? nitems : per_sm * sms;   // persistent CTAs
     ProfScope ps(p, FFB_KC_BESSEL, s);
-    k_tc_bessel<KIND, NPA, NPB, NPROD><<<grid, 32 * TCB_WARPS, smem, s>>>(
-        t->mA0, t->mA1, t->mB0, t->mB1, t->ld, nimg, p->d_p, p->d_off, p->P, d_coef_chunk, t->BN, t->tmem_cols, nst,
-        nM, nitems, p->d_status);
+    // launched with programmatic serialization: the prologue (barriers, TMEM)
+    // overlaps the previous kernel's tail; the producer waits before its loads
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * TCB_WARPS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD>, t->mA0, t->mA1, t->mB0,
+                                                    t->mB1, t->ld, nimg, (const int *)p->d_p, (const int *)p->d_off,
+                                                    p->P, d_coef_chunk, t->BN, t->tmem_cols, nst, nM, nitems,
+                                                    p->d_status));
     p->launches++;
-    return ffb_check_cuda(cudaGetLastError());
+    return e;
 }
 
 int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s) {

@@ -183,11 +183,13 @@ class Plan:
                       "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup",
                       "grid_interp", "ring_fft"]
 
-    def profile(self, enable=True):
-        _check(load().ffb_profile(self._h, int(bool(enable))), "ffb_profile")
+    def profile(self, enable=True, stride=1):
+        """Time every ``stride``-th launch of each kernel class (off if not enable)."""
+        _check(load().ffb_profile(self._h, int(stride) if enable else 0), "ffb_profile")
 
     def profile_read(self):
-        """{class: (total_ms, launches)} of the launches recorded since profile(True)."""
+        """{class: (total_ms, launches)} since profile(True); with a stride,
+        total_ms is the timed launches' mean times the launch count."""
         ms = (ctypes.c_double * 16)()
         calls = (ctypes.c_int64 * 16)()
         _check(load().ffb_profile_read(self._h, ms, calls), "ffb_profile_read")
