@@ -249,15 +249,29 @@ int ffb_launch_cov_group(int precision, const CovGroup &g, int grid, int *status
     return ffb_check_cuda(cudaGetLastError());
 }
 
-// pilot shift for the k = 0 block: mean of a_0 over the first min(n, 4096)
-// images of the first batch after a reset
-__global__ void k_cov_shift(const float2 *__restrict__ coef, int64_t n, int P, int p0, float *shift) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= p0) return;
-    int64_t m = min(n, (int64_t)4096);
-    double s = 0.0;
-    for (int64_t i = 0; i < m; ++i) s += (double)coef[i * P + q].x;
-    shift[q] = (float)(s / (double)m);
+// pilot shift for the k = 0 block: mean of Re a_{i,0,q} over the first
+// min(n, 512) images of the first batch after a reset (any shift near the
+// mean keeps the shifted sums well conditioned; C = acc/n - d d^T is exact for
+// every shift).  Block of 4 x 64 threads: q = threadIdx.x % 64 within the
+// block's 64 rows, image group threadIdx.x / 64 (every fourth image).
+__global__ void __launch_bounds__(256) k_cov_shift(const float2 *__restrict__ coef, int64_t n, int P, int p0,
+                                                   float *shift) {
+    __shared__ float part[4][64];
+    const int qq = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int q = blockIdx.x * 64 + qq;
+    const int m = (int)min(n, (int64_t)512);
+    float s0 = 0.f, s1 = 0.f;
+    if (q < p0) {
+        int i = grp;
+        for (; i + 4 < m; i += 8) {
+            s0 += coef[(int64_t)i * P + q].x;
+            s1 += coef[(int64_t)(i + 4) * P + q].x;
+        }
+        if (i < m) s0 += coef[(int64_t)i * P + q].x;
+    }
+    part[grp][qq] = s0 + s1;
+    __syncthreads();
+    if (grp == 0 && q < p0) shift[q] = (part[0][qq] + part[1][qq] + part[2][qq] + part[3][qq]) / (float)m;
 }
 
 // C^(k) = acc^(k)/n; for k = 0: C = acc/n - d d^T, mean = shift + d, d = sum0/n
@@ -281,7 +295,7 @@ __global__ void k_cov_final(const double *__restrict__ acc, const double *__rest
 
 int ffb_launch_cov_shift(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
     ProfScope ps(p, FFB_KC_COVAUX, s);
-    k_cov_shift<<<(p->p[0] + 63) / 64, 64, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0], p->d_shift);
+    k_cov_shift<<<(p->p[0] + 63) / 64, 256, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0], p->d_shift);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }

@@ -85,7 +85,7 @@ __device__ __forceinline__ int fswz(int k) {
 
 template <int N>
 __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, const float2 *__restrict__ tw,
-                                                  int lane) {
+                                                  const float2 *__restrict__ twA, int lane) {
     static_assert(N == 128 || N == 256, "N in {128, 256}");
     constexpr int M = N / 32, R = 32 / M;
     float2 x[M];
@@ -118,8 +118,9 @@ __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, 
         x[0] = cadd(a, d); x[1] = make_float2(a.x - d.y, a.y + d.x);
         x[2] = csub(a, d); x[3] = make_float2(a.x + d.y, a.y - d.x);
     }
+    // W^{lane k1} from the plan's table [k1][lane] (coalesced)
 #pragma unroll
-    for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&tw[(lane * k1) & (N - 1)]));
+    for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twA[k1 * 32 + lane]));
 #pragma unroll
     for (int k1 = 0; k1 < M; ++k1) buf[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
     __syncwarp();
@@ -166,7 +167,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 template <int N, int W, bool CL>
 __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
-                   const float2 *__restrict__ tw, int n_xi, int n_theta, int nq0,
+                   const float2 *__restrict__ tw, const float2 *__restrict__ twA, int n_xi, int n_theta, int nq0,
                    const float4 *__restrict__ units, const int2 *__restrict__ blocks, int nblk0, int nblk1,
                    float2 *__restrict__ Fpol, int *status) {
     constexpr int L = N / 2;
@@ -215,7 +216,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             const float ca = corr[a2];
             z[q] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
         }
-        warp_fft_halfzero<N>(z, buf, tw, lane);
+        warp_fft_halfzero<N>(z, buf, tw, twA, lane);
         for (int e = lane; e < MH; e += 32) {
             const int m = (e - H) & (N - 1);
             const float2 Z = buf[fswz<N>(m)];
@@ -247,7 +248,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
         float2 z[L / 32];
 #pragma unroll
         for (int q = 0; q < L / 32; ++q) z[q] = row[lane + 32 * q];
-        warp_fft_halfzero<N>(z, buf, tw, lane);
+        warp_fft_halfzero<N>(z, buf, tw, twA, lane);
         for (int c = lane; c < MH; c += 32) row[c] = buf[fswz<N>((c + m1lo) & (N - 1))];
         if (lane < SLD - MH) row[MH + lane] = make_float2(0.f, 0.f);
         if constexpr (CL) {
@@ -433,7 +434,7 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
     cfg.numAttrs = na;
     int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, cl ? k_grid_interp_half<N, W, true> : k_grid_interp_half<N, W, false>,
                                               img, p->off, (const float *)p->d_corr, (const float2 *)p->d_twN,
-                                              p->n_xi, p->n_theta, p->nq0, (const float4 *)p->d_nodes,
+                                              (const float2 *)p->d_twG, p->n_xi, p->n_theta, p->nq0, (const float4 *)p->d_nodes,
                                               (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
                                               p->d_status));
     p->launches++;
@@ -603,6 +604,23 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             ++nb[half];
             t0 = t1;
         }
+    }
+    // FFT twiddles W_N^{j k1} as [k1][j] (k1 < N / 32, j < 32), from float64
+    {
+        const int MG = N / 32;
+        std::vector<float2> twg((size_t)MG * 32);
+        for (int k1 = 0; k1 < MG; ++k1)
+            for (int j = 0; j < 32; ++j) {
+                const double a = -2.0 * M_PI * (double)((j * k1) % N) / (double)N;
+                twg[(size_t)k1 * 32 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        if (p->d_twG) cudaFree(p->d_twG);
+        p->d_twG = nullptr;
+        e = ffb_check_cuda(cudaMalloc((void **)&p->d_twG, sizeof(float2) * twg.size()));
+        if (!e) e = ffb_check_cuda(cudaMemcpyAsync(p->d_twG, twg.data(), sizeof(float2) * twg.size(),
+                                                   cudaMemcpyHostToDevice, s));
+        if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
+        if (e) return e;
     }
     if (p->d_nodes) cudaFree(p->d_nodes);
     if (p->d_node_blk) cudaFree(p->d_node_blk);

@@ -230,7 +230,7 @@ static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent) {
     int64_t gl = 0;
     if (cg.nitems > 0) {
         CKG(ffb_launch_cov_group(g->precision, cg, g->grid, g->d_status, main));
-        gl = (g->precision == FFB_FP32) ? 1 : 2;
+        gl = 1;
     }
     if (ent) {
         ent->plan_launches.resize(g->S);

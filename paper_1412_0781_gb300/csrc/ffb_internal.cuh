@@ -74,6 +74,7 @@ struct ffb_plan_s {
     float4 *d_nodes = nullptr;   // [blocks][9][units] phase-3 unit records (fused path)
     int2 *d_node_blk = nullptr;  // [blocks] (first node, node count), half 0 then half 1
     float2 *d_twA = nullptr;     // [n_theta/32][32] ring FFT twiddles W^{j k1} (fused path)
+    float2 *d_twG = nullptr;     // [N/32][32] grid FFT twiddles W_N^{j k1} (fused path)
     int node_nblk[2] = {0, 0};   // blocks per half
     // covariance state
     double *d_acc = nullptr;     // [cov_total] sum Re(a a^*), k = 0 shifted

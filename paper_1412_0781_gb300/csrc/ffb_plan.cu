@@ -182,7 +182,7 @@ static void free_plan(ffb_plan_t p) {
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
                     p->d_cov_work, p->d_cov_sb, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
-                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA};
+                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA, p->d_twG};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (ProfEv &e : p->prof) {

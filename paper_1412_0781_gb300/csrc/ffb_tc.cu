@@ -516,7 +516,8 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 // each item it stages tiles of 32 images from the coefficient array (one
 // contiguous run of <= 128 values per image) into the 128-byte-swizzle
 // K-major layout (hi/lo split, the k = 0 rows shifted by the pilot mean and
-// their imaginary column zero); the raw values arrive by cp.async in a ring
+// their imaginary column zero, and summed per row for the k = 0 mean); the
+// raw values arrive by cp.async in a ring
 // COV_RS - 1 tiles ahead.  Tile t of an item accumulates into TMEM
 // accumulator t mod nacc (4 x 128 columns): the tensor core's float32
 // accumulation error grows with the number of accumulate steps, so no chain
@@ -614,6 +615,11 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
         };
 #pragma unroll
         for (int t = 0; t < COV_RS - 1; ++t) issue_tile(t);
+        // k = 0 rows: sums of the shifted real parts per slot (a slot keeps its
+        // (row, image-in-tile) for the whole item)
+        float s0acc[COV_PF];
+#pragma unroll
+        for (int u = 0; u < COV_PF; ++u) s0acc[u] = 0.f;
         for (int t = 0; t < ntiles && *okflag; ++t, ++gt) {
             const int buf = (int)(gt & 1);
             uint8_t *B0 = sm + buf * BUF_BYTES;
@@ -638,6 +644,7 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
                 if (q < p0) {   // k = 0: shifted real part; images past the range stay zero
                     re = (!last || ib + (int64_t)t * COV_TI + ii < ie) ? re - S.shift[q] : 0.f;
                     im = 0.f;
+                    s0acc[u] += re;
                 }
                 const int kidx = 2 * ii;                 // K index of the real part
                 const int ch = kidx / KCH, e = kidx % KCH;
@@ -683,6 +690,15 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
             }
         }
         tc::cp_async_wait<0>();   // no copy of this item outstanding (an early exit leaves some)
+        if (p0 > 0) {   // sum_i (Re a_{i,0,q} - shift_q) into the float64 sums
+#pragma unroll
+            for (int u = 0; u < COV_PF; ++u) {
+                const int it = threadIdx.x + COV_NT * u;
+                if (it >= nslots) break;
+                const int pr = it >> 5, q = 8 * (pr & (QBP - 1)) + (it & 7);
+                if (q < p0) atomicAdd(&S.sum0[q], (double)s0acc[u]);
+            }
+        }
         __syncthreads();
         // the last commit covers every MMA issued before it
         if (ntiles > 0 && *okflag) {
@@ -746,21 +762,6 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
     if (warp == 0) tc::tmem_dealloc(tbase, 512u);
 }
 
-// k = 0 mean: sum0[q] += sum_i (Re a_{i,0,q} - shift_q), float64; grid
-// (image ranges, stacks)
-__global__ void k_cov_sum0(const __grid_constant__ CovGroup g, int64_t per0) {
-    const CovStack &S = g.st[blockIdx.y];
-    const int64_t ib = (int64_t)blockIdx.x * per0;
-    if (ib >= S.n) return;
-    const int64_t ie = min(S.n, ib + per0);
-    const int p0 = S.pk[0];
-    for (int q = threadIdx.x; q < p0; q += blockDim.x) {
-        double s = 0.0;
-        for (int64_t i = ib; i < ie; ++i) s += (double)(S.coef[i * S.P + q].x - S.shift[q]);
-        atomicAdd(&S.sum0[q], s);
-    }
-}
-
 // one CTA per SM, so the 512-column TMEM allocation never waits for another CTA
 static size_t tc_cov_smem(int prec) {
     const bool tf = (prec == FFB_TF32 || prec == FFB_TF32X3);
@@ -807,13 +808,7 @@ int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *sta
         case FFB_BF16X3: e = launch_tc_cov<1, 2>(g, grid, status, s); break;
         default: return FFB_ERR_ARG;
     }
-    if (e) return e;
-    const int64_t per0 = 2048;
-    int64_t nr = 1;
-    for (int i = 0; i < g.S; ++i) nr = max(nr, (g.st[i].n + per0 - 1) / per0);
-    if (nr > 65535 * 16) return FFB_ERR_ARG;
-    k_cov_sum0<<<dim3((unsigned)nr, (unsigned)g.S), 64, 0, s>>>(g, per0);
-    return ffb_check_cuda(cudaGetLastError());
+    return e;
 }
 
 int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t s) {
@@ -825,6 +820,6 @@ int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t
     g.nitems = (int64_t)g.st[0].nk * ((n + g.st[0].per - 1) / g.st[0].per);
     ProfScope ps(p, FFB_KC_COV, s);
     const int e = ffb_launch_cov_group_tc(p->precision, g, 0, p->d_status, s);
-    p->launches += 2;
+    p->launches += 1;
     return e;
 }
