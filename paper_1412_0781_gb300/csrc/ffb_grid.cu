@@ -34,7 +34,9 @@
 // (phase 3 is bound by the shared-memory pipe).  One 8-byte load of a half
 // warp takes a single wavefront when the 16 unit origins r0 * SLD + c0 fall in
 // distinct 8-byte bank slots (the origin mod 16) or coincide, so the units are
-// ordered into half warps with distinct slots.  Everything here depends on
+// ordered into half warps with distinct slots; a unit whose nodes share their
+// column origin (or a single node) may start its union one column to the
+// left, which the plan uses to even out the slots' unit counts.  Everything here depends on
 // the geometry alone and is built by the plan in float64
 // (ffb_fused_prepare): blocks of consecutive nodes t = j nl + l, at most
 // FUS_GU units each, and per unit the origin, both
@@ -271,13 +273,13 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     // block b of the half covers the nodes t in [t0, t0 + cnt);
     // unit record s holds, as FUS_REC planes of FUS_GU float4,
     //   0, 1  row weights of node A    2, 3  row weights of node B
-    //   4, 5  column weights of A (columns 0..7 of the union)
+    //   4, 5  column weights of A, columns 0..7 of the union; 8.w: column 8
     //   6, 7  column weights of B, columns 0..7; 8.x: column 8
     //   8.y   r0 | c0 << 16 (union origin in S)   8.z  slotA | slotB << 16
     // slots index the block's nodes (0xFFFF: none; node B of a single unit
     // carries zero weights).  Results are staged in the (now idle) warp
     // buffers, two blocks deep so that one barrier per block suffices.
-    static_assert(W == 8, "unit records hold 8 + 8 row and 8 + 9 column weights");
+    static_assert(W == 8, "unit records hold 8 + 8 row and 9 + 9 column weights");
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
     const int nl = (half == 0) ? nq0 : nh - nq0;
@@ -310,7 +312,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
                 if (lb < cnt) stage[lb] = make_float2(0.f, 0.f);
                 continue;
             }
-            const float wxa[8] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w};
+            const float wxa[9] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w, meta.w};
             const float wxb[9] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w, meta.x};
             // row by row: the 9 values of the union row, interpolated along
             // the row with each node's column weights, then weighted by the
@@ -330,10 +332,8 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 #pragma unroll
                     for (int q = 0; q <= W; ++q) {
                         const float2 g = row[q];
-                        if (q < W) {
-                            ra.x = fmaf(wxa[q], g.x, ra.x);
-                            ra.y = fmaf(wxa[q], g.y, ra.y);
-                        }
+                        ra.x = fmaf(wxa[q], g.x, ra.x);
+                        ra.y = fmaf(wxa[q], g.y, ra.y);
                         rb.x = fmaf(wxb[q], g.x, rb.x);
                         rb.y = fmaf(wxb[q], g.y, rb.y);
                     }
@@ -552,32 +552,67 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             rec.resize(base + (size_t)FUS_REC * GU, make_float4(0.f, 0.f, 0.f, 0.f));
             float4 *R = rec.data() + base;
             for (int sl = 0; sl < GU; ++sl) R[8 * GU + sl] = make_float4(0.f, 0.f, bits(0xFFFF | (0xFFFF << 16)), 0.f);
-            std::vector<int> bucket[16];
-            for (int u = (int)un.size() - 1; u >= 0; --u) {
+            // union origin of each unit: A's window origin, or one column to
+            // its left where both nodes' windows still fit (the same column
+            // origin, or a single node), chosen to even out the bank slots:
+            // the fixed units first, then each movable one into the emptier
+            // of its two slots
+            const int nu0 = (int)un.size();
+            std::vector<int> ucol(nu0);
+            int cnt16[16] = {};
+            std::vector<char> movable(nu0);
+            for (int u = 0; u < nu0; ++u) {
                 const Node &a = nd[t0 + un[u].first];
-                bucket[(a.r0 * SLD + a.c0) & 15].push_back(u);
+                movable[u] = (un[u].second < 0 || nd[t0 + un[u].second].c0 == a.c0) && a.c0 >= 1;
+                ucol[u] = a.c0;
+                if (!movable[u]) cnt16[(a.r0 * SLD + a.c0) & 15]++;
+            }
+            for (int u = 0; u < nu0; ++u) {
+                if (!movable[u]) continue;
+                const Node &a = nd[t0 + un[u].first];
+                const int s0 = (a.r0 * SLD + a.c0) & 15, s1 = (s0 + 15) & 15;
+                if (cnt16[s1] < cnt16[s0]) ucol[u] = a.c0 - 1;
+                cnt16[(a.r0 * SLD + ucol[u]) & 15]++;
+            }
+            std::vector<int> bucket[16];
+            for (int u = nu0 - 1; u >= 0; --u) {
+                const Node &a = nd[t0 + un[u].first];
+                bucket[(a.r0 * SLD + ucol[u]) & 15].push_back(u);
             }
             int pos = 0;
             auto put = [&](int u) {
                 const int ia = un[u].first, ib = un[u].second;
                 const Node &a = nd[t0 + ia];
-                float w[34] = {};   // row A, row B, column A (8), column B (9)
+                const int cu = ucol[u];
+                float w[36] = {};   // row A (8), row B (8), column A (9), column B (9)
                 for (int q = 0; q < W; ++q) {
                     w[q] = (float)phi(a.f2 - q);
-                    w[16 + q] = (float)phi(a.f1 - q);
+                    w[16 + (a.c0 - cu) + q] = (float)phi(a.f1 - q);
                 }
                 if (ib >= 0) {
                     const Node &bn = nd[t0 + ib];
-                    const int d = bn.c0 - a.c0;   // 0 or 1
+                    const int d = bn.c0 - cu;   // 0, 1
                     for (int q = 0; q < W; ++q) {
                         w[8 + q] = (float)phi(bn.f2 - q);
-                        w[24 + d + q] = (float)phi(bn.f1 - q);
+                        w[25 + d + q] = (float)phi(bn.f1 - q);
                     }
                 }
-                for (int f = 0; f < 8; ++f)
-                    R[f * GU + pos] = make_float4(w[4 * f], w[4 * f + 1], w[4 * f + 2], w[4 * f + 3]);
+                // fields: rows A, rows B, columns A 0..7, columns B 0..7,
+                // (column B 8, origin, slots, column A 8)
+                const float4 f0 = make_float4(w[0], w[1], w[2], w[3]), f1 = make_float4(w[4], w[5], w[6], w[7]);
+                const float4 f2 = make_float4(w[8], w[9], w[10], w[11]), f3 = make_float4(w[12], w[13], w[14], w[15]);
+                const float4 f4 = make_float4(w[16], w[17], w[18], w[19]), f5 = make_float4(w[20], w[21], w[22], w[23]);
+                const float4 f6 = make_float4(w[25], w[26], w[27], w[28]), f7 = make_float4(w[29], w[30], w[31], w[32]);
+                R[0 * GU + pos] = f0;
+                R[1 * GU + pos] = f1;
+                R[2 * GU + pos] = f2;
+                R[3 * GU + pos] = f3;
+                R[4 * GU + pos] = f4;
+                R[5 * GU + pos] = f5;
+                R[6 * GU + pos] = f6;
+                R[7 * GU + pos] = f7;
                 const int locs = ia | ((ib >= 0 ? ib : 0xFFFF) << 16);
-                R[8 * GU + pos] = make_float4(w[32], bits(a.r0 | (a.c0 << 16)), bits(locs), 0.f);
+                R[8 * GU + pos] = make_float4(w[33], bits(a.r0 | (cu << 16)), bits(locs), w[24]);
                 ++pos;
             };
             const int nu = (int)un.size();
