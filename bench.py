@@ -129,13 +129,13 @@ PROF_STRIDE = 32   # kernel timing: every 32nd launch of each kernel class
 # while the kernel's sources are byte-identical to the profiled ones (the
 # kernel's file and the register-FFT header; from ffb_internal.cuh it uses
 # only the complex arithmetic and the status flag).  ncu empties L2 before the
-# capture, so the figure includes one read of the plan's 2.6 MB node table,
+# capture, so the figure includes one read of the plan's 2.6 MB unit table,
 # which stays in L2 between launches in a live run.
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "adcb0df265a168cfe0a329b56ce0647fe8443f8bb76165fd9e22cd926113e538",
-                    "bytes_per_launch": 12653056 + 97536, "images_per_launch": 152},
+                    "sha256": "bbd27bb678656419b2e25f144df0d5aab023d5fc31395b590d141500da477561",
+                    "bytes_per_launch": 12654080 + 89856, "images_per_launch": 152},
 }
 
 
