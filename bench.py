@@ -37,6 +37,7 @@ def _args():
     ap.add_argument("--n", type=int, default=0, help="override images per GPU (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-post", action="store_true", help="skip the a8-a10 timings after the step")
     return ap.parse_args()
 
 
@@ -122,6 +123,17 @@ def algorithmic_flops(plan):
 
 
 PROF_STRIDE = 32   # kernel timing: every 32nd launch of each kernel class
+POST_N = 20000     # images for the a8-a10 timings after the step
+
+
+def hbm_floor():
+    """images/s if only the image in (L^2 float32) and the coefficients out
+    (P complex float32) crossed HBM, at the measured copy bandwidth."""
+    try:
+        gbs = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        gbs = 6800.0
+    return gbs * 1e9 / (128 * 128 * 4 + 4848 * 8)
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
@@ -252,7 +264,7 @@ def run_ours(args):
 
     spec = data.PRECISION_L128
     n = args.n or spec.n
-    images, _, _ = data.blob_stack(data.StackSpec(n, spec.L, spec.R, spec.n_blobs, spec.width, spec.snr,
+    images, _, sigma2 = data.blob_stack(data.StackSpec(n, spec.L, spec.R, spec.n_blobs, spec.width, spec.snr,
                                                   spec.seed + 7919 * rank), device=dev)
     if args.precision == "auto":
         precisions = ["fp32", "tf32x3", "bf16x3", "tf32", "bf16"]
@@ -329,6 +341,45 @@ def run_ours(args):
                 "kernel_ms_per_launch": dom_ms / dom_calls, "images_per_launch": imgs_per_launch,
                 "kernel_timing": "CUDA events around every %dth launch of each kernel in the timed region" % PROF_STRIDE,
                 "share": share}
+
+    # the whole step against its floor: the FP32-ALU work of a1-a4 at the
+    # FFMA peak (the tensor-core and HBM floors are far higher)
+    alu_flops = flops["grid_interp"] + flops["ring_fft"]
+    floor = peak * 1e12 / alu_flops
+    roofline["step"] = {"bound": "alu", "floor_images_per_s": floor, "frac": value / floor,
+                        "note": "a1-a4 FP32 work %.2f MFLOP/image at the FFMA peak; HBM floor %.1f M images/s" % (
+                            alu_flops / 1e6, hbm_floor() / 1e6)}
+
+    # a8-a10 after the timed step (reported beside the metric, not part of
+    # it): the eigendecomposition of the step's covariance, MP-Wiener
+    # denoising (a9 selection and filter, a10 synthesis through the adjoint,
+    # including the images' own expansion) and the adjoint alone, on the first
+    # POST_N images, each timed with CUDA events after one untimed run
+    post = None
+    if rank == 0 and not args.no_post:
+        m = min(n, POST_N)
+        sub = images[:m]
+
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        eig_ms = timed(lambda: plan.eig())
+        den = torch.empty_like(sub)
+        den_ms = timed(lambda: plan.denoise(sub, mode="mp_wiener", sigma2=sigma2, out=den))
+        adj = torch.empty_like(sub)
+        adj_ms = timed(lambda: plan.expand_adjoint(r["coef"][:m], out=adj))
+        post = {"a8_eig_ms": eig_ms, "eig_blocks": plan.k_max + 1,
+                "a9_a10_denoise_images_per_s": m / (den_ms / 1e3), "a10_adjoint_images_per_s": m / (adj_ms / 1e3),
+                "images": m, "mode": "mp_wiener (known noise variance)"}
+        del den, adj
 
     # end to end through the public API with host buffers
     e2e = None
@@ -420,7 +471,7 @@ def run_ours(args):
                 "precisions": {p: {"images_per_s": world * n / (v["ms"] / args.steps / 1e3),
                                    "kernel_ms": {c: round(t[0] / args.steps, 4) for c, t in v["prof"].items()}}
                                for p, v in results.items()},
-                "roofline": roofline, "stages": stages, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "stages": stages, "after_step": post, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": r["launches"],
                 "clocks": r["clocks"]}
         print(json.dumps(line))
