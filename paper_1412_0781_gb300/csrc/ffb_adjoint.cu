@@ -6,7 +6,9 @@
 //   a = B Fhat, Im a_0 := 0                 Yhat = B^T y, Im y_0 := 0
 //   Fhat_k = s DFT(ring)_k, k <= k_max,     g = inverse DFT of Yhat (zero-padded),
 //     ring = [F_l, conj F_l] (l < n/2)       G_l = s (g_l + conj g_{l+n/2})
-//   F_pt = sum psi psi Gext[tap]            Gext[tap] += psi psi G_pt (spreading)
+//   F_pt = sum psi psi Gext[tap]            Gext[tap] += psi psi G_pt (spreading; for
+//                                            the fused path's plans in shared memory
+//                                            per image half, ffb_grid.cu)
 //   Gext = halo copy of G (conj mirror)     G += conj(mirror of the halo rows)
 //   G[.][m2] = DFT over i1 of H[m2][.]      H[m2][a1] = inverse DFT over m1
 //   H[m2][a1] = DFT over i2 (real rows)     P'[a1][i2] = Re sum_{m2=0}^{N/2} H e^{+...}
@@ -158,6 +160,48 @@ k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, f
 }
 
 // ---------------------------------------------------------------------------
+// inverse ring DFT + fold only (fused-path plans, whose spreading runs in
+// ffb_grid.cu): Gpol[img][j][l] = s (g_l + conj g_{l + n/2}), l < n/2, the
+// layout of the forward's polar buffer.  grid (ceil(n_xi/ADJ_RB), nimg).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(ADJ_NT)
+k_adj_ring_polar(const float *__restrict__ Yhat, int n_xi, int n_theta, const float2 *__restrict__ twT,
+                 FftPlanDev fpT, int kmax, int chunk, float2 *__restrict__ Gpol) {
+    extern __shared__ float2 sm[];
+    float2 *ringA = sm;
+    float2 *ringB = sm + ADJ_RB * n_theta;
+    const int img = blockIdx.y;
+    const int j0 = blockIdx.x * ADJ_RB;
+    const int nh = n_theta / 2;
+    for (int t = threadIdx.x; t < ADJ_RB * n_theta; t += ADJ_NT) ringA[t] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int t = threadIdx.x; t < (kmax + 1) * 2 * ADJ_RB; t += ADJ_NT) {
+        const int jj = t % ADJ_RB, cc = (t / ADJ_RB) & 1, k = t / (2 * ADJ_RB);
+        const int j = j0 + jj;
+        if (j < n_xi) {
+            float v = __ldg(&Yhat[(((size_t)k * chunk + img) * 2 + cc) * n_xi + j]);
+            if (cc) ringA[jj * n_theta + k].y = v;
+            else ringA[jj * n_theta + k].x = v;
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int jj = warp; jj < ADJ_RB; jj += ADJ_NT / 32)
+        smem_fft<true>(ringA + jj * n_theta, ringB + jj * n_theta, fpT, twT, lane, 32, WarpSync());
+    __syncthreads();
+    const float2 *g = (fpT.nst & 1) ? ringB : ringA;
+    const float scale = 6.283185307179586f / (float)n_theta;
+    float2 *Gi = Gpol + (size_t)img * n_xi * nh;
+    for (int t = threadIdx.x; t < ADJ_RB * nh; t += ADJ_NT) {
+        const int jj = t / nh, l = t - jj * nh;
+        const int j = j0 + jj;
+        if (j >= n_xi) continue;
+        const float2 a = g[jj * n_theta + l], b = g[jj * n_theta + l + nh];
+        Gi[(size_t)j * nh + l] = make_float2(scale * (a.x + b.x), scale * (a.y - b.y));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // halo fold + inverse column DFT: for column m2 in [0, N/2],
 // Gc[m1] = Gext[m2+h][m1] (+ conj Gext[h-m2][-m1] if 1 <= m2 <= h)
 //                         (+ conj Gext[h+N-m2][-m1] if N/2-h <= m2 <= N/2-1);
@@ -273,6 +317,8 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
     const size_t sm_rows = sizeof(float2) * (size_t)AROW_WARPS * 2 * N;
     if ((e = set_smem((const void *)k_adj_bessel, sm_bes, &a_bes))) return e;
     if ((e = set_smem((const void *)k_adj_ring_spread, sm_ring, &a_ring))) return e;
+    static int a_ringp = 0;
+    if ((e = set_smem((const void *)k_adj_ring_polar, sm_ring, &a_ringp))) return e;
     if ((e = set_smem((const void *)k_adj_cols, sm_cols, &a_cols))) return e;
     if ((e = set_smem((const void *)k_adj_rows, sm_rows, &a_rows))) return e;
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
@@ -286,7 +332,17 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
         }
         e = ffb_check_cuda(cudaMemsetAsync(p->d_G, 0, sizeof(float2) * (size_t)m * p->Mh * N, s));
         if (e) return e;
-        {
+        if (p->fused) {
+            // inverse ring DFT to the polar buffer, then the half grids in
+            // shared memory with the forward's unit table
+            ProfScope ps(p, FFB_KC_ADJ_RING, s);
+            dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
+            k_adj_ring_polar<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max,
+                                                        p->chunk, p->d_Fpol);
+            p->launches++;
+            if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
+            if ((e = ffb_launch_fused_spread(p, p->d_Fpol, m, p->d_G, s))) return e;
+        } else {
             ProfScope ps(p, FFB_KC_ADJ_RING, s);
             dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
             k_adj_ring_spread<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,

@@ -300,7 +300,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
         for (int s = threadIdx.x; s < GU; s += FUS_NT) {
             const float4 meta = __ldg(&rec[8 * GU + s]);
             const int locs = __float_as_int(meta.z);
-            const int la = locs & 0xFFFF, lb = locs >> 16;
+            const int la = locs & 0xFFFF, lb = (int)((unsigned)locs >> 16);   // 0xFFFF: no node B
             if (la >= cnt) continue;
             const int rc = __float_as_int(meta.y);
             const int r0 = rc & 0xFFFF, c0 = rc >> 16;
@@ -396,6 +396,127 @@ static int fused_cluster_ok() {
         return 0;
     }
     return (2 * ncl >= sms) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of phase 3 (step a10): spreading.  One CTA per (image, half): the
+// half's polar values g (from the inverse ring DFT, layout of the polar
+// buffer) are spread into the half grid held in shared memory with the
+// forward's unit table, S[r0 + b][c0 + q] += wy_b wx_q g for both nodes of a
+// unit (shared-memory atomics; the unit order that keeps the forward's
+// gathers on distinct banks does the same for these adds), and the half grid
+// is then added into the extended grid Gext[m2 + h][m1 mod N] (global
+// atomics: both halves overlap near m1 = 0 and m1 = +-N/2).  Gext is zeroed
+// by the caller.  This is the transpose of phase 3 with the same weights, so
+// the adjoint stays exact against the forward.
+// ---------------------------------------------------------------------------
+template <int N, int W>
+__global__ void __launch_bounds__(FUS_NT, 1)
+k_adj_spread_half(const float2 *__restrict__ Gpol, int n_xi, int n_theta, int nq0,
+                  const float4 *__restrict__ units, const int2 *__restrict__ blocks, int nblk0, int nblk1,
+                  float2 *__restrict__ Gext, int *status) {
+    constexpr int H = (W + 1) / 2;
+    constexpr int MH = fus_mh(N, W);
+    constexpr int SLD = fus_sld(N, W);
+    constexpr int GN = FUS_WARPS * N / 2;
+    constexpr int GU = (FUS_GU < GN / 2) ? FUS_GU : GN / 2;
+    static_assert(W == 8, "unit records hold 8 + 8 row and 9 + 9 column weights");
+    extern __shared__ float2 smz[];
+    float *S = (float *)smz;                      // [MH][SLD] complex, as float pairs
+    const int half = blockIdx.x;
+    const int img = blockIdx.y;
+    for (int i = threadIdx.x; i < MH * SLD; i += FUS_NT) smz[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int nh = n_theta / 2;
+    const int lbeg = (half == 0) ? 0 : nq0;
+    const int nl = (half == 0) ? nq0 : nh - nq0;
+    const int nblk = (half == 0) ? nblk0 : nblk1;
+    const int gb0 = (half == 0) ? 0 : nblk0;
+    const float2 *Gp = Gpol + (size_t)img * n_xi * nh;
+    const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;   // t / nl, as in phase 3
+    for (int b = 0; b < nblk; ++b) {
+        const int2 tb = __ldg(&blocks[gb0 + b]);
+        const int t0 = tb.x, cnt = tb.y;
+        const float4 *rec = units + (size_t)(gb0 + b) * FUS_REC * GU;
+        for (int s = threadIdx.x; s < GU; s += FUS_NT) {
+            const float4 meta = __ldg(&rec[8 * GU + s]);
+            const int locs = __float_as_int(meta.z);
+            const int la = locs & 0xFFFF, lb = (int)((unsigned)locs >> 16);   // 0xFFFF: no node B
+            if (la >= cnt) continue;
+            const int rc = __float_as_int(meta.y);
+            const int r0 = rc & 0xFFFF, c0 = rc >> 16;
+            if (r0 + W > MH || c0 + W + 1 > SLD) {
+                ffb_flag(status, FFB_ERR_ARG);
+                continue;
+            }
+            const int ta = t0 + la;
+            const int ja = (int)__umulhi((unsigned)ta, nl_magic);
+            const float2 va = __ldg(&Gp[(size_t)ja * nh + lbeg + (ta - ja * nl)]);
+            float2 vb = make_float2(0.f, 0.f);
+            if (lb < cnt) {
+                const int tbn = t0 + lb;
+                const int jb = (int)__umulhi((unsigned)tbn, nl_magic);
+                vb = __ldg(&Gp[(size_t)jb * nh + lbeg + (tbn - jb * nl)]);
+            }
+            const float4 xa0 = __ldg(&rec[4 * GU + s]), xa1 = __ldg(&rec[5 * GU + s]);
+            const float4 xb0 = __ldg(&rec[6 * GU + s]), xb1 = __ldg(&rec[7 * GU + s]);
+            const float wxa[9] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w, meta.w};
+            const float wxb[9] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w, meta.x};
+            float *base = S + 2 * (r0 * SLD + c0);
+#pragma unroll
+            for (int h4 = 0; h4 < 2; ++h4) {
+                const float4 ya = __ldg(&rec[h4 * GU + s]), yb = __ldg(&rec[(2 + h4) * GU + s]);
+                const float wya[4] = {ya.x, ya.y, ya.z, ya.w};
+                const float wyb[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+                for (int b4 = 0; b4 < 4; ++b4) {
+                    const float2 ua = make_float2(wya[b4] * va.x, wya[b4] * va.y);
+                    const float2 ub = make_float2(wyb[b4] * vb.x, wyb[b4] * vb.y);
+                    float *row = base + 2 * (4 * h4 + b4) * SLD;
+#pragma unroll
+                    for (int q = 0; q <= W; ++q) {
+                        atomicAdd(&row[2 * q], fmaf(wxa[q], ua.x, wxb[q] * ub.x));
+                        atomicAdd(&row[2 * q + 1], fmaf(wxa[q], ua.y, wxb[q] * ub.y));
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // the half grid into Gext: row e is m2 = e - H (Gext's own offset), column
+    // c is m1 = c + m1lo
+    const int m1lo = (half == 0) ? -H : -(N / 2) - H;
+    float2 *Gi = Gext + (size_t)img * MH * N;
+    for (int i = threadIdx.x; i < MH * MH; i += FUS_NT) {
+        const int e = i / MH, c = i - e * MH;
+        const int col = (c + m1lo + N) & (N - 1);
+        atomicAdd(&Gi[(size_t)e * N + col], smz[e * SLD + c]);
+    }
+}
+
+int ffb_launch_fused_spread(ffb_plan_t p, const float2 *Gpol, int m, float2 *Gext, cudaStream_t s) {
+    if (p->N != 256 && p->N != 128) return FFB_ERR_UNSUPPORTED;
+    const int N = p->N;
+    const size_t smem = sizeof(float2) * (size_t)fus_mh(N, 8) * fus_sld(N, 8);
+    static int attr256 = 0, attr128 = 0;
+    int &done = (N == 256) ? attr256 : attr128;
+    const void *fn = (N == 256) ? (const void *)k_adj_spread_half<256, 8> : (const void *)k_adj_spread_half<128, 8>;
+    if (done < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (e) return e;
+        done = (int)smem;
+    }
+    dim3 g(2, m);
+    if (N == 256)
+        k_adj_spread_half<256, 8><<<g, FUS_NT, smem, s>>>(Gpol, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
+                                                           p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Gext,
+                                                           p->d_status);
+    else
+        k_adj_spread_half<128, 8><<<g, FUS_NT, smem, s>>>(Gpol, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
+                                                           p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Gext,
+                                                           p->d_status);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
 }
 
 // pdl: launched with programmatic serialization (the previous kernel in the
@@ -551,7 +672,7 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             const size_t base = rec.size();
             rec.resize(base + (size_t)FUS_REC * GU, make_float4(0.f, 0.f, 0.f, 0.f));
             float4 *R = rec.data() + base;
-            for (int sl = 0; sl < GU; ++sl) R[8 * GU + sl] = make_float4(0.f, 0.f, bits(0xFFFF | (0xFFFF << 16)), 0.f);
+            for (int sl = 0; sl < GU; ++sl) R[8 * GU + sl] = make_float4(0.f, 0.f, bits((int)0xFFFFFFFFu), 0.f);
             // union origin of each unit: A's window origin, or one column to
             // its left where both nodes' windows still fit (the same column
             // origin, or a single node), chosen to even out the bank slots:
@@ -611,8 +732,10 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
                 R[5 * GU + pos] = f5;
                 R[6 * GU + pos] = f6;
                 R[7 * GU + pos] = f7;
-                const int locs = ia | ((ib >= 0 ? ib : 0xFFFF) << 16);
-                R[8 * GU + pos] = make_float4(w[33], bits(a.r0 | (cu << 16)), bits(locs), w[24]);
+                // slots as unsigned halves (0xFFFF: no node B); the kernels
+                // decode them with logical shifts
+                const unsigned locs = (unsigned)ia | ((unsigned)(ib >= 0 ? ib : 0xFFFF) << 16);
+                R[8 * GU + pos] = make_float4(w[33], bits(a.r0 | (cu << 16)), bits((int)locs), w[24]);
                 ++pos;
             };
             const int nu = (int)un.size();

@@ -330,6 +330,9 @@ bool ffb_fused_supported(ffb_plan_t plan);
 int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_fused_mode(ffb_plan_t plan);   // 1 plain, 2 cluster variant of the fused kernel
 int ffb_ring_prepare(ffb_plan_t plan, cudaStream_t s);   // ring FFT twiddle table (fused path)
+// adjoint spreading of m images' half-ring values (polar-buffer layout) into
+// the zeroed extended grid [m][Mh][N] with the fused path's unit table
+int ffb_launch_fused_spread(ffb_plan_t plan, const float2 *Gpol, int m, float2 *Gext, cudaStream_t s);
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
                            cudaStream_t s, bool pdl = false);
 struct RingOut {

@@ -63,11 +63,14 @@ def test_adjoint_dot_product(dev, L, n):
 
 
 # --- adjoint / synthesis vs oracle -------------------------------------------
-@pytest.mark.parametrize("L", [32, 64])
+@pytest.mark.parametrize("L", [32, 64, 128])
 def test_adjoint_matches_oracle(dev, L):
+    """L = 64 and 128 run the shared-memory spreading of the fused path's
+    plans (unit table, two CTAs per image); L = 32 the global one."""
     gp, op = gplan(L), fb.make_plan(L, 0.5, L / 2)
     rng = np.random.default_rng(L)
-    y = rng.standard_normal((4, gp.P)) + 1j * rng.standard_normal((4, gp.P))
+    m = 2 if L >= 128 else 4
+    y = rng.standard_normal((m, gp.P)) + 1j * rng.standard_normal((m, gp.P))
     y = y.astype(np.complex64).astype(np.complex128)
     g = gp.expand_adjoint(from_np_complex(y, dev)).double().cpu().numpy()
     assert rel(g, fb.adjoint(op, y)) <= TOL
