@@ -257,7 +257,8 @@ int ffb_profile(ffb_plan_t plan, int enable);
  * 3 radial quadrature, 4 covariance, 5 covariance shift/finalise, 6 Jacobi,
  * 7 transposed quadrature, 8 inverse ring DFT + spreading, 9 inverse column
  * FFT, 10 inverse row FFT + deconvolution, 11 steerable filter, 12 setup,
- * 13 shared-memory grid + interpolation, 14 ring FFT from the polar buffer.
+ * 13 shared-memory grid + interpolation, 14 ring FFT from the polar buffer,
+ * 15 adjoint spreading in shared memory.
  * Synchronises on the recorded events. */
 int ffb_profile_read(ffb_plan_t plan, double *h_ms, int64_t *h_calls);
 

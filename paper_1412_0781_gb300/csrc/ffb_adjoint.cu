@@ -335,12 +335,14 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
         if (p->fused) {
             // inverse ring DFT to the polar buffer, then the half grids in
             // shared memory with the forward's unit table
-            ProfScope ps(p, FFB_KC_ADJ_RING, s);
-            dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
-            k_adj_ring_polar<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max,
-                                                        p->chunk, p->d_Fpol);
-            p->launches++;
-            if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
+            {
+                ProfScope ps(p, FFB_KC_ADJ_RING, s);
+                dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
+                k_adj_ring_polar<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT, p->fftT,
+                                                            p->k_max, p->chunk, p->d_Fpol);
+                p->launches++;
+                if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
+            }
             if ((e = ffb_launch_fused_spread(p, p->d_Fpol, m, p->d_G, s))) return e;
         } else {
             ProfScope ps(p, FFB_KC_ADJ_RING, s);

@@ -507,6 +507,7 @@ int ffb_launch_fused_spread(ffb_plan_t p, const float2 *Gpol, int m, float2 *Gex
         done = (int)smem;
     }
     dim3 g(2, m);
+    ProfScope ps(p, FFB_KC_ADJ_SPREAD, s);
     if (N == 256)
         k_adj_spread_half<256, 8><<<g, FUS_NT, smem, s>>>(Gpol, p->n_xi, p->n_theta, p->nq0, p->d_nodes,
                                                            p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Gext,

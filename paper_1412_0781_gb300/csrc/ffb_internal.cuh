@@ -23,7 +23,7 @@ struct FftPlanDev {
 enum { FFB_KC_ROWS = 0, FFB_KC_COLS = 1, FFB_KC_INTERP = 2, FFB_KC_BESSEL = 3, FFB_KC_COV = 4,
        FFB_KC_COVAUX = 5, FFB_KC_EIG = 6, FFB_KC_ADJ_BESSEL = 7, FFB_KC_ADJ_RING = 8,
        FFB_KC_ADJ_COLS = 9, FFB_KC_ADJ_ROWS = 10, FFB_KC_FILTER = 11, FFB_KC_SETUP = 12,
-       FFB_KC_GRID_INTERP = 13, FFB_KC_RING_FFT = 14, FFB_NKC = 16 };
+       FFB_KC_GRID_INTERP = 13, FFB_KC_RING_FFT = 14, FFB_KC_ADJ_SPREAD = 15, FFB_NKC = 16 };
 
 struct ProfEv {
     cudaEvent_t a, b;

@@ -181,7 +181,7 @@ class Plan:
 
     KERNEL_CLASSES = ["rows_fft", "cols_fft", "interp_ring", "bessel", "covariance", "cov_aux", "jacobi",
                       "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup",
-                      "grid_interp", "ring_fft"]
+                      "grid_interp", "ring_fft", "adj_spread"]
 
     def profile(self, enable=True, stride=1):
         """Time every ``stride``-th launch of each kernel class (off if not enable)."""
