@@ -146,8 +146,8 @@ def hbm_floor():
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "bbd27bb678656419b2e25f144df0d5aab023d5fc31395b590d141500da477561",
-                    "bytes_per_launch": 12654080 + 89856, "images_per_launch": 152},
+                    "sha256": "ba306058583a5f770fbd2ef4311bc0cbac80acac2f91ccf9380d1fb050972b43",
+                    "bytes_per_launch": 12652800 + 90112, "images_per_launch": 152},
 }
 
 
