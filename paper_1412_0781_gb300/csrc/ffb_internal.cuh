@@ -46,7 +46,7 @@ struct ffb_plan_s {
     FftPlanDev fftN, fftT;
     int chunk;           // images per internal chunk
     int nq0;             // half-ring angles with cos(theta) >= 0 (fused path split)
-    int fused;           // 1: grid held in shared memory (ffb_fused.cu); 2: as 1, in CTA-pair clusters
+    int fused;           // 1: grid held in shared memory (ffb_grid.cu); 2: as 1, in CTA-pair clusters
     // device tables (float64 setup results)
     double *d_zeros = nullptr;   // [P]
     double *d_xi = nullptr;      // [n_xi]

@@ -1,16 +1,20 @@
-// ffb_tc.cu -- step a5 (radial quadrature, Eq. a) on the tcgen05 tensor cores.
+// ffb_tc.cu -- steps a5 (radial quadrature, Eq. a) and a6/a7 (covariance,
+// Eqs. ck, ck_0) on the tcgen05 tensor cores.
 //
-// For every k, D^(k) = A^(k) B^(k)T with A^(k) the (2 chunk) x n_xi ring
-// spectra (rows = (image, re/im), contiguous per k) and B^(k) the p_k x n_xi
-// radial table; both operands are K-major.  One CTA owns an M tile of 128 rows
-// and one k:
-//   * TMA (cp.async.bulk.tensor, 128-byte swizzle) brings all K of the A planes
-//     and B planes into shared memory behind one mbarrier;
-//   * one thread issues tcgen05.mma (M = 128, N = p_k rounded up to 16,
-//     K = 8 (tf32) or 16 (bf16) per instruction) accumulating in TMEM, then
-//     tcgen05.commit arrives on a second mbarrier;
-//   * four warps read the 128 x N float32 accumulator with tcgen05.ld and write
-//     the coefficients a_{k,q} (re/im rows) to the interleaved output.
+// Quadrature: for every k, D^(k) = A^(k) B^(k)T with A^(k) the ring spectra of
+// a group of chunks (rows = (image, re/im), contiguous per k; the ring FFT
+// writes them as operand planes) and B^(k) the p_k x n_xi radial table; both
+// operands K-major.  A persistent, warp-specialised CTA walks the (k, M tile
+// of 128 rows) items:
+//   * warp 0 streams the 128-byte K chunks of A and B (hi/lo planes) by TMA
+//     (cp.async.bulk.tensor, 128-byte swizzle) through a ring of stages with
+//     full/empty mbarriers;
+//   * warp 1 allocates TMEM and one thread issues tcgen05.mma (M = 128,
+//     N = p_k rounded up to 16, K = 8 (tf32) or 16 (bf16) per instruction)
+//     into one of two alternating accumulators;
+//   * eight epilogue warps read an accumulator with tcgen05.ld, release it and
+//     write the coefficients a_{k,q} (re/im rows) to the interleaved output.
+// Covariance: see the section below (super-blocks of consecutive k).
 //
 // Precisions (hi/lo splitting, Markidis et al. 2018; Ootomo & Yokota 2022):
 //   TF32    A (float32, truncated by the tensor core) x B_hi
