@@ -24,15 +24,16 @@
 // Every wait is bounded by a clock budget; a timeout latches FFB_ERR_TIMEOUT,
 // waits (bounded) for in-flight copies, frees TMEM and returns.
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
 #include <algorithm>
+
+#include "ffb_internal.cuh"
 
 // operand planes of one quadrature group: 4 BF16x3 chunks at L = 128 (114 MB;
 // measured 1.7 % faster per step than 2 chunks in 64 MiB, though the planes
 // and the polar buffer then exceed L2)
 #define FFB_PLANE_BUDGET_MB 128
-#include <cuda_bf16.h>
-
-#include "ffb_internal.cuh"
 #include "ffb_tc.cuh"
 
 #define TC_BUDGET (4000000000LL)  // ~2 s at 2 GHz
