@@ -29,12 +29,12 @@
 #include <algorithm>
 
 #include "ffb_internal.cuh"
+#include "ffb_tc.cuh"
 
 // operand planes of one quadrature group: 4 BF16x3 chunks at L = 128 (114 MB;
 // measured 1.7 % faster per step than 2 chunks in 64 MiB, though the planes
 // and the polar buffer then exceed L2)
 #define FFB_PLANE_BUDGET_MB 128
-#include "ffb_tc.cuh"
 
 #define TC_BUDGET (4000000000LL)  // ~2 s at 2 GHz
 
