@@ -134,61 +134,80 @@ k_cov_fp32(const __grid_constant__ CovGroup g) {
         const int P = S.P;
         const float *shift = S.shift;
         const bool do_sum = (k == 0 && q0 == q1);  // diagonal tiles of block 0 carry the mean
-        float accf[4][4];
-        double accd[4][4];
+        const bool diag = (q0 == q1);              // X_b = X_a: staged once
+        float accf[4][4], hi[4][4], lo[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                accf[r][c] = 0.f;
-                accd[r][c] = 0.0;
-            }
+            for (int c = 0; c < 4; ++c) accf[r][c] = hi[r][c] = lo[r][c] = 0.f;
         float sf = 0.f;
         double sd = 0.0;
         int tiles = 0;
-        for (int64_t i = ib; i < ie; i += COV_TI) {
-            __syncthreads();
-            for (int t = threadIdx.x; t < COV_TI * 64; t += 256) {
-                int ii = t >> 6, qq = t & 63;
-                int64_t img = i + ii;
+        // the next tile's values are fetched into registers while this tile's
+        // products run: thread t stages entries e = t + 256 u of the 32 x 64
+        // block (image e / 64, column e % 64)
+        float2 pa[COV_TI * 64 / 256], pb[COV_TI * 64 / 256];
+        auto fetch = [&](int64_t i) {
+#pragma unroll
+            for (int u = 0; u < COV_TI * 64 / 256; ++u) {
+                const int e = threadIdx.x + 256 * u, ii = e >> 6, qq = e & 63;
+                const int64_t img = i + ii;
                 float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
                 if (img < ie) {
                     if (q0 + qq < pk) va = __ldg(&coef[img * P + o + q0 + qq]);
-                    if (q1 + qq < pk) vb = __ldg(&coef[img * P + o + q1 + qq]);
-                    if (k == 0) {
-                        va = make_float2(q0 + qq < pk ? va.x - shift[q0 + qq] : 0.f, 0.f);
-                        vb = make_float2(q1 + qq < pk ? vb.x - shift[q1 + qq] : 0.f, 0.f);
-                    }
+                    if (!diag && q1 + qq < pk) vb = __ldg(&coef[img * P + o + q1 + qq]);
+                }
+                pa[u] = va;
+                pb[u] = vb;
+            }
+        };
+        if (ib < ie) fetch(ib);
+        for (int64_t i = ib; i < ie; i += COV_TI) {
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < COV_TI * 64 / 256; ++u) {
+                const int e = threadIdx.x + 256 * u, ii = e >> 6, qq = e & 63;
+                float2 va = pa[u], vb = pb[u];
+                if (k == 0 && i + ii < ie) {
+                    va = make_float2(q0 + qq < pk ? va.x - shift[q0 + qq] : 0.f, 0.f);
+                    vb = make_float2(q1 + qq < pk && !diag ? vb.x - shift[q1 + qq] : 0.f, 0.f);
                 }
                 Xa[ii][qq] = va;
-                Xb[ii][qq] = vb;
+                if (!diag) Xb[ii][qq] = vb;
             }
             __syncthreads();
+            if (i + COV_TI < ie) fetch(i + COV_TI);
+            const float2(*Xs)[64] = diag ? Xa : Xb;
             if (16 * (warp & 3) < pk - q0 && 32 * (warp >> 2) < pk - q1) {
 #pragma unroll 4
                 for (int ii = 0; ii < COV_TI; ++ii) {
-                    float2 a[4], b[4];
+                    float2 a[4], bq[4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) a[r] = Xa[ii][r0w + r];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) b[c] = Xb[ii][c0w + c];
+                    for (int c = 0; c < 4; ++c) bq[c] = Xs[ii][c0w + c];
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
-                            accf[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, accf[r][c]));
+                            accf[r][c] = fmaf(a[r].x, bq[c].x, fmaf(a[r].y, bq[c].y, accf[r][c]));
                 }
             }
             if (do_sum && threadIdx.x < 64) {
                 for (int ii = 0; ii < COV_TI; ++ii) sf += Xa[ii][threadIdx.x].x;
             }
             if (++tiles == 4) {
+                // fold the 128-image partials into a compensated float32 sum
+                // (TwoSum; float64 arithmetic runs at a small fraction of the
+                // float32 rate on this GPU)
                 tiles = 0;
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        accd[r][c] += (double)accf[r][c];
+                        const float x = accf[r][c], s2 = hi[r][c] + x, bp = s2 - hi[r][c];
+                        lo[r][c] += (hi[r][c] - (s2 - bp)) + (x - bp);
+                        hi[r][c] = s2;
                         accf[r][c] = 0.f;
                     }
                 sd += (double)sf;
@@ -202,7 +221,7 @@ k_cov_fp32(const __grid_constant__ CovGroup g) {
             for (int c = 0; c < 4; ++c) {
                 const int qa = q0 + r0w + r, qb = q1 + c0w + c;
                 if (qa < pk && qb < pk) {
-                    double v = accd[r][c] + (double)accf[r][c];
+                    const double v = (double)hi[r][c] + (double)lo[r][c] + (double)accf[r][c];
                     atomicAdd(&blk[(size_t)qa * pk + qb], v);
                     if (q0 != q1) atomicAdd(&blk[(size_t)qb * pk + qa], v);
                 }
