@@ -8,79 +8,71 @@
 // ---------------------------------------------------------------------------
 // a5, FP32: one CTA per (k, 32 images).  Rows of the A operand are the 64
 // (image, re/im) rows of Fhat[k] (contiguous in memory), columns of B are
-// the p_k rows of B^(k); K = n_xi.  Each thread owns 2 images x 4 q.
+// the p_k rows of B^(k) in tiles of 64; K = n_xi.  Both tiles are stored
+// transposed in shared memory (K-major: At[j][row], Bt[j][q]) so that a
+// thread reads its 4 rows and 4 columns with two 16-byte loads per j.
+// Thread (ty = t % 16, tx = t / 16): rows 4 ty .., columns 4 tx ..; a warp
+// spans 8 columns, so warps whose columns lie past p_k skip the products.
 // ---------------------------------------------------------------------------
 #define BES_IMG 32
-// NC: 16-column groups of q computed per 64-column tile (ceil(p_k / 16),
-// at most 4), so that blocks with small p_k skip the padding columns
-template <int NC>
-__device__ __forceinline__ void bessel_fp32_tile(const float *As, const float *Bs, int ld, int n_xi, int tx, int ty,
-                                                 float (&acc)[4][4]) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-    for (int j = 0; j < n_xi; ++j) {
-        float a[4], b[NC];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = As[(ty * 4 + r) * ld + j];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) b[c] = Bs[(tx + 16 * c) * ld + j];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-}
+#define BES_TP 68    // row pitch of the transposed tiles (floats): 64 + 4, 16-byte aligned
+
+static size_t bessel_fp32_smem(int n_xi) { return sizeof(float) * (size_t)n_xi * 2 * BES_TP; }
 
 __global__ void __launch_bounds__(256)
 k_bessel_fp32(const float *__restrict__ Fhat, const float *__restrict__ Bf, const int *__restrict__ pk_,
               const int *__restrict__ off_, int n_xi, int chunk, int nimg, int P, float2 *__restrict__ coef) {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
+    float *At = (float *)sm4;                    // [n_xi][BES_TP]
+    float *Bt = At + (size_t)n_xi * BES_TP;      // [n_xi][BES_TP]
     const int k = blockIdx.y;
     const int pk = pk_[k], o = off_[k];
     const int i0 = blockIdx.x * BES_IMG;
-    const int ld = n_xi + 1;
-    float *As = sm;                  // [64][ld]
-    float *Bs = sm + 64 * ld;        // [64][ld]
     const float *Ak = Fhat + ((size_t)k * chunk + i0) * 2 * n_xi;
     const int rows = min(BES_IMG, nimg - i0) * 2;
-    for (int t = threadIdx.x; t < 64 * n_xi; t += 256) {
-        int r = t / n_xi, j = t - r * n_xi;
-        As[r * ld + j] = (r < rows) ? __ldg(&Ak[(size_t)r * n_xi + j]) : 0.f;
+    for (int e = threadIdx.x; e < 2 * BES_IMG * n_xi; e += 256) {
+        const int r = e / n_xi, j = e - r * n_xi;
+        At[j * BES_TP + r] = (r < rows) ? __ldg(&Ak[(size_t)r * n_xi + j]) : 0.f;
     }
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty: image pair, tx: q lane
+    const int ty = threadIdx.x & 15, tx = threadIdx.x >> 4;
     for (int q0 = 0; q0 < pk; q0 += 64) {
         __syncthreads();
-        for (int t = threadIdx.x; t < 64 * n_xi; t += 256) {
-            int q = t / n_xi, j = t - q * n_xi;
-            Bs[q * ld + j] = (q0 + q < pk) ? __ldg(&Bf[(size_t)(o + q0 + q) * n_xi + j]) : 0.f;
+        for (int e = threadIdx.x; e < 64 * n_xi; e += 256) {
+            const int q = e / n_xi, j = e - q * n_xi;
+            Bt[j * BES_TP + q] = (q0 + q < pk) ? __ldg(&Bf[(size_t)(o + q0 + q) * n_xi + j]) : 0.f;
         }
         __syncthreads();
+        if (8 * (threadIdx.x >> 5) >= pk - q0) continue;   // the warp's 8 columns are padding
         float acc[4][4];
-        const int nc = min(4, (pk - q0 + 15) >> 4);   // uniform over the CTA
-        if (nc == 1) bessel_fp32_tile<1>(As, Bs, ld, n_xi, tx, ty, acc);
-        else if (nc == 2) bessel_fp32_tile<2>(As, Bs, ld, n_xi, tx, ty, acc);
-        else if (nc == 3) bessel_fp32_tile<3>(As, Bs, ld, n_xi, tx, ty, acc);
-        else bessel_fp32_tile<4>(As, Bs, ld, n_xi, tx, ty, acc);
 #pragma unroll
-        for (int ii = 0; ii < 2; ++ii) {
-            const int img = i0 + ty * 2 + ii;
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < n_xi; ++j) {
+            const float4 a = *(const float4 *)&At[j * BES_TP + 4 * ty];
+            const float4 b = *(const float4 *)&Bt[j * BES_TP + 4 * tx];
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {             // rows 4 ty + 2 ii (re), + 1 (im)
+            const int img = i0 + 2 * ty + ii;
             if (img >= nimg) continue;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int q = q0 + tx + 16 * c;
-                if (q < pk) {
-                    float2 v = make_float2(acc[2 * ii][c], (k == 0) ? 0.f : acc[2 * ii + 1][c]);
-                    coef[(size_t)img * P + o + q] = v;
-                }
+                const int q = q0 + 4 * tx + c;
+                if (q < pk) coef[(size_t)img * P + o + q] = make_float2(acc[2 * ii][c], (k == 0) ? 0.f : acc[2 * ii + 1][c]);
             }
         }
     }
 }
 
 int ffb_launch_bessel_fp32(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    size_t smem = sizeof(float) * 2 * 64 * (size_t)(p->n_xi + 1);
+    const size_t smem = bessel_fp32_smem(p->n_xi);
     static int attr = 0;
     if (smem > 48 * 1024 && attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_bessel_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
