@@ -285,6 +285,26 @@ def test_launch_count_grows(dev):
     assert gp.launch_count() >= before + 4
 
 
+def test_profile_stride_counts_every_launch(dev):
+    """Sampled kernel timing: with a stride s only every s-th launch of a
+    class is bracketed by events, but the launch count is complete and the
+    class total is the sampled mean times that count."""
+    gp = gplan(64)
+    imgs = torch.zeros((5 * gp.chunk + 3, 64, 64), device=dev)
+    gp.expand(imgs)
+    torch.cuda.synchronize()
+    for stride in (1, 4):
+        gp.profile(True, stride=stride)
+        gp.expand(imgs)
+        torch.cuda.synchronize()
+        prof = gp.profile_read()
+        gp.profile(False)
+        ms, calls = prof["grid_interp"]
+        assert calls == 6 and ms > 0.0
+    with pytest.raises(FFBError):
+        gp.profile(True, stride=-1)
+
+
 def test_cov_export_merge_import_roundtrip(dev):
     """Statistics of two disjoint halves pooled with ffb_cov_merge equal the
     statistics of the whole stack; importing them reproduces its eigenpairs."""
