@@ -376,9 +376,38 @@ def run_ours(args):
         den_ms = timed(lambda: plan.denoise(sub, mode="mp_wiener", sigma2=sigma2, out=den))
         adj = torch.empty_like(sub)
         adj_ms = timed(lambda: plan.expand_adjoint(r["coef"][:m], out=adj))
+        # the rows beyond the hot path: radial eigenfunctions and the top-20
+        # eigenimages, the SVD route and the rotation-invariant features on
+        # the first m coefficients (with the HBM share of their coefficient
+        # reads), R and c from the first m images
+        ev, _ = plan.eig()
+        evn = ev.cpu().numpy()
+        offs = list(plan.offset) + [plan.P]
+        top = sorted(range(plan.P), key=lambda t: -evn[t])[:20]
+        pairs = []
+        for t in top:
+            k = max(i for i in range(plan.k_max + 1) if offs[i] <= t)
+            pairs.append((k, t - offs[k]))
+        f1_rad_ms = timed(lambda: plan.radial_eigenfunctions())
+        f1_img_ms = timed(lambda: plan.eigenimages(pairs))
+        coef_m = r["coef"][:m]
+        coef_bytes = m * plan.P * 8
+        f2_svd_ms = timed(lambda: plan.svd(coef_m))
+        inv_pairs = pairs[:10]
+        triples = [(1, 0, 1, 0, 0), (1, 0, 2, 0, 0), (2, 0, 1, 0, 0), (1, 0, 0, 0, 0)]
+        f2_inv_ms = timed(lambda: plan.invariants(coef_m, inv_pairs, triples))
+        f3_est_ms = timed(lambda: plan.estimate_support(sub), reps=1)
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
         post = {"a8_eig_ms": eig_ms, "eig_blocks": plan.k_max + 1,
                 "a9_a10_denoise_images_per_s": m / (den_ms / 1e3), "a10_adjoint_images_per_s": m / (adj_ms / 1e3),
-                "images": m, "mode": "mp_wiener (known noise variance)"}
+                "images": m, "mode": "mp_wiener (known noise variance)",
+                "next1_radial_eigenfunctions_ms": f1_rad_ms, "next1_eigenimages_20_ms": f1_img_ms,
+                "next2_svd_route_ms": f2_svd_ms,
+                "next2_svd_coef_read_frac_hbm": coef_bytes / (f2_svd_ms / 1e3) / (hbm * 1e9),
+                "next2_invariants_images_per_s": m / (f2_inv_ms / 1e3),
+                "next2_invariants_coef_read_frac_hbm": coef_bytes / (f2_inv_ms / 1e3) / (hbm * 1e9),
+                "next3_estimate_support_images_per_s": m / (f3_est_ms / 1e3)}
         del den, adj
 
     # end to end through the public API with host buffers
