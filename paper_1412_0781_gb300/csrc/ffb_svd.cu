@@ -150,13 +150,24 @@ k_tsqr_merge(const float *__restrict__ Rin, int nranges, const int *__restrict__
     }
 }
 
-// k = 0 mean of Re a_{i,0,q} in float64 (one thread per q)
-__global__ void k_mean0(const float2 *__restrict__ coef, int64_t n, int P, int p0, double *__restrict__ mean) {
+// k = 0 mean of Re a_{i,0,q} in float64: block b sums the images
+// [512 b, 512 b + 512) (thread: row q = t % 64, every fourth image from
+// t / 64) into sum[q] by atomics; k_mean0_final divides by n
+#define MEAN0_PER 512
+__global__ void __launch_bounds__(256) k_mean0(const float2 *__restrict__ coef, int64_t n, int P, int p0,
+                                               double *__restrict__ sum) {
+    const int q = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int64_t i0 = (int64_t)blockIdx.x * MEAN0_PER;
+    const int64_t i1 = min(n, i0 + MEAN0_PER);
+    for (int qq = q; qq < p0; qq += 64) {
+        double s = 0.0;
+        for (int64_t i = i0 + grp; i < i1; i += 4) s += (double)coef[i * P + qq].x;
+        atomicAdd(&sum[qq], s);
+    }
+}
+__global__ void k_mean0_final(int p0, double n, double *__restrict__ mean) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= p0) return;
-    double s = 0.0;
-    for (int64_t i = 0; i < n; ++i) s += (double)coef[i * P + q].x;
-    mean[q] = s / (double)n;
+    if (q < p0) mean[q] /= n;
 }
 
 extern "C" int ffb_svd(ffb_plan_t p, const float *d_coef, int64_t n, double *d_evals, double *d_evecs, void *stream) {
@@ -166,8 +177,10 @@ extern "C" int ffb_svd(ffb_plan_t p, const float *d_coef, int64_t n, double *d_e
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // ranges per k: about four CTAs per SM over all k, at least 2 p_max rows each
-    int64_t nr = (4LL * sms + p->k_max) / (p->k_max + 1);
+    // ranges per k: about sixteen CTAs per SM over all k (each CTA's QR steps
+    // run one after another, so shorter ranges shorten the chain), at least
+    // 2 p_max rows each
+    int64_t nr = (16LL * sms + p->k_max) / (p->k_max + 1);
     nr = std::max<int64_t>(1, std::min<int64_t>(nr, (2 * n) / (2 * p->pmax) + 1));
     const int64_t per0 = (2 * n + nr - 1) / nr;
     const size_t smem = sizeof(float) * (size_t)p->pmax * (TSQR_MB + 1);
@@ -185,13 +198,16 @@ extern "C" int ffb_svd(ffb_plan_t p, const float *d_coef, int64_t n, double *d_e
     if (e) return e;
     {
         ProfScope ps(p, FFB_KC_EIG, s);
-        k_mean0<<<(p->p[0] + 63) / 64, 64, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0], p->d_mean);
+        cudaMemsetAsync(p->d_mean, 0, sizeof(double) * p->p[0], s);
+        k_mean0<<<(unsigned)((n + MEAN0_PER - 1) / MEAN0_PER), 256, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0],
+                                                                        p->d_mean);
+        k_mean0_final<<<(p->p[0] + 63) / 64, 64, 0, s>>>(p->p[0], (double)n, p->d_mean);
         // k = 0 has n rows, k > 0 have 2n: the k = 0 ranges use half the length
         k_tsqr<<<dim3((unsigned)nr, p->k_max + 1), TSQR_THREADS, smem, s>>>(
             (const float2 *)d_coef, n, p->P, p->d_p, p->d_off, p->d_mean, per0, p->pmax, R);
         k_tsqr_merge<<<p->k_max + 1, TSQR_THREADS, smem, s>>>(R, (int)nr, p->d_p, p->d_cov_off, p->pmax, (double)n,
                                                                p->d_Cfin);
-        p->launches += 3;
+        p->launches += 4;
         e = ffb_check_cuda(cudaGetLastError());
     }
     cudaFreeAsync(R, s);
