@@ -485,6 +485,18 @@ def run_ours(args):
         else:
             stages[c] = {"bound": "alu", "achieved": rate, "peak": peak, "unit": "TFLOP/s", "frac": rate / peak,
                          "ms_per_step": ms_c / args.steps}
+            if c == "grid_interp" and plan.polar_variant > 0:
+                # what actually bounds it: the L1 / shared-memory pipe.  Per
+                # polar node, algorithmically: 36 complex grid gathers (one
+                # 8 x 9 window per node pair) and half a 144-byte unit record
+                pts = plan.n_xi * (plan.n_theta // 2)
+                l1_bytes = pts * (36 * 8 + 72)
+                l1_rate = l1_bytes * n * args.steps / (ms_c / 1e3) / 1e12
+                l1_peak = 152 * 128 * 2.070e9 / 1e12
+                stages[c]["l1"] = {"achieved": l1_rate, "peak": l1_peak, "unit": "TB/s", "frac": l1_rate / l1_peak,
+                                   "bytes_per_image": l1_bytes,
+                                   "note": "interpolation gathers + unit records through L1 / shared memory; peak "
+                                           "152 SMs x 128 B/clk x 2070 MHz (derived); the FFT phases add more"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
