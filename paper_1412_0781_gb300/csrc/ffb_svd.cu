@@ -198,7 +198,7 @@ extern "C" int ffb_svd(ffb_plan_t p, const float *d_coef, int64_t n, double *d_e
     if (e) return e;
     {
         ProfScope ps(p, FFB_KC_EIG, s);
-        cudaMemsetAsync(p->d_mean, 0, sizeof(double) * p->p[0], s);
+        e = ffb_check_cuda(cudaMemsetAsync(p->d_mean, 0, sizeof(double) * p->p[0], s));
         k_mean0<<<(unsigned)((n + MEAN0_PER - 1) / MEAN0_PER), 256, 0, s>>>((const float2 *)d_coef, n, p->P, p->p[0],
                                                                         p->d_mean);
         k_mean0_final<<<(p->p[0] + 63) / 64, 64, 0, s>>>(p->p[0], (double)n, p->d_mean);
