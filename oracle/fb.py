@@ -123,6 +123,31 @@ def ndft_polar(plan, images, batch=4):
     return out.reshape(n, plan.n_xi, plan.n_theta)
 
 
+def polar_grid(c, n_xi, n_theta):
+    """The polar nodes without the Bessel tables of a full plan (for sizes
+    whose plan takes too long here): Gauss-Legendre radii xi_j on [0, c]
+    (Alg. 1 step 2) and angles theta_l = 2 pi l / n_theta (Sec. III).
+    Returns (xi, theta), both float64."""
+    xi, _ = gauss_legendre(int(n_xi), 0.0, float(c))
+    return xi, 2.0 * math.pi * np.arange(int(n_theta)) / int(n_theta)
+
+
+def ndft_points(images, x1, x2):
+    """F(I)(x1, x2) = sum_{i1,i2} I(i1,i2) exp(-2 pi i (x1 i1 + x2 i2)) at
+    arbitrary frequency points (the definition inside Eq. nufft, without the
+    1/(2R)^2 factor), one point at a time as u^T I v with u(i1), v(i2) the
+    two exponential factors.  images (n, L, L), x1, x2 (m,) -> complex (n, m)."""
+    images = np.asarray(images, dtype=np.float64)
+    L = images.shape[-1]
+    idx = np.arange(L, dtype=np.float64) - (L // 2)     # i = -ceil((L-1)/2) .. (Sec. II)
+    out = np.empty((images.shape[0], len(x1)), dtype=np.complex128)
+    for t, (a, b) in enumerate(zip(x1, x2)):
+        u = np.exp(-2j * math.pi * float(a) * idx)
+        v = np.exp(-2j * math.pi * float(b) * idx)
+        out[:, t] = np.einsum("i,nij,j->n", u, images, v)
+    return out
+
+
 def ring_dft_matrix(plan):
     """E[l, k] = (2 pi / n_theta) exp(-2 pi i k l / n_theta), k = 0..k_max."""
     l = np.arange(plan.n_theta)[:, None]

@@ -170,6 +170,38 @@ def test_ndft_brute_force():
             assert abs(F[i, j, l] - s) < 1e-13
 
 
+@pytest.mark.parametrize("L", [8, 9])
+def test_ndft_points_on_the_dft_grid_is_fft2(L):
+    """At x = m / L the sum of Eq. nufft is the 2D DFT of the image: with
+    i = a - floor(L/2), F(m/L) = fft2(I)[m] exp(2 pi i (m1 + m2) floor(L/2) / L)
+    (library special case, even and odd L)."""
+    rng = np.random.default_rng(4)
+    I = rng.standard_normal((2, L, L))
+    m1 = rng.integers(0, L, 12)
+    m2 = rng.integers(0, L, 12)
+    F = fb.ndft_points(I, m1 / L, m2 / L)
+    ref = np.fft.fft2(I)[:, m1, m2] * np.exp(2j * math.pi * (m1 + m2) * (L // 2) / L)[None, :]
+    assert np.max(np.abs(F - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_ndft_points_of_a_delta_and_polar_grid():
+    """A single unit pixel at i0 has F(x) = exp(-2 pi i x . i0) (closed form);
+    the plan-free polar grid has the full plan's radii and angles."""
+    L = 10
+    I = np.zeros((1, L, L))
+    I[0, 7, 2] = 1.0                                  # i0 = (7 - 5, 2 - 5)
+    rng = np.random.default_rng(5)
+    x1, x2 = rng.uniform(-0.5, 0.5, 9), rng.uniform(-0.5, 0.5, 9)
+    F = fb.ndft_points(I, x1, x2)[0]
+    assert np.max(np.abs(F - np.exp(-2j * math.pi * (x1 * 2 + x2 * -3)))) < 1e-13
+    p = fb.make_plan(16, 0.5, 8.0)
+    xi, th = fb.polar_grid(0.5, p.n_xi, p.n_theta)
+    assert np.array_equal(xi, p.xi)
+    a, b = p.polar_points()
+    assert np.max(np.abs(xi[:, None] * np.cos(th)[None, :] - a)) == 0.0
+    assert np.max(np.abs(xi[:, None] * np.sin(th)[None, :] - b)) == 0.0
+
+
 def test_ndft_hermitian_half_ring():
     """Real images: F(xi, theta + pi) = conj F(xi, theta)."""
     p = fb.make_plan(16, 0.5, 8.0)
