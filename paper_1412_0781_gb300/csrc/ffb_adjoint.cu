@@ -85,8 +85,10 @@ k_adj_bessel(const float2 *__restrict__ y, const float *__restrict__ Bf, const i
 
 // ---------------------------------------------------------------------------
 // inverse ring DFT + fold + spreading onto the extended half grid (zeroed
-// beforehand).  grid (ceil(n_xi/ADJ_RB), nimg), ADJ_NT threads.
+// beforehand).  grid (ceil(n_xi/RB), nimg), ADJ_NT threads,
+// RB rings per CTA.
 // ---------------------------------------------------------------------------
+template <int RB>
 __global__ void __launch_bounds__(ADJ_NT)
 k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, float beta,
                   const float2 *__restrict__ rad, const float4 *__restrict__ ang, int n_xi, int n_theta,
@@ -94,14 +96,14 @@ k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, f
                   float2 *__restrict__ Gext, int *status) {
     extern __shared__ float2 sm[];
     float2 *ringA = sm;
-    float2 *ringB = sm + ADJ_RB * n_theta;
+    float2 *ringB = sm + RB * n_theta;
     const int img = blockIdx.y;
-    const int j0 = blockIdx.x * ADJ_RB;
+    const int j0 = blockIdx.x * RB;
     const int nh = n_theta / 2;
-    for (int t = threadIdx.x; t < ADJ_RB * n_theta; t += ADJ_NT) ringA[t] = make_float2(0.f, 0.f);
+    for (int t = threadIdx.x; t < RB * n_theta; t += ADJ_NT) ringA[t] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int t = threadIdx.x; t < (kmax + 1) * 2 * ADJ_RB; t += ADJ_NT) {
-        const int jj = t % ADJ_RB, cc = (t / ADJ_RB) & 1, k = t / (2 * ADJ_RB);
+    for (int t = threadIdx.x; t < (kmax + 1) * 2 * RB; t += ADJ_NT) {
+        const int jj = t % RB, cc = (t / RB) & 1, k = t / (2 * RB);
         const int j = j0 + jj;
         if (j < n_xi) {
             float v = __ldg(&Yhat[(((size_t)k * chunk + img) * 2 + cc) * n_xi + j]);
@@ -111,7 +113,7 @@ k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, f
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int jj = warp; jj < ADJ_RB; jj += ADJ_NT / 32)
+    for (int jj = warp; jj < RB; jj += ADJ_NT / 32)
         smem_fft<true>(ringA + jj * n_theta, ringB + jj * n_theta, fpT, twT, lane, 32, WarpSync());
     __syncthreads();
     const float2 *g = (fpT.nst & 1) ? ringB : ringA;
@@ -119,7 +121,7 @@ k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, f
     float2 *Gi = Gext + (size_t)img * Mh * N;
     const float halfw = 0.5f * (float)w;
     const float two_over_w = 2.0f / (float)w;
-    for (int t = threadIdx.x; t < ADJ_RB * nh; t += ADJ_NT) {
+    for (int t = threadIdx.x; t < RB * nh; t += ADJ_NT) {
         const int jj = t / nh, l = t - jj * nh;
         const int j = j0 + jj;
         if (j >= n_xi) continue;
@@ -162,21 +164,22 @@ k_adj_ring_spread(const float *__restrict__ Yhat, int N, int h, int Mh, int w, f
 // ---------------------------------------------------------------------------
 // inverse ring DFT + fold only (fused-path plans, whose spreading runs in
 // ffb_grid.cu): Gpol[img][j][l] = s (g_l + conj g_{l + n/2}), l < n/2, the
-// layout of the forward's polar buffer.  grid (ceil(n_xi/ADJ_RB), nimg).
+// layout of the forward's polar buffer.  grid (ceil(n_xi/RB), nimg).
 // ---------------------------------------------------------------------------
+template <int RB>
 __global__ void __launch_bounds__(ADJ_NT)
 k_adj_ring_polar(const float *__restrict__ Yhat, int n_xi, int n_theta, const float2 *__restrict__ twT,
                  FftPlanDev fpT, int kmax, int chunk, float2 *__restrict__ Gpol) {
     extern __shared__ float2 sm[];
     float2 *ringA = sm;
-    float2 *ringB = sm + ADJ_RB * n_theta;
+    float2 *ringB = sm + RB * n_theta;
     const int img = blockIdx.y;
-    const int j0 = blockIdx.x * ADJ_RB;
+    const int j0 = blockIdx.x * RB;
     const int nh = n_theta / 2;
-    for (int t = threadIdx.x; t < ADJ_RB * n_theta; t += ADJ_NT) ringA[t] = make_float2(0.f, 0.f);
+    for (int t = threadIdx.x; t < RB * n_theta; t += ADJ_NT) ringA[t] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int t = threadIdx.x; t < (kmax + 1) * 2 * ADJ_RB; t += ADJ_NT) {
-        const int jj = t % ADJ_RB, cc = (t / ADJ_RB) & 1, k = t / (2 * ADJ_RB);
+    for (int t = threadIdx.x; t < (kmax + 1) * 2 * RB; t += ADJ_NT) {
+        const int jj = t % RB, cc = (t / RB) & 1, k = t / (2 * RB);
         const int j = j0 + jj;
         if (j < n_xi) {
             float v = __ldg(&Yhat[(((size_t)k * chunk + img) * 2 + cc) * n_xi + j]);
@@ -186,13 +189,13 @@ k_adj_ring_polar(const float *__restrict__ Yhat, int n_xi, int n_theta, const fl
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int jj = warp; jj < ADJ_RB; jj += ADJ_NT / 32)
+    for (int jj = warp; jj < RB; jj += ADJ_NT / 32)
         smem_fft<true>(ringA + jj * n_theta, ringB + jj * n_theta, fpT, twT, lane, 32, WarpSync());
     __syncthreads();
     const float2 *g = (fpT.nst & 1) ? ringB : ringA;
     const float scale = 6.283185307179586f / (float)n_theta;
     float2 *Gi = Gpol + (size_t)img * n_xi * nh;
-    for (int t = threadIdx.x; t < ADJ_RB * nh; t += ADJ_NT) {
+    for (int t = threadIdx.x; t < RB * nh; t += ADJ_NT) {
         const int jj = t / nh, l = t - jj * nh;
         const int j = j0 + jj;
         if (j >= n_xi) continue;
@@ -310,15 +313,23 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
     if (e) return e;
     if ((e = ffb_ensure_scratch_grid(p))) return e;
     const int N = p->N, L = p->L, Nh = N / 2 + 1;
-    static int a_bes = 0, a_ring = 0, a_cols = 0, a_rows = 0;
+    static int a_bes = 0, a_ring = 0, a_ring4 = 0, a_ringp = 0, a_cols = 0, a_rows = 0;
+    // ADJ_RB rings per CTA, or half as many where their ring buffers would
+    // not fit in shared memory (n_theta > 1816 at 227 KB)
+    const int rb = ffb_ring_buffers_fit(p->n_theta, ADJ_RB) ? ADJ_RB : ADJ_RB / 2;
+    if (!ffb_ring_buffers_fit(p->n_theta, rb) || (p->fused && rb != ADJ_RB)) return FFB_ERR_UNSUPPORTED;
     const size_t sm_bes = sizeof(float) * 2 * 64 * (size_t)(p->pmax + 1);
-    const size_t sm_ring = sizeof(float2) * 2 * ADJ_RB * (size_t)p->n_theta;
+    const size_t sm_ring = sizeof(float2) * 2 * rb * (size_t)p->n_theta;
     const size_t sm_cols = sizeof(float2) * (size_t)ACOL_WARPS * 2 * N;
     const size_t sm_rows = sizeof(float2) * (size_t)AROW_WARPS * 2 * N;
     if ((e = set_smem((const void *)k_adj_bessel, sm_bes, &a_bes))) return e;
-    if ((e = set_smem((const void *)k_adj_ring_spread, sm_ring, &a_ring))) return e;
-    static int a_ringp = 0;
-    if ((e = set_smem((const void *)k_adj_ring_polar, sm_ring, &a_ringp))) return e;
+    if (p->fused) {
+        if ((e = set_smem((const void *)k_adj_ring_polar<ADJ_RB>, sm_ring, &a_ringp))) return e;
+    } else if (rb == ADJ_RB) {
+        if ((e = set_smem((const void *)k_adj_ring_spread<ADJ_RB>, sm_ring, &a_ring))) return e;
+    } else {
+        if ((e = set_smem((const void *)k_adj_ring_spread<ADJ_RB / 2>, sm_ring, &a_ring4))) return e;
+    }
     if ((e = set_smem((const void *)k_adj_cols, sm_cols, &a_cols))) return e;
     if ((e = set_smem((const void *)k_adj_rows, sm_rows, &a_rows))) return e;
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
@@ -338,18 +349,23 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
             {
                 ProfScope ps(p, FFB_KC_ADJ_RING, s);
                 dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
-                k_adj_ring_polar<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT, p->fftT,
-                                                            p->k_max, p->chunk, p->d_Fpol);
+                k_adj_ring_polar<ADJ_RB><<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT,
+                                                                    p->fftT, p->k_max, p->chunk, p->d_Fpol);
                 p->launches++;
                 if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
             }
             if ((e = ffb_launch_fused_spread(p, p->d_Fpol, m, p->d_G, s))) return e;
         } else {
             ProfScope ps(p, FFB_KC_ADJ_RING, s);
-            dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
-            k_adj_ring_spread<<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,
-                                                         p->d_ang, p->n_xi, p->n_theta, p->d_twT, p->fftT,
-                                                         p->k_max, p->chunk, p->d_G, p->d_status);
+            dim3 g((p->n_xi + rb - 1) / rb, m);
+            if (rb == ADJ_RB)
+                k_adj_ring_spread<ADJ_RB><<<g, ADJ_NT, sm_ring, s>>>(
+                    p->d_Fhat, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad, p->d_ang, p->n_xi, p->n_theta,
+                    p->d_twT, p->fftT, p->k_max, p->chunk, p->d_G, p->d_status);
+            else
+                k_adj_ring_spread<ADJ_RB / 2><<<g, ADJ_NT, sm_ring, s>>>(
+                    p->d_Fhat, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad, p->d_ang, p->n_xi, p->n_theta,
+                    p->d_twT, p->fftT, p->k_max, p->chunk, p->d_G, p->d_status);
             p->launches++;
         }
         {

@@ -14,22 +14,25 @@
 // latches FFB_ERR_NOT_CONVERGED and still returns its current estimate.
 #include "ffb_internal.cuh"
 
-#define EIG_MAXP 200       // A (p+1 stride, float64) must fit in shared memory
+#define EIG_MAXP 512          // larger blocks are rejected (p_k <= 255 for L <= 512)
 #define EIG_VSHARED_MAXP 110  // beyond this V lives in a global workspace
+#define EIG_ASHARED_MAXP 166  // beyond this A does too (its pp x (pp+1) doubles fill 227 KB)
 #define EIG_MAX_SWEEPS 40
 
 __global__ void __launch_bounds__(256)
 k_jacobi(const double *__restrict__ Cfin, const int *__restrict__ pk_, const int *__restrict__ off_,
          const int *__restrict__ cov_off, double *__restrict__ evals, double *__restrict__ evecs, int *status,
-         double *__restrict__ vwork, int ldmax) {
+         double *__restrict__ vwork, int ldmax, int aglobal) {
     extern __shared__ double shd[];
     const int k = blockIdx.x;
     const int p = pk_[k];
     const int pp = p + (p & 1);
     const int ld = (vwork ? ldmax : pp + 1);
-    double *A = shd;                                                   // [pp][ld]
-    double *V = vwork ? vwork + (size_t)k * ldmax * ldmax : A + pp * ld;  // [pp][ld]
-    double *cs = vwork ? A + (size_t)ldmax * ldmax : V + pp * ld;      // [pp/2][2]
+    // workspace of block k: V [ldmax][ldmax], then A [ldmax][ldmax] when aglobal
+    double *wk = vwork ? vwork + (size_t)k * (aglobal ? 2 : 1) * ldmax * ldmax : nullptr;
+    double *A = aglobal ? wk + (size_t)ldmax * ldmax : shd;            // [pp][ld]
+    double *V = vwork ? wk : A + pp * ld;                              // [pp][ld]
+    double *cs = aglobal ? shd : (vwork ? A + (size_t)ldmax * ldmax : V + pp * ld);   // [pp/2][2]
     double *red = cs + pp;            // [256]
     int *pos = (int *)(red + 256);    // [pp]
     int *pair = pos + pp;             // [pp/2][2]
@@ -171,13 +174,17 @@ int ffb_launch_eig(ffb_plan_t p, cudaStream_t s) {
     if (p->pmax > EIG_MAXP) return FFB_ERR_UNSUPPORTED;
     const int pp = p->pmax + (p->pmax & 1);
     const bool vglobal = pp > EIG_VSHARED_MAXP;
+    const bool aglobal = pp > EIG_ASHARED_MAXP;
     const int ldmax = pp + 1;
     if (vglobal && !p->d_eig_work) {
-        int e = ffb_check_cuda(cudaMalloc(&p->d_eig_work, sizeof(double) * (size_t)(p->k_max + 1) * ldmax * ldmax));
+        int e = ffb_check_cuda(cudaMalloc(&p->d_eig_work, sizeof(double) * (size_t)(p->k_max + 1) *
+                                                              (aglobal ? 2 : 1) * ldmax * ldmax));
         if (e) return e;
     }
-    size_t smem = vglobal ? sizeof(double) * ((size_t)ldmax * ldmax + pp + 256) + sizeof(int) * (size_t)(2 * pp)
-                          : sizeof(double) * (2 * (size_t)pp * (pp + 1) + pp + 256) + sizeof(int) * (size_t)(2 * pp);
+    const size_t tail = sizeof(double) * ((size_t)pp + 256) + sizeof(int) * (size_t)(2 * pp);
+    size_t smem = aglobal   ? tail
+                  : vglobal ? sizeof(double) * (size_t)ldmax * ldmax + tail
+                            : sizeof(double) * 2 * (size_t)pp * (pp + 1) + tail;
     static int attr = 0;
     if (smem > 48 * 1024 && attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -186,7 +193,8 @@ int ffb_launch_eig(ffb_plan_t p, cudaStream_t s) {
     }
     ProfScope ps(p, FFB_KC_EIG, s);
     k_jacobi<<<p->k_max + 1, 256, smem, s>>>(p->d_Cfin, p->d_p, p->d_off, p->d_cov_off, p->d_evals, p->d_evecs,
-                                             p->d_status, vglobal ? p->d_eig_work : nullptr, ldmax);
+                                             p->d_status, vglobal ? p->d_eig_work : nullptr, ldmax,
+                                             aglobal ? 1 : 0);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }

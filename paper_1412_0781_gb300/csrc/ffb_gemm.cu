@@ -8,7 +8,8 @@
 // ---------------------------------------------------------------------------
 // a5, FP32: one CTA per (k, 32 images).  Rows of the A operand are the 64
 // (image, re/im) rows of Fhat[k] (contiguous in memory), columns of B are
-// the p_k rows of B^(k) in tiles of 64; K = n_xi.  Both tiles are stored
+// the p_k rows of B^(k) in tiles of 64; K = n_xi, in slabs of at most
+// BES_KT (one slab up to L = 384 at R = L/2).  Both tiles are stored
 // transposed in shared memory (K-major: At[j][row], Bt[j][q]) so that a
 // thread reads its 4 rows and 4 columns with two 16-byte loads per j.
 // Thread (ty = t % 16, tx = t / 16): rows 4 ty .., columns 4 tx ..; a warp
@@ -16,48 +17,61 @@
 // ---------------------------------------------------------------------------
 #define BES_IMG 32
 #define BES_TP 68    // row pitch of the transposed tiles (floats): 64 + 4, 16-byte aligned
+#define BES_KT 384   // K slab: two [BES_KT][BES_TP] float tiles = 204 KB
 
-static size_t bessel_fp32_smem(int n_xi) { return sizeof(float) * (size_t)n_xi * 2 * BES_TP; }
+static int bessel_fp32_kt(int n_xi) { return n_xi < BES_KT ? n_xi : BES_KT; }
+static size_t bessel_fp32_smem(int n_xi) { return sizeof(float) * (size_t)bessel_fp32_kt(n_xi) * 2 * BES_TP; }
 
 __global__ void __launch_bounds__(256)
 k_bessel_fp32(const float *__restrict__ Fhat, const float *__restrict__ Bf, const int *__restrict__ pk_,
-              const int *__restrict__ off_, int n_xi, int chunk, int nimg, int P, float2 *__restrict__ coef) {
+              const int *__restrict__ off_, int n_xi, int kt, int chunk, int nimg, int P,
+              float2 *__restrict__ coef) {
     extern __shared__ float4 sm4[];
-    float *At = (float *)sm4;                    // [n_xi][BES_TP]
-    float *Bt = At + (size_t)n_xi * BES_TP;      // [n_xi][BES_TP]
+    float *At = (float *)sm4;                    // [kt][BES_TP]
+    float *Bt = At + (size_t)kt * BES_TP;        // [kt][BES_TP]
     const int k = blockIdx.y;
     const int pk = pk_[k], o = off_[k];
     const int i0 = blockIdx.x * BES_IMG;
     const float *Ak = Fhat + ((size_t)k * chunk + i0) * 2 * n_xi;
     const int rows = min(BES_IMG, nimg - i0) * 2;
-    for (int e = threadIdx.x; e < 2 * BES_IMG * n_xi; e += 256) {
-        const int r = e / n_xi, j = e - r * n_xi;
-        At[j * BES_TP + r] = (r < rows) ? __ldg(&Ak[(size_t)r * n_xi + j]) : 0.f;
-    }
+    const bool one_slab = kt >= n_xi;
+    auto load_a = [&](int j0, int kl) {
+        for (int e = threadIdx.x; e < 2 * BES_IMG * kl; e += 256) {
+            const int r = e / kl, j = e - r * kl;
+            At[j * BES_TP + r] = (r < rows) ? __ldg(&Ak[(size_t)r * n_xi + j0 + j]) : 0.f;
+        }
+    };
+    if (one_slab) load_a(0, n_xi);
     const int ty = threadIdx.x & 15, tx = threadIdx.x >> 4;
     for (int q0 = 0; q0 < pk; q0 += 64) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < 64 * n_xi; e += 256) {
-            const int q = e / n_xi, j = e - q * n_xi;
-            Bt[j * BES_TP + q] = (q0 + q < pk) ? __ldg(&Bf[(size_t)(o + q0 + q) * n_xi + j]) : 0.f;
-        }
-        __syncthreads();
-        if (8 * (threadIdx.x >> 5) >= pk - q0) continue;   // the warp's 8 columns are padding
+        const bool active = 8 * (threadIdx.x >> 5) < pk - q0;   // else the warp's 8 columns are padding
         float acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+        for (int j0 = 0; j0 < n_xi; j0 += kt) {
+            const int kl = min(kt, n_xi - j0);
+            __syncthreads();
+            if (!one_slab) load_a(j0, kl);
+            for (int e = threadIdx.x; e < 64 * kl; e += 256) {
+                const int q = e / kl, j = e - q * kl;
+                Bt[j * BES_TP + q] = (q0 + q < pk) ? __ldg(&Bf[(size_t)(o + q0 + q) * n_xi + j0 + j]) : 0.f;
+            }
+            __syncthreads();
+            if (!active) continue;
 #pragma unroll 4
-        for (int j = 0; j < n_xi; ++j) {
-            const float4 a = *(const float4 *)&At[j * BES_TP + 4 * ty];
-            const float4 b = *(const float4 *)&Bt[j * BES_TP + 4 * tx];
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            for (int j = 0; j < kl; ++j) {
+                const float4 a = *(const float4 *)&At[j * BES_TP + 4 * ty];
+                const float4 b = *(const float4 *)&Bt[j * BES_TP + 4 * tx];
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+            }
         }
+        if (!active) continue;
 #pragma unroll
         for (int ii = 0; ii < 2; ++ii) {             // rows 4 ty + 2 ii (re), + 1 (im)
             const int img = i0 + 2 * ty + ii;
@@ -81,8 +95,8 @@ int ffb_launch_bessel_fp32(ffb_plan_t p, int nimg, float *d_coef_chunk, cudaStre
     }
     dim3 g((nimg + BES_IMG - 1) / BES_IMG, p->k_max + 1);
     ProfScope ps(p, FFB_KC_BESSEL, s);
-    k_bessel_fp32<<<g, 256, smem, s>>>(p->d_Fhat, p->d_Bf, p->d_p, p->d_off, p->n_xi, p->chunk, nimg, p->P,
-                                       (float2 *)d_coef_chunk);
+    k_bessel_fp32<<<g, 256, smem, s>>>(p->d_Fhat, p->d_Bf, p->d_p, p->d_off, p->n_xi, bessel_fp32_kt(p->n_xi),
+                                       p->chunk, nimg, p->P, (float2 *)d_coef_chunk);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
@@ -358,16 +372,22 @@ __global__ void k_filter_matrix(const double *__restrict__ U, const double *__re
 __global__ void __launch_bounds__(256)
 k_filter(const float2 *__restrict__ cin, float2 *__restrict__ cout, int64_t n, int P, const float *__restrict__ M,
          const double *__restrict__ mean, const int *__restrict__ pk_, const int *__restrict__ off_,
-         const int *__restrict__ cov_off, int flags) {
+         const int *__restrict__ cov_off, int flags, int mglobal) {
     extern __shared__ float smf[];
     const int k = blockIdx.y;
     const int pk = pk_[k], o = off_[k];
     const int64_t i0 = (int64_t)blockIdx.x * FIL_IMG;
     const bool affine = !(flags & 1) && k == 0;
-    // float2 tile first: it needs 8-byte alignment (pk * pk floats may be odd)
+    // float2 tile first: it needs 8-byte alignment (pk * pk floats may be odd);
+    // M^(k) is staged behind it unless it is read from global memory (blocks
+    // whose pk x pk floats do not fit next to the tile)
     float2 *X = (float2 *)smf;                    // [FIL_IMG][pk]
-    float *Ms = smf + 2 * FIL_IMG * pk;           // [pk][pk]
-    for (int e = threadIdx.x; e < pk * pk; e += blockDim.x) Ms[e] = M[cov_off[k] + e];
+    const float *Ms = M + cov_off[k];             // [pk][pk]
+    if (!mglobal) {
+        float *Mst = smf + 2 * FIL_IMG * pk;
+        for (int e = threadIdx.x; e < pk * pk; e += blockDim.x) Mst[e] = Ms[e];
+        Ms = Mst;
+    }
     for (int t = threadIdx.x; t < FIL_IMG * pk; t += blockDim.x) {
         const int ii = t / pk, q = t - ii * pk;
         float2 v = make_float2(0.f, 0.f);
@@ -414,7 +434,13 @@ int ffb_launch_filter_matrix(ffb_plan_t p, cudaStream_t s) {
 
 int ffb_launch_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, int flags,
                       cudaStream_t s) {
-    const size_t smem = sizeof(float) * (size_t)p->pmax * p->pmax + sizeof(float2) * FIL_IMG * (size_t)p->pmax;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t tile = sizeof(float2) * FIL_IMG * (size_t)p->pmax;
+    const size_t mbytes = sizeof(float) * (size_t)p->pmax * p->pmax;
+    const int mglobal = (tile + mbytes > (size_t)optin) ? 1 : 0;
+    const size_t smem = mglobal ? tile : tile + mbytes;
     static int attr = 0;
     if (smem > 48 * 1024 && attr < (int)smem) {
         int e = ffb_check_cuda(cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -424,7 +450,7 @@ int ffb_launch_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_
     dim3 g((unsigned)((n + FIL_IMG - 1) / FIL_IMG), p->k_max + 1);
     ProfScope ps(p, FFB_KC_FILTER, s);
     k_filter<<<g, 256, smem, s>>>((const float2 *)d_coef_in, (float2 *)d_coef_out, n, p->P, p->d_M, p->d_mean,
-                                  p->d_p, p->d_off, p->d_cov_off, flags);
+                                  p->d_p, p->d_off, p->d_cov_off, flags, mglobal);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }

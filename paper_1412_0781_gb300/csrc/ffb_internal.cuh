@@ -326,6 +326,9 @@ __device__ __forceinline__ double bessel_j_miller(int k, double x) {
 int ffb_check_cuda(cudaError_t e);
 int ffb_ensure_scratch(ffb_plan_t plan);
 int ffb_ensure_scratch_grid(ffb_plan_t plan);
+// true when two buffers of rb rings of n_theta complex values each fit in
+// the shared memory one CTA may opt in to (the ring DFT kernels' staging)
+bool ffb_ring_buffers_fit(int n_theta, int rb);
 bool ffb_fused_supported(ffb_plan_t plan);
 int ffb_fused_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_fused_mode(ffb_plan_t plan);   // 1 plain, 2 cluster variant of the fused kernel

@@ -121,32 +121,32 @@ k_cols(const float2 *__restrict__ H, int L, int off, int N, int h, int Mh,
 }
 
 // ---------------------------------------------------------------------------
-// a3 + a4: interpolation at the half-ring nodes of RING_RB rings and the
+// a3 + a4: interpolation at the half-ring nodes of RB rings and the
 // length-n_theta ring FFT (Eq. 1DFFT) with F(theta + pi) = conj F(theta).
 // POLAR = true writes the interpolated half rings (ffb_polar) instead.
-// grid (ceil(n_xi / RING_RB), nimg), block RING_NT
+// grid (ceil(n_xi / RB), nimg), block RING_NT
 //
 // Node coordinates t = N xi_j cos(theta_l) are formed in double-float
 // (hi + lo parts) so that the stencil offset f = t - m0 keeps ~1e-7 absolute
 // accuracy even where t ~ N/2: rounding xi to float32 alone would move the
 // node by ~3e-8 and the phase of F by 2 pi * 3e-8 * |i|.
 // ---------------------------------------------------------------------------
-template <bool POLAR>
+template <bool POLAR, int RB>
 __global__ void __launch_bounds__(RING_NT)
 k_interp_ring(const float2 *__restrict__ G, int N, int h, int Mh, int w, float beta,
               const float2 *__restrict__ rad, const float4 *__restrict__ ang, int n_xi, int n_theta,
               const float2 *__restrict__ twT, FftPlanDev fpT, int kmax, int chunk,
               float *__restrict__ Fhat, float2 *__restrict__ Fpolar, int *status) {
     extern __shared__ float2 sm[];
-    float2 *ringA = sm;                         // [RING_RB][n_theta]
-    float2 *ringB = sm + RING_RB * n_theta;     // [RING_RB][n_theta]
+    float2 *ringA = sm;                         // [RB][n_theta]
+    float2 *ringB = sm + RB * n_theta;     // [RB][n_theta]
     const int img = blockIdx.y;
-    const int j0 = blockIdx.x * RING_RB;
+    const int j0 = blockIdx.x * RB;
     const int nh = n_theta / 2;
     const float2 *Gi = G + (size_t)img * Mh * N;
     const float halfw = 0.5f * (float)w;
     const float two_over_w = 2.0f / (float)w;
-    for (int t = threadIdx.x; t < RING_RB * nh; t += RING_NT) {
+    for (int t = threadIdx.x; t < RB * nh; t += RING_NT) {
         const int jj = t / nh, l = t - jj * nh;
         const int j = j0 + jj;
         float2 val = make_float2(0.f, 0.f);
@@ -197,16 +197,16 @@ k_interp_ring(const float2 *__restrict__ G, int N, int h, int Mh, int w, float b
     if (POLAR) return;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int jj = warp; jj < RING_RB; jj += RING_NT / 32)
+    for (int jj = warp; jj < RB; jj += RING_NT / 32)
         smem_fft<false>(ringA + jj * n_theta, ringB + jj * n_theta, fpT, twT, lane, 32, WarpSync());
     __syncthreads();
     const float2 *res = (fpT.nst & 1) ? ringB : ringA;
     const float scale = 6.283185307179586f / (float)n_theta;
-    const int tot = (kmax + 1) * 2 * RING_RB;
+    const int tot = (kmax + 1) * 2 * RB;
     for (int t = threadIdx.x; t < tot; t += RING_NT) {
-        const int jj = t % RING_RB;
-        const int cc = (t / RING_RB) & 1;
-        const int k = t / (2 * RING_RB);
+        const int jj = t % RB;
+        const int cc = (t / RB) & 1;
+        const int k = t / (2 * RB);
         const int j = j0 + jj;
         if (j < n_xi) {
             float2 v = res[jj * n_theta + k];
@@ -250,22 +250,32 @@ int ffb_launch_grid(ffb_plan_t p, const float *d_images, int64_t i0, int nimg, c
     return ffb_check_cuda(cudaGetLastError());
 }
 
-template <bool POLAR>
-static int launch_interp(ffb_plan_t p, int nimg, float2 *d_F, cudaStream_t s) {
-    size_t smem = POLAR ? 0 : sizeof(float2) * 2 * RING_RB * (size_t)p->n_theta;
+template <bool POLAR, int RB>
+static int launch_interp_rb(ffb_plan_t p, int nimg, float2 *d_F, cudaStream_t s) {
+    size_t smem = POLAR ? 0 : sizeof(float2) * 2 * RB * (size_t)p->n_theta;
     static int attr = 0;
     if (smem > 48 * 1024 && attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_interp_ring<POLAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_interp_ring<POLAR, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
         if (e) return e;
         attr = (int)smem;
     }
-    dim3 g((p->n_xi + RING_RB - 1) / RING_RB, nimg);
+    dim3 g((p->n_xi + RB - 1) / RB, nimg);
     ProfScope ps(p, FFB_KC_INTERP, s);
-    k_interp_ring<POLAR><<<g, RING_NT, smem, s>>>(p->d_G, p->N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,
-                                                  p->d_ang, p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max,
-                                                  p->chunk, p->d_Fhat, d_F, p->d_status);
+    k_interp_ring<POLAR, RB><<<g, RING_NT, smem, s>>>(p->d_G, p->N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,
+                                                      p->d_ang, p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max,
+                                                      p->chunk, p->d_Fhat, d_F, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
+}
+
+// RING_RB rings per CTA, or half as many where their two ring buffers would
+// not fit in shared memory (n_theta > 1816 at 227 KB: L > 454 when R = L/2)
+template <bool POLAR>
+static int launch_interp(ffb_plan_t p, int nimg, float2 *d_F, cudaStream_t s) {
+    if (POLAR || ffb_ring_buffers_fit(p->n_theta, RING_RB)) return launch_interp_rb<POLAR, RING_RB>(p, nimg, d_F, s);
+    if (ffb_ring_buffers_fit(p->n_theta, RING_RB / 2)) return launch_interp_rb<POLAR, RING_RB / 2>(p, nimg, d_F, s);
+    return FFB_ERR_UNSUPPORTED;
 }
 
 int ffb_launch_interp_ring(ffb_plan_t p, int nimg, cudaStream_t s) {
@@ -357,10 +367,10 @@ extern "C" int ffb_polar_noalloc(ffb_plan_t p, const float *d_images, int64_t n,
         dim3 g2((Nh + COL_WARPS - 1) / COL_WARPS, m);
         k_cols<<<g2, 32 * COL_WARPS, sm_cols, s>>>(H, L, p->off, N, p->h, p->Mh, p->d_twN, p->fftN, G);
         dim3 g3((p->n_xi + RING_RB - 1) / RING_RB, m);
-        k_interp_ring<true><<<g3, RING_NT, 0, s>>>(G, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad, p->d_ang,
-                                                   p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max, m,
-                                                   nullptr, (float2 *)(d_F + (size_t)i0 * per_out),
-                                                   p->d_status);
+        k_interp_ring<true, RING_RB><<<g3, RING_NT, 0, s>>>(G, N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,
+                                                            p->d_ang, p->n_xi, p->n_theta, p->d_twT, p->fftT,
+                                                            p->k_max, m, nullptr,
+                                                            (float2 *)(d_F + (size_t)i0 * per_out), p->d_status);
         p->launches += 3;
         e = ffb_check_cuda(cudaGetLastError());
         if (e) return e;

@@ -371,6 +371,13 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
 }
 
 // row spectra and half grid of a chunk (separate-kernel NUFFT and adjoint)
+bool ffb_ring_buffers_fit(int n_theta, int rb) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return sizeof(float2) * 2 * (size_t)rb * n_theta <= (size_t)optin;
+}
+
 int ffb_ensure_scratch_grid(ffb_plan_t p) {
     if (p->d_H) return FFB_OK;
     CK(dalloc(&p->d_H, (size_t)p->chunk * (p->N / 2 + 1) * p->L));
