@@ -78,7 +78,12 @@ typedef enum {
  * Eq. a, and builds the type-2 NUFFT used for Eq. nufft (exponential-of-
  * semicircle kernel, oversampling 2, width ceil(log10(1/eps)) + 2).
  *   L in [8, 512], c in (0, 1/2], R in (0, L/2], eps in [1e-7, 1e-2],
- *   precision an ffb_precision.  2L and n_theta must factor into 2, 3, 5.
+ *   precision an ffb_precision (FFB_ERR_ARG otherwise).  2L and n_theta must
+ *   factor into 2, 3, 5 (FFB_ERR_UNSUPPORTED otherwise).  Every accepted
+ *   size runs every entry point of this header except where one states a
+ *   tighter bound (ffb_svd; the tensor-core covariance of ffb_group_*); the
+ *   largest, L = 512 with R = 256 and c = 1/2, has p_0 = 255 and n_theta =
+ *   2048, for which some kernels switch to smaller shared-memory tiles.
  * On success *out owns device memory until ffb_plan_destroy.  Synchronous. */
 int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
              int precision, void *stream);
