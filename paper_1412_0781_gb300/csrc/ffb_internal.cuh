@@ -87,7 +87,7 @@ struct ffb_plan_s {
     double *d_mean = nullptr;    // [p0]
     double *d_evals = nullptr;   // [P]
     double *d_evecs = nullptr;   // [cov_total]
-    double *d_eig_work = nullptr;  // Jacobi eigenvector workspace for large blocks
+    double *d_eig_work = nullptr;  // Jacobi workspace of large blocks (V, and A above 166 rows)
     // denoising
     float2 *d_coef_den = nullptr;  // [den_cap][P]
     int64_t den_cap = 0;
