@@ -139,14 +139,15 @@ def hbm_floor():
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (profiles/k_grid_interp_half_L128.md: 152-image launch), valid only
 # while the kernel's sources are byte-identical to the profiled ones (the
-# kernel's file and the register-FFT header; from ffb_internal.cuh it uses
+# kernel's file from its top through the kernel, i.e. its macros, device
+# helpers and body, and the register-FFT header; from ffb_internal.cuh it uses
 # only the complex arithmetic and the status flag).  ncu empties L2 before the
 # capture, so the figure includes one read of the plan's 2.6 MB unit table,
 # which stays in L2 between launches in a live run.
 NCU_TRAFFIC = {
-    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu",
+    "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu:^k_grid_interp_half",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "ba306058583a5f770fbd2ef4311bc0cbac80acac2f91ccf9380d1fb050972b43",
+                    "sha256": "e5875d077193c9ebc126ce8e8002b8b182eb036906f5b86b1b32c92eb895e4aa",
                     "bytes_per_launch": 12652800 + 90112, "images_per_launch": 152},
 }
 
@@ -154,17 +155,21 @@ NCU_TRAFFIC = {
 def _source_digest(sources):
     """sha256 over the listed files (the kernel's file and the header its
     inlined helpers come from); "file:kernel" hashes only the text from the
-    kernel's template line to the next section banner."""
+    kernel's template line to the next section banner, "file:^kernel" the
+    text from the top of the file (its macros and device helpers) to that
+    banner, so that host code further down does not count."""
     import hashlib
     h = hashlib.sha256()
     for src in sources:
         path, _, kern = src.partition(":")
         txt = open(os.path.join(ROOT, path)).read()
         if kern:
+            top = kern.startswith("^")
+            kern = kern.lstrip("^")
             a = txt.index(kern + "(")
             a = txt.rindex("template", 0, a)
             b = txt.index("\n// " + "-" * 75 + "\n", a)   # the next full-width section banner
-            txt = txt[a:b]
+            txt = txt[:b] if top else txt[a:b]
         h.update(txt.encode())
     return h.hexdigest()
 

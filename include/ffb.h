@@ -88,6 +88,34 @@ typedef enum {
 int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
              int precision, void *stream);
 
+/* ffb_interp_units -- the interpolation table that ffb_plan builds for the
+ * shared-memory grid path (plan_info[10] = 1 or 2), computed on the host for
+ * inspection and tests; no GPU work.  It drives the type-2 NUFFT's last step
+ * (Eq. nufft, Sec. III): the polar node (xi_j, theta_l), theta_l = 2 pi l /
+ * n_theta, l < n_theta/2, sits at p = N xi_j (cos, sin) in grid units; its
+ * w x w window of the half grid starts at row r0 = ceil(p2 - w/2) + (w+1)/2
+ * and column c0 = ceil(p1 - w/2) - m1lo (m1lo = -(w+1)/2 for half 0, the
+ * nodes with cos theta >= 0, i.e. l <= n_theta/4; -N/2 - (w+1)/2 for half 1),
+ * with the weights phi(f - b), f = p - ceil(p - w/2), b < w, phi(x) =
+ * exp(beta (sqrt(1 - (2x/w)^2) - 1)) evaluated in float64.
+ *   N in {128, 256}, w = 8 (FFB_ERR_UNSUPPORTED otherwise), beta > 0 (the
+ *   plan uses 2.30 w), h_xi[n_xi] the radii on [0, c] (the plan's
+ *   Gauss-Legendre nodes), n_theta even.
+ * h_counts[7] (out): float4 records, blocks, blocks of half 0, blocks of
+ *   half 1, units per block GU, half-grid size MH, its row pitch SLD.
+ * h_rec (may be NULL: sizing call): float[4 h_counts[0]], per block 9 fields
+ *   of GU float4 ([block][field][unit]): fields 0-1 the 8 row weights of node
+ *   A, 2-3 those of node B, 4-5 A's column weights 0..7 over the unit's
+ *   9-column union, 6-7 B's, field 8 = (B's column 8, bits of r0 | cu << 16
+ *   with cu the union's first column, bits of the block-local node slots
+ *   A | B << 16 as unsigned halves, B = 0xFFFF for a single node, A's column
+ *   8); an empty unit has slots 0xFFFFFFFF.
+ * h_blk (may be NULL): int[2 h_counts[1]], per block (first node t0, node
+ *   count), nodes numbered t = j nl + (l - l0) within the half (nl nodes per
+ *   ring of the half, l0 its first angle); half 0's blocks come first. */
+int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta, const double *h_xi,
+                     int64_t *h_counts, float *h_rec, int *h_blk);
+
 /* Releases everything the plan owns.  NULL is accepted. */
 int ffb_plan_destroy(ffb_plan_t plan);
 

@@ -593,18 +593,16 @@ bool ffb_fused_supported(ffb_plan_t p) {
 // this interval structure); the rest are single units.  Units are ordered per
 // half warp with distinct bank slots (r0 SLD + c0) mod 16: one unit from every
 // nonempty slot, fullest slot first, then fill from the fullest.
-int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
-    const int N = p->N, W = p->w, H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W);
-    if (W != 8) return FFB_ERR_UNSUPPORTED;
+static int build_units(int N, int W, double beta, int n_xi, int n_theta, const double *xi,
+                       std::vector<float4> &rec, std::vector<int2> &blk, int nb[2]) {
+    if (W != 8 || !(N == 128 || N == 256) || n_xi < 1 || n_theta < 4 || (n_theta & 1) || !xi)
+        return FFB_ERR_UNSUPPORTED;
+    const int H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W);
     const int GN = FUS_WARPS * N / 2, GU = std::min(FUS_GU, GN / 2);
-    const int nh = p->n_theta / 2;
-    std::vector<double> xi(p->n_xi);
-    int e = ffb_check_cuda(cudaMemcpyAsync(xi.data(), p->d_xi, sizeof(double) * p->n_xi, cudaMemcpyDeviceToHost, s));
-    if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
-    if (e) return e;
+    const int nh = n_theta / 2, nq0 = n_theta / 4 + 1;
     auto phi = [&](double x) {
         const double z = 2.0 * x / W, u = 1.0 - z * z;
-        return (u > 0.0) ? std::exp(p->beta * (std::sqrt(u) - 1.0)) : 0.0;
+        return (u > 0.0) ? std::exp(beta * (std::sqrt(u) - 1.0)) : 0.0;
     };
     auto bits = [](int v) {
         float f;
@@ -615,19 +613,19 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
         int r0, c0;
         double f1, f2;
     };
-    std::vector<float4> rec;
-    std::vector<int2> blk;
-    int nb[2] = {0, 0};
+    rec.clear();
+    blk.clear();
+    nb[0] = nb[1] = 0;
     for (int half = 0; half < 2; ++half) {
-        const int lbeg = (half == 0) ? 0 : p->nq0;
-        const int nl = (half == 0) ? p->nq0 : nh - p->nq0;
-        const int npts = p->n_xi * nl;
+        const int lbeg = (half == 0) ? 0 : nq0;
+        const int nl = (half == 0) ? nq0 : nh - nq0;
+        const int npts = n_xi * nl;
         const int m1lo = (half == 0) ? -H : -(N / 2) - H;
         if (nl > GN) return FFB_ERR_UNSUPPORTED;
         std::vector<Node> nd(npts);
         for (int t = 0; t < npts; ++t) {
             const int j = t / nl, l = lbeg + t % nl;
-            const double th = 2.0 * M_PI * (double)l / (double)p->n_theta;
+            const double th = 2.0 * M_PI * (double)l / (double)n_theta;
             const double p1 = N * xi[j] * std::cos(th), p2 = N * xi[j] * std::sin(th);
             const double m1 = std::ceil(p1 - 0.5 * W), m2 = std::ceil(p2 - 0.5 * W);
             const int c0 = (int)m1 - m1lo, r0 = (int)m2 + H;
@@ -764,6 +762,19 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
             t0 = t1;
         }
     }
+    return FFB_OK;
+}
+
+int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
+    const int N = p->N;
+    std::vector<double> xi(p->n_xi);
+    int e = ffb_check_cuda(cudaMemcpyAsync(xi.data(), p->d_xi, sizeof(double) * p->n_xi, cudaMemcpyDeviceToHost, s));
+    if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
+    if (e) return e;
+    std::vector<float4> rec;
+    std::vector<int2> blk;
+    int nb[2] = {0, 0};
+    if ((e = build_units(N, p->w, p->beta, p->n_xi, p->n_theta, xi.data(), rec, blk, nb))) return e;
     // FFT twiddles W_N^{j k1} as [k1][j] (k1 < N / 32, j < 32), from float64
     {
         const int MG = N / 32;
@@ -795,6 +806,26 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
     p->node_nblk[0] = nb[0];
     p->node_nblk[1] = nb[1];
     return e;
+}
+
+extern "C" int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta, const double *h_xi,
+                                int64_t *h_counts, float *h_rec, int *h_blk) {
+    if (!h_counts || !h_xi || n_xi < 1 || n_theta < 4 || !(beta > 0.0)) return FFB_ERR_ARG;
+    std::vector<float4> rec;
+    std::vector<int2> blk;
+    int nb[2] = {0, 0};
+    const int e = build_units(N, w, beta, n_xi, n_theta, h_xi, rec, blk, nb);
+    if (e) return e;
+    h_counts[0] = (int64_t)rec.size();
+    h_counts[1] = (int64_t)blk.size();
+    h_counts[2] = nb[0];
+    h_counts[3] = nb[1];
+    h_counts[4] = std::min(FUS_GU, FUS_WARPS * N / 4);
+    h_counts[5] = fus_mh(N, w);
+    h_counts[6] = fus_sld(N, w);
+    if (h_rec) std::memcpy(h_rec, rec.data(), sizeof(float4) * rec.size());
+    if (h_blk) std::memcpy(h_blk, blk.data(), sizeof(int2) * blk.size());
+    return FFB_OK;
 }
 
 int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,

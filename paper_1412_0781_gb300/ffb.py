@@ -63,6 +63,7 @@ SIGNATURES = {
     "ffb_group_sync": (_i, [_vp, _vp]),
     "ffb_group_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "ffb_group_tuning": (_i, [_vp, _i, _pi, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
+    "ffb_interp_units": (_i, [_i, _i, _d, _i, _i, _pd, ctypes.POINTER(ctypes.c_int64), _vp, _pi]),
     "ffb_strerror": (ctypes.c_char_p, [_i]),
 }
 
@@ -82,6 +83,26 @@ def load(path=LIB_PATH):
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def interp_units(N, w, beta, n_theta, xi):
+    """Host-only: the shared-memory grid path's interpolation table for radii
+    ``xi`` (see ffb_interp_units).  Returns (records float32 (blocks, 9, GU,
+    4), blocks int32 (blocks, 2), (blocks of half 0, blocks of half 1), MH,
+    SLD)."""
+    import numpy as np
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    cnt = (ctypes.c_int64 * 7)()
+    lib = load()
+    _check(lib.ffb_interp_units(int(N), int(w), float(beta), len(x), int(n_theta), x.ctypes.data_as(_pd), cnt,
+                                None, None), "ffb_interp_units")
+    rec = np.zeros(4 * cnt[0], dtype=np.float32)
+    blk = np.zeros(2 * cnt[1], dtype=np.int32)
+    _check(lib.ffb_interp_units(int(N), int(w), float(beta), len(x), int(n_theta), x.ctypes.data_as(_pd), cnt,
+                                rec.ctypes.data_as(ctypes.c_void_p), blk.ctypes.data_as(_pi)),
+           "ffb_interp_units")
+    gu = int(cnt[4])
+    return rec.reshape(int(cnt[1]), 9, gu, 4), blk.reshape(-1, 2), (int(cnt[2]), int(cnt[3])), int(cnt[5]), int(cnt[6])
 
 
 def cov_merge(p, states):
