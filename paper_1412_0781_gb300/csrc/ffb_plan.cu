@@ -2,6 +2,7 @@
 // Bessel zeros R_{k,q}, the sampling criterion (Eq. criterion1), the
 // Gauss-Legendre rule on [0, c], the radial table of Eq. a, and the NUFFT
 // tables (kernel deconvolution, FFT twiddles, polar node coordinates).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -176,6 +177,17 @@ static cudaError_t dalloc(T **p, size_t count) {
     return cudaMalloc((void **)p, count * sizeof(T));
 }
 
+// a temporary device buffer of plan construction, freed on every return path
+struct ScopedDev {
+    void *ptr = nullptr;
+    ScopedDev() = default;
+    ScopedDev(const ScopedDev &) = delete;
+    ScopedDev &operator=(const ScopedDev &) = delete;
+    ~ScopedDev() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
 static void free_plan(ffb_plan_t p) {
     ffb_tc_release(p);
     void *ptrs[] = {p->d_zeros, p->d_xi, p->d_wq, p->d_B64, p->d_Bf, p->d_p, p->d_off,
@@ -206,10 +218,11 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     const int kcand = (int)floor(X) + 2;
     const int qcap = (int)floor(X / M_PI) + 4;
     const double step = 0.25;
-    double *d_z = nullptr;
-    int *d_cnt = nullptr;
-    CK(cudaMalloc(&d_z, sizeof(double) * (size_t)kcand * qcap));
-    CK(cudaMalloc(&d_cnt, sizeof(int) * kcand));
+    ScopedDev tz, tc;
+    CK(cudaMalloc(&tz.ptr, sizeof(double) * (size_t)kcand * qcap));
+    CK(cudaMalloc(&tc.ptr, sizeof(int) * kcand));
+    double *d_z = (double *)tz.ptr;
+    int *d_cnt = (int *)tc.ptr;
     int ngrid_max = (int)ceil((X + 2.0 * step) / step) + 2;
     size_t shm = sizeof(double) * (size_t)ngrid_max;
     if (shm > 48 * 1024) CK(cudaFuncSetAttribute(k_bessel_zeros, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -223,8 +236,6 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     int hstatus = 0;
     CK(cudaMemcpyAsync(&hstatus, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    cudaFree(d_z);
-    cudaFree(d_cnt);
     if (hstatus != 0) return hstatus;
     std::vector<double> zsel;
     std::vector<int> kof;
@@ -256,9 +267,10 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     p->cov_total = co;
 
     // ---- device copies of the selection ---------------------------------
-    int *d_kof = nullptr;
+    ScopedDev tk;
     CK(dalloc(&p->d_zeros, p->P));
-    CK(dalloc(&d_kof, p->P));
+    CK(cudaMalloc(&tk.ptr, sizeof(int) * (size_t)std::max(p->P, 1)));
+    int *d_kof = (int *)tk.ptr;
     CK(dalloc(&p->d_p, p->k_max + 1));
     CK(dalloc(&p->d_off, p->k_max + 1));
     CK(dalloc(&p->d_cov_off, p->k_max + 2));
@@ -287,9 +299,10 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     // ---- NUFFT kernel deconvolution ------------------------------------
     {
         const int ng = 256;
-        double *d_xg = nullptr, *d_wg = nullptr;
-        CK(dalloc(&d_xg, ng));
-        CK(dalloc(&d_wg, ng));
+        ScopedDev txg, twg;
+        CK(cudaMalloc(&txg.ptr, sizeof(double) * ng));
+        CK(cudaMalloc(&twg.ptr, sizeof(double) * ng));
+        double *d_xg = (double *)txg.ptr, *d_wg = (double *)twg.ptr;
         k_gauss_legendre<<<(ng + 127) / 128, 128, 0, s>>>(ng, 0.0, 0.5 * p->w, d_xg, d_wg);
         p->launches++;
         CK(dalloc(&p->d_corr, p->L));
@@ -298,8 +311,6 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
         p->launches++;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
-        cudaFree(d_xg);
-        cudaFree(d_wg);
     }
 
     // ---- FFT twiddles, polar node coordinates --------------------------
@@ -365,7 +376,6 @@ static int build_plan(ffb_plan_t p, cudaStream_t s) {
     CK(cudaMemsetAsync(p->d_acc, 0, sizeof(double) * p->cov_total, s));
     CK(cudaMemsetAsync(p->d_sum0, 0, sizeof(double) * p->p[0], s));
     CK(cudaStreamSynchronize(s));
-    cudaFree(d_kof);
     CK(cudaMemcpy(&hstatus, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     return hstatus;
 }
