@@ -81,6 +81,29 @@ def test_expand_tiny_config_matches_oracle(dev):
     assert np.all(a[:, :gp.p[0]].imag == 0.0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_odd_image_size_matches_oracle(dev, prec):
+    """Odd L (45: pixel indices -22..22, N = 90 = 2 3^2 5, n_theta = 180, a
+    mixed-radix FFT on both axes): the expansion and the adjoint against the
+    oracle."""
+    L, c, R = 45, 0.5, 22.5
+    imgs, _, _ = data.blob_stack(data.StackSpec(6, L, R, 6, (1.5, 4.0), 0.2, 20141209))
+    gp = Plan(L, c, R, eps=1e-6, precision=prec)
+    try:
+        op = fb.make_plan(L, c, R)
+        assert (gp.P, gp.n_xi, gp.n_theta, gp.N) == (op.P, op.n_xi, op.n_theta, 90)
+        a = as_complex(gp.expand(imgs.to(dev)))
+        assert rel(a, fb.expand(op, imgs.double().numpy())) <= TOL
+        rng = np.random.default_rng(45)
+        y = rng.standard_normal((3, gp.P)) + 1j * rng.standard_normal((3, gp.P))
+        y = y.astype(np.complex64).astype(np.complex128)
+        yd = torch.view_as_real(torch.from_numpy(y.astype(np.complex64))).contiguous().to(dev)
+        g = gp.expand_adjoint(yd).double().cpu().numpy()
+        assert rel(g, fb.adjoint(op, y)) <= TOL
+    finally:
+        gp.close()
+
+
 def test_expand_ragged_chunks_and_independence(dev):
     """n spans several internal chunks plus a ragged tail; each image's
     coefficients do not depend on which chunk it fell in."""
