@@ -479,3 +479,227 @@ def test_invariant_features_under_rotation_and_reflection():
     pwf, bsf = fb.invariant_features(plan, af, mean0, vecs, pairs, triples)
     assert np.max(np.abs(pwf - pw)) <= 1e-10 * np.max(np.abs(pw))
     assert np.max(np.abs(bsf - np.conj(bs))) <= 1e-10 * np.max(np.abs(bs))
+
+
+# --- radial eigenfunctions, selection and filtering (Eqs. sPCArad, sPCAcoeff,
+# --- compselect; Sec. V): pins that do not pass through the oracle's formulas
+def test_radial_eigenfunctions_of_identity_are_the_basis_radial_parts():
+    """With U^(k) = I the radial eigenfunctions are the radial parts of the
+    Fourier-Bessel basis itself, N_{k,q} J_k(R_{k,q} xi / c) with
+    N_{k,q} = 1 / (c sqrt(pi) |J_{k+1}(R_{k,q})|) (Sec. II-A), evaluated here
+    with SciPy's Bessel functions and zeros at the Gauss-Legendre nodes of
+    numpy.  A quadrature factor xi_j w_j left in, or a wrong normalisation,
+    fails this."""
+    L, c, R = 32, 0.5, 16.0
+    plan = fb.make_plan(L, c, R)
+    xi, _ = np.polynomial.legendre.leggauss(plan.n_xi)
+    xi = 0.5 * c * (xi + 1.0)
+    f = fb.radial_eigenfunctions(plan, [np.eye(pk) for pk in plan.p])
+    for k, pk in enumerate(plan.p):
+        z = sp.jn_zeros(k, pk)
+        ref = sp.jv(k, z[None, :] * xi[:, None] / c) / (c * math.sqrt(math.pi) * np.abs(sp.jv(k + 1, z)))[None, :]
+        assert f[k].shape == (plan.n_xi, pk)
+        assert np.max(np.abs(f[k] - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_radial_eigenfunctions_are_orthonormal_on_the_disk():
+    """For any orthogonal U^(k) the functions f^{k,l}(xi) e^{ik theta} are
+    orthonormal on the disk of radius c: 2 pi int_0^c f f' xi dxi = delta
+    (orthonormality of the Fourier-Bessel basis, Fig. 2a).  The integral is
+    taken with 64 extra Gauss-Legendre nodes on [0, c] (numpy's rule), where
+    its error is at rounding level, so the check is against the mathematics,
+    not against the plan's own quadrature."""
+    L, c, R = 48, 0.5, 24.0
+    base = fb.make_plan(L, c, R)
+    fine = fb.Plan(L, c, R, n_xi=base.n_xi + 64)
+    t, wt = np.polynomial.legendre.leggauss(fine.n_xi)
+    xi, w = 0.5 * c * (t + 1.0), 0.5 * c * wt
+    rng = np.random.default_rng(31)
+    vecs = [np.linalg.qr(rng.standard_normal((pk, pk)))[0] for pk in fine.p]
+    f = fb.radial_eigenfunctions(fine, vecs)
+    for k in (0, 1, 5, len(fine.p) // 2, len(fine.p) - 1):
+        G = 2.0 * math.pi * (f[k] * (xi * w)[:, None]).T @ f[k]
+        assert np.max(np.abs(G - np.eye(G.shape[0]))) < 1e-11
+
+
+class _Sizes:
+    """Stand-in for a plan where a rule needs only the block sizes p_k."""
+
+    def __init__(self, p):
+        self.p = np.asarray(p, dtype=np.int64)
+
+
+def test_mp_selection_worked_example():
+    """Eq. compselect worked by hand for p = (25, 16, 9), n = 100, sigma^2 = 1:
+    gamma_0 = p_0/n = 0.25 gives the edge (1 + 0.5)^2 = 2.25; gamma_1 =
+    p_1/(2n) = 0.08 gives (1 + 0.28284)^2 = 1.64569; gamma_2 = 0.045 gives
+    (1 + 0.21213)^2 = 1.46926.  The eigenvalues below sit on both sides of
+    each edge and also on both sides of the edges that a wrong gamma
+    (p_0/(2n) for k = 0: 1.832; p_k/n for k > 0: 1.96 and 1.69) would give."""
+    lams = [np.array([3.0, 2.3, 2.2] + [1.0] * 22),
+            np.array([1.7, 1.6] + [0.9] * 14),
+            np.array([1.5, 1.45] + [0.8] * 7)]
+    hs = fb.select_filter(_Sizes([25, 16, 9]), lams, "mp_wiener", sigma2=1.0, n=100)
+    expect = [{0: 2.0 / 3.0, 1: 1.3 / 2.3}, {0: 0.7 / 1.7}, {0: 0.5 / 1.5}]
+    for k in range(3):
+        for l in range(lams[k].size):
+            assert hs[k][l] == pytest.approx(expect[k].get(l, 0.0), abs=1e-15)
+    hs = fb.select_filter(_Sizes([25, 16, 9]), lams, "mp_hard", sigma2=1.0, n=100)
+    for k in range(3):
+        assert sorted(np.flatnonzero(hs[k])) == sorted(expect[k])
+        assert np.all(hs[k][list(expect[k])] == 1.0)
+
+
+def test_topk_selection_worked_example():
+    """Ranking of (k, l) pairs by eigenvalue with ties to the smaller k, then
+    the smaller l, worked by hand on three blocks."""
+    lams = [np.array([5.0, 1.0]), np.array([7.0, 3.0, 3.0]), np.array([5.0, 0.5])]
+    order = [(1, 0), (0, 0), (2, 0), (1, 1), (1, 2), (0, 1), (2, 1)]
+    for K in range(len(order) + 1):
+        hs = fb.select_filter(_Sizes([2, 3, 2]), lams, "topk", K=K)
+        kept = {(k, l) for k in range(3) for l in range(lams[k].size) if hs[k][l] == 1.0}
+        assert kept == set(order[:K])
+        assert sum(int(np.count_nonzero(h)) for h in hs) == K
+
+
+def test_mp_selection_keeps_exactly_the_planted_components():
+    """Spiked white-noise model (Sec. V): coefficients of white noise of
+    variance sigma^2 (real for k = 0, complex with E|a|^2 = sigma^2 for k > 0)
+    plus rank-one signals planted in three blocks.  The noise eigenvalues stay
+    below the Marchenko-Pastur edge and the spikes lie far above it, so the
+    selection must keep exactly the planted (k, l), and the Wiener gain must be
+    close to the population value s / (s + sigma^2)."""
+    p = [9, 12, 7, 5]
+    n, sigma2 = 6000, 1.5
+    rng = np.random.default_rng(37)
+    planted = {0: 2.0, 1: 3.0, 3: 1.5}
+    lams = []
+    for k, pk in enumerate(p):
+        if k == 0:
+            A = math.sqrt(sigma2) * rng.standard_normal((n, pk))
+        else:
+            A = math.sqrt(sigma2 / 2) * (rng.standard_normal((n, pk)) + 1j * rng.standard_normal((n, pk)))
+        if k in planted:
+            u = rng.standard_normal(pk)
+            u /= np.linalg.norm(u)
+            s = rng.standard_normal(n) if k == 0 else (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2)
+            A = A + math.sqrt(planted[k]) * s[:, None] * u[None, :]
+        C = (A.real.T @ A.real + A.imag.T @ A.imag) / n
+        lams.append(np.sort(np.linalg.eigvalsh(C))[::-1])
+    hs = fb.select_filter(_Sizes(p), lams, "mp_wiener", sigma2=sigma2, n=n)
+    for k in range(len(p)):
+        kept = list(np.flatnonzero(hs[k]))
+        assert kept == ([0] if k in planted else [])
+        if k in planted:
+            assert hs[k][0] == pytest.approx(planted[k] / (planted[k] + sigma2), abs=0.05)
+
+
+def _planted_coefficients(plan, n, rng, mean_scale=2.0):
+    a = rng.standard_normal((n, plan.P)) + 1j * rng.standard_normal((n, plan.P))
+    a[:, :plan.p[0]] = a[:, :plan.p[0]].real
+    m = mean_scale * rng.standard_normal(plan.p[0])
+    a[:, :plan.p[0]] += m[None, :]
+    return a, m
+
+
+def test_filter_with_signed_permutation_eigenvectors():
+    """Closed form of Eq. sPCAcoeff and the filter when every U^(k) is a signed
+    permutation (u_l = s_l e_{pi(l)}): the steerable coefficient c_{k,l} is
+    s_l (a - m)_{pi(l)}, and the filtered coefficient q is
+    h_{pi^-1(q)} (a - m)_q + m_q, whatever the signs.  The k = 0 mean m is
+    nonzero and the gains are distinct and not 0 or 1."""
+    plan = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(41)
+    a, m = _planted_coefficients(plan, 7, rng)
+    vecs, perms, signs, hs = [], [], [], []
+    for pk in plan.p:
+        pi = rng.permutation(pk)
+        s = rng.choice([-1.0, 1.0], pk)
+        U = np.zeros((pk, pk))
+        U[pi, np.arange(pk)] = s
+        vecs.append(U)
+        perms.append(pi)
+        signs.append(s)
+        hs.append(rng.uniform(0.1, 0.9, pk))
+    cs = fb.steerable_coefficients(plan, a, m, vecs)
+    out = fb.filter_coefficients(plan, a, m, vecs, hs)
+    for k, (o, pk) in enumerate(zip(plan.offset, plan.p)):
+        x = a[:, o:o + pk] - (m[None, :] if k == 0 else 0.0)
+        assert np.allclose(cs[k], signs[k][None, :] * x[:, perms[k]], rtol=0, atol=1e-14)
+        inv = np.argsort(perms[k])
+        ref = hs[k][inv][None, :] * x + (m[None, :] if k == 0 else 0.0)
+        assert np.allclose(out[:, o:o + pk], ref, rtol=0, atol=1e-13)
+
+
+def test_filter_against_dense_operator_on_the_full_coefficient_vector():
+    """Brute force over the full coefficient vector a_{k,q}, k = -k_max..k_max
+    (a_{-k,q} = conj a_{k,q} for a real image): one dense matrix
+    F = blockdiag_k U^(|k|) diag(h^(|k|)) U^(|k|)T acting on a - m, plus m,
+    where m is the k = 0 mean.  The +k part must equal the oracle's filtered
+    coefficients and the -k part their conjugate (the filtered image stays
+    real).  Eigenvectors are random orthogonal, gains random in (0, 1)."""
+    import scipy.linalg as sla
+    plan = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(43)
+    a, m = _planted_coefficients(plan, 5, rng)
+    vecs = [np.linalg.qr(rng.standard_normal((pk, pk)))[0] for pk in plan.p]
+    hs = [rng.uniform(0.0, 1.0, pk) for pk in plan.p]
+    K = len(plan.p) - 1
+    ks = list(range(-K, K + 1))
+    blocks = [vecs[abs(k)] @ np.diag(hs[abs(k)]) @ vecs[abs(k)].T for k in ks]
+    F = sla.block_diag(*blocks)
+    full = np.concatenate([np.conj(a[:, plan.offset[-k]:plan.offset[-k] + plan.p[-k]]) if k < 0
+                           else a[:, plan.offset[k]:plan.offset[k] + plan.p[k]] for k in ks], axis=1)
+    mfull = np.zeros(full.shape[1])
+    z = int(sum(plan.p[abs(k)] for k in ks if k < 0))
+    mfull[z:z + plan.p[0]] = m
+    den = (full - mfull[None, :]) @ F.T + mfull[None, :]
+    out = fb.filter_coefficients(plan, a, m, vecs, hs)
+    pos, neg = den[:, z:], den[:, :z]
+    assert np.max(np.abs(pos - out)) <= 1e-13 * np.max(np.abs(out))
+    for k in range(1, K + 1):
+        o = plan.offset[k]
+        start = z - int(sum(plan.p[1:k + 1]))
+        assert np.max(np.abs(neg[:, start:start + plan.p[k]] - np.conj(out[:, o:o + plan.p[k]]))) < 1e-13
+
+
+def test_filter_zero_gain_returns_the_mean_and_unit_gain_the_input():
+    """h = 0 removes every component: the result is the k = 0 mean and zero
+    for k > 0.  h = 1 keeps all of them: the result is the input itself (the
+    mean is removed and added back).  Both with a nonzero mean."""
+    plan = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(47)
+    a, m = _planted_coefficients(plan, 6, rng, mean_scale=5.0)
+    vecs = [np.linalg.qr(rng.standard_normal((pk, pk)))[0] for pk in plan.p]
+    zero = fb.filter_coefficients(plan, a, m, vecs, [np.zeros(pk) for pk in plan.p])
+    assert np.max(np.abs(zero[:, :plan.p[0]] - m[None, :])) < 1e-14
+    assert np.max(np.abs(zero[:, plan.p[0]:])) == 0.0
+    one = fb.filter_coefficients(plan, a, m, vecs, [np.ones(pk) for pk in plan.p])
+    assert np.max(np.abs(one - a)) < 1e-13 * np.max(np.abs(a))
+
+
+def test_steerable_coefficients_recover_planted_components():
+    """Images built as a = m + sum_l t_{i,l} u_l in each block (u_l orthonormal,
+    m the k = 0 mean) have steerable coefficients exactly t (Eq. sPCAcoeff
+    with the k = 0 centring of Alg. 2 step 1); the covariance of the same
+    stack, built with the oracle's own mean, reproduces m."""
+    plan = fb.make_plan(16, 0.5, 8.0)
+    rng = np.random.default_rng(53)
+    n = 40
+    m = 3.0 * rng.standard_normal(plan.p[0])
+    vecs = [np.linalg.qr(rng.standard_normal((pk, pk)))[0] for pk in plan.p]
+    a = np.zeros((n, plan.P), complex)
+    ts = []
+    for k, (o, pk) in enumerate(zip(plan.offset, plan.p)):
+        t = rng.standard_normal((n, pk))
+        if k == 0:
+            t -= t.mean(axis=0)            # the planted components have zero mean
+        else:
+            t = t + 1j * rng.standard_normal((n, pk))
+        ts.append(t)
+        a[:, o:o + pk] = t @ vecs[k].T + (m[None, :] if k == 0 else 0.0)
+    mean0, _ = fb.covariance(plan, a)
+    assert np.max(np.abs(mean0 - m)) < 1e-13 * np.max(np.abs(m))
+    cs = fb.steerable_coefficients(plan, a, mean0, vecs)
+    for k in range(len(plan.p)):
+        assert np.max(np.abs(cs[k] - ts[k])) < 1e-12
