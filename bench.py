@@ -100,44 +100,67 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work per image (flops) of each kernel class, and its roofline
 # ---------------------------------------------------------------------------
-def algorithmic_flops(plan):
-    """Algorithmic flops per image of each kernel class (5 n log2 n per
-    complex FFT of length n; 2 flop per real multiply-add)."""
-    n_xi, nth, w, N, L = plan.n_xi, plan.n_theta, plan.w, plan.N, plan.L
-    pts = n_xi * (nth // 2)
-    fftN = 5 * N * math.log2(N)
-    ring = n_xi * 5 * nth * math.log2(nth)
-    interp = pts * w * w * 4
-    rows = (L / 2) * fftN
-    cols = (N / 2 + 1) * fftN
-    sum_p2_sym = sum(pk * (pk + 1) // 2 for pk in plan.p)
+def algorithmic_flops(plan, eps=EPS):
+    """Algorithmic flops per image of each kernel class: the work the method
+    needs, counted as the scope table of the hot path counts it (5 n log2 n
+    per complex FFT of length n, half of it for a real-input or Hermitian
+    transform; 2 flop per real multiply-add).
+
+    * interpolation: n_xi * n_theta/2 half-polar nodes x w_a^2 taps x 5 flop
+      (4 for the complex value times a real weight, 1 for the separable weight
+      product), w_a = ceil(log10(1/eps)) + 1 the width the accuracy needs
+      (the kernel runs w_a + 1 = 8 taps, see ``executed_flops``);
+    * oversampled 2-D FFT: real input, half of whose rows are zero padding:
+      2.5 N^2 log2(N^2) / 2;
+    * ring DFT: each ring is Hermitian (F(theta + pi) = conj F(theta)), so a
+      real-input count 2.5 n_theta log2 n_theta per ring;
+    * radial quadrature: 4 P n_xi (complex vector times real matrix);
+    * covariance: 2 sum_k p_k^2 (real SYRK of the Re and Im parts, symmetric
+      half)."""
+    n_xi, nth, N = plan.n_xi, plan.n_theta, plan.N
+    w_a = math.ceil(math.log10(1.0 / eps) - 1e-12) + 1
+    interp = n_xi * (nth // 2) * w_a * w_a * 5
+    fft2 = 2.5 * N * N * math.log2(N * N) / 2
+    ring = n_xi * 2.5 * nth * math.log2(nth)
     return {
-        "rows_fft": rows,
-        "cols_fft": cols,
-        "interp_ring": interp + ring,          # separate-kernel path
-        "grid_interp": rows + cols + interp,   # shared-memory grid path
+        "interp_ring": fft2 + interp + ring,   # separate-kernel path (rows, cols, interp + ring kernels)
+        "rows_fft": fft2 / 2,                  # L real rows of length N: half of the 2-D count
+        "cols_fft": fft2 / 2,
+        "grid_interp": fft2 + interp,          # shared-memory grid path
         "ring_fft": ring,
         "bessel": 4.0 * plan.P * n_xi,
-        "covariance": 4.0 * sum_p2_sym,
+        "covariance": 2.0 * sum(pk * pk for pk in plan.p),
     }
+
+
+def executed_flops(plan):
+    """Flops per image that the kernels execute (context for the
+    algorithmic counts above): w = plan.w taps of 4 flop per half-polar node,
+    complex FFTs of every row pair and of the N/2 + 1 column half, full
+    complex ring FFTs of length n_theta."""
+    n_xi, nth, w, N, L = plan.n_xi, plan.n_theta, plan.w, plan.N, plan.L
+    fftN = 5 * N * math.log2(N)
+    return {"grid_interp": (L / 2) * fftN + (N / 2 + 1) * fftN + n_xi * (nth // 2) * w * w * 4,
+            "ring_fft": n_xi * 5 * nth * math.log2(nth)}
 
 
 PROF_STRIDE = 32   # kernel timing: every 32nd launch of each kernel class
 POST_N = 20000     # images for the a8-a10 timings after the step
 
 
-def hbm_floor():
+def hbm_floor(plan):
     """images/s if only the image in (L^2 float32) and the coefficients out
     (P complex float32) crossed HBM, at the measured copy bandwidth."""
     try:
         gbs = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, KeyError, ValueError):
         gbs = 6800.0
-    return gbs * 1e9 / (128 * 128 * 4 + 4848 * 8)
+    return gbs * 1e9 / (plan.L * plan.L * 4 + plan.P * 8)
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (profiles/k_grid_interp_half_L128.md: 152-image launch), valid only
+# capture of a 152-image launch (the committed profile of the grid kernel at
+# L = 128), valid only
 # while the kernel's sources are byte-identical to the profiled ones (the
 # kernel's file from its top through the kernel, i.e. its macros, device
 # helpers and body, and the register-FFT header; from ffb_internal.cuh it uses
@@ -197,9 +220,9 @@ def measured_tensor_peak(precision):
     return bf16, src
 
 
-def fp32_peak_tflops(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sms, sm_mhz):
+    """SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -335,14 +358,19 @@ def run_ours(args):
     prof = r["prof"]
     dom = max(prof, key=lambda c: prof[c][0])
     dom_ms, dom_calls = prof[dom]
-    sm_mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
     share = {c: round(v[0] / sum(x[0] for x in prof.values()), 4) for c, v in prof.items()}
     imgs_per_launch = (n * args.steps) / dom_calls if dom_calls else 0
     achieved = flops.get(dom, 0.0) * imgs_per_launch / (dom_ms / dom_calls / 1e3) / 1e12 if dom_calls else 0.0
-    peak = fp32_peak_tflops(2070.0)
+    peak = fp32_peak_tflops(sms, max_mhz)
+    exe = executed_flops(plan)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(dom, imgs_per_launch),
-                "peak_note": "FP32 FFMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, max clock)",
+                "algorithmic_mflop_per_image": flops.get(dom, 0.0) / 1e6,
+                "executed_mflop_per_image": exe.get(dom, 0.0) / 1e6,
+                "peak_note": "FP32 FFMA peak %d SMs x 128 lanes x 2 flop x %.0f MHz (derived, max clock)" % (
+                    sms, max_mhz),
                 "kernel_ms_per_launch": dom_ms / dom_calls, "images_per_launch": imgs_per_launch,
                 "kernel_timing": "CUDA events around every %dth launch of each kernel in the timed region" % PROF_STRIDE,
                 "share": share}
@@ -353,7 +381,7 @@ def run_ours(args):
     floor = peak * 1e12 / alu_flops
     roofline["step"] = {"bound": "alu", "floor_images_per_s": floor, "frac": value / floor,
                         "note": "a1-a4 FP32 work %.2f MFLOP/image at the FFMA peak; HBM floor %.1f M images/s" % (
-                            alu_flops / 1e6, hbm_floor() / 1e6)}
+                            alu_flops / 1e6, hbm_floor(plan) / 1e6)}
 
     # a8-a10 after the timed step (reported beside the metric, not part of
     # it): the eigendecomposition of the step's covariance, MP-Wiener
@@ -497,11 +525,12 @@ def run_ours(args):
                 pts = plan.n_xi * (plan.n_theta // 2)
                 l1_bytes = pts * (36 * 8 + 72)
                 l1_rate = l1_bytes * n * args.steps / (ms_c / 1e3) / 1e12
-                l1_peak = 152 * 128 * 2.070e9 / 1e12
+                l1_peak = sms * 128 * max_mhz * 1e6 / 1e12
                 stages[c]["l1"] = {"achieved": l1_rate, "peak": l1_peak, "unit": "TB/s", "frac": l1_rate / l1_peak,
                                    "bytes_per_image": l1_bytes,
                                    "note": "interpolation gathers + unit records through L1 / shared memory; peak "
-                                           "152 SMs x 128 B/clk x 2070 MHz (derived); the FFT phases add more"}
+                                           "%d SMs x 128 B/clk x %.0f MHz (derived); the FFT phases add more" % (
+                                               sms, max_mhz)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -141,6 +141,21 @@ int ffb_plan_tables(ffb_plan_t plan, double *h_zeros, double *h_xi, double *h_w,
 /* Changes the arithmetic of the dense contractions (ffb_precision). */
 int ffb_set_precision(ffb_plan_t plan, int precision);
 
+/* ffb_set_wait_budget -- the bound, in SM clock cycles, of the waits between
+ * the pipeline roles of the tensor-core kernels of this plan (the TMA
+ * producer, the MMA issuer and the epilogue of the radial quadrature; the
+ * tile buffers and the final accumulator of the covariance).  The paper has
+ * no counterpart: the default (4e9 cycles, about 2 s) only stops a wait
+ * that could otherwise spin forever.  A wait that runs out latches
+ * FFB_ERR_TIMEOUT, which the next synchronising call returns (and clears);
+ * the kernel then waits, with the default budget whatever this setting, for
+ * the copies and MMAs it has already issued, releases its tensor memory and
+ * returns, so the context stays usable; the results of that call are
+ * undefined.  Meant for tests of that error path: cycles = 0 makes every
+ * such wait give up at once.  cycles < 0 restores the default.  FFB_ERR_ARG
+ * for a null plan. */
+int ffb_set_wait_budget(ffb_plan_t plan, long long cycles);
+
 /* ffb_polar -- Eq. nufft at the polar nodes with theta_l in [0, pi):
  * d_F[n][n_xi][n_theta/2][2] (interleaved complex, float32); the other half
  * of every ring is the complex conjugate (real images).  Exposes steps

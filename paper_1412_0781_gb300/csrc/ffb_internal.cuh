@@ -30,6 +30,11 @@ struct ProfEv {
     int cls;
 };
 
+// Default bound, in SM clock cycles, of every device-side wait of the
+// tensor-core kernels (~2 s at 2 GHz); a wait that runs out latches
+// FFB_ERR_TIMEOUT instead of spinning forever.
+#define FFB_WAIT_BUDGET (4000000000LL)
+
 struct ffb_plan_s {
     // problem
     int L, off;          // image size, pixel index offset (i = a - off)
@@ -97,6 +102,10 @@ struct ffb_plan_s {
     int eig_ready = 0;             // d_evals / d_evecs hold eigenpairs
     // status word written by kernels (first nonzero error wins)
     int *d_status = nullptr;
+    // clock-cycle budget of the waits between the pipeline roles of the
+    // tensor-core kernels (ffb_set_wait_budget); the drains of copies and
+    // MMAs already issued always keep FFB_WAIT_BUDGET
+    long long wait_budget = FFB_WAIT_BUDGET;
     int64_t launches = 0;
     // tensor-core operand tables and TMA descriptors (ffb_tc.cu)
     void *tc = nullptr;
@@ -403,7 +412,8 @@ void ffb_cov_stack(ffb_plan_t p, const float *d_coef, int64_t n, bool tc, CovSta
 // one CTA per SM (tensor cores) or a full wave (FP32)
 int ffb_launch_cov_group(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s);
 int ffb_cov_grid_default(int precision);
-int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s);
+int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s,
+                            long long wait_budget = FFB_WAIT_BUDGET);
 int ffb_expand_on(ffb_plan_t plan, const float *d_images, int64_t n, float *d_coef, cudaStream_t s);
 int ffb_launch_adjoint(ffb_plan_t plan, const float *d_coef, int64_t n, float *d_images,
                        cudaStream_t s);

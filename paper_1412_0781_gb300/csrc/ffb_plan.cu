@@ -508,6 +508,12 @@ extern "C" int ffb_set_precision(ffb_plan_t p, int precision) {
     return FFB_OK;
 }
 
+extern "C" int ffb_set_wait_budget(ffb_plan_t p, long long cycles) {
+    if (!p) return FFB_ERR_ARG;
+    p->wait_budget = (cycles < 0) ? FFB_WAIT_BUDGET : cycles;
+    return FFB_OK;
+}
+
 extern "C" int64_t ffb_launch_count(ffb_plan_t p) { return p ? p->launches : 0; }
 
 extern "C" const char *ffb_strerror(int status) {

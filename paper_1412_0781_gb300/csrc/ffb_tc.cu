@@ -22,7 +22,9 @@
 //   BF16    A_hi B_hi with bf16 operands
 //   BF16X3  A_hi B_hi + A_hi B_lo + A_lo B_hi, hi = bf16(x), lo = bf16(x - hi)
 // Every wait is bounded by a clock budget; a timeout latches FFB_ERR_TIMEOUT,
-// waits (bounded) for in-flight copies, frees TMEM and returns.
+// waits (bounded, with the full default budget) for the copies and MMAs it
+// has issued, frees TMEM and returns.  The waits between the pipeline roles
+// take the plan's budget `wb` (the default unless a test shortens it).
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
@@ -36,7 +38,7 @@
 // and the polar buffer then exceed L2)
 #define FFB_PLANE_BUDGET_MB 128
 
-#define TC_BUDGET (4000000000LL)  // ~2 s at 2 GHz
+#define TC_BUDGET FFB_WAIT_BUDGET   // drains of issued copies and MMAs
 
 // ---------------------------------------------------------------------------
 // operand preparation
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(32 * TCB_WARPS)
 k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
             const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int ld,
             int nimg, const int *__restrict__ pk_, const int *__restrict__ off_, int P, float *__restrict__ coef,
-            int BNmax, int acc_cols, int nst, int nM, int nitems, int *status) {
+            int BNmax, int acc_cols, int nst, int nM, int nitems, int *status, long long wb) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     constexpr int ES = (KIND == 0) ? 4 : 2;
@@ -148,12 +150,12 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             pdl_wait();   // the operand planes come from the previous kernels
             int64_t g = 0;
             bool ok = true;
-            for (int it = 0; it < myitems && ok; ++it) {
+            for (int it = 0; it < myitems && ok && *(volatile int *)okflag; ++it) {
                 const int item = blockIdx.x + it * gridDim.x;
                 const int k = item / nM, m = item - k * nM;
                 for (int ch = 0; ch < NCH; ++ch, ++g) {
                     const int si = (int)(g % nst);
-                    if (g >= nst && !tc::mbar_wait(&empty[si], (uint32_t)(((g / nst) - 1) & 1), TC_BUDGET)) {
+                    if (g >= nst && !tc::mbar_wait(&empty[si], (uint32_t)(((g / nst) - 1) & 1), wb)) {
                         ok = false;
                         break;
                     }
@@ -186,7 +188,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                 const int BN = max(16, (pk + 15) & ~15);
                 const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
                 const int a = it & 1;
-                if (it >= 2 && !tc::mbar_wait(&acce[a], (uint32_t)(((it >> 1) - 1) & 1), TC_BUDGET)) {
+                if (it >= 2 && !tc::mbar_wait(&acce[a], (uint32_t)(((it >> 1) - 1) & 1), wb)) {
                     ok = false;
                     break;
                 }
@@ -194,7 +196,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                 const uint32_t dt = tbase + (uint32_t)(a * acc_cols);
                 for (int ch = 0; ch < NCH; ++ch, ++g) {
                     const int si = (int)(g % nst);
-                    if (!tc::mbar_wait(&full[si], (uint32_t)((g / nst) & 1), TC_BUDGET)) {
+                    if (!tc::mbar_wait(&full[si], (uint32_t)((g / nst) & 1), wb)) {
                         ok = false;
                         break;
                     }
@@ -240,9 +242,9 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             const int a = it & 1;
             // after a failure elsewhere, stop waiting long (the loop count stays
             // the same for all epilogue warps: they meet at named barriers)
-            const long long budget = (*(volatile int *)okflag) ? TC_BUDGET : 0;
-            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), budget);
-            if (!ok && budget) {
+            const bool live = *(volatile int *)okflag != 0;
+            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), live ? wb : 0);
+            if (!ok && live) {
                 ffb_flag(status, FFB_ERR_TIMEOUT);
                 atomicExch(okflag, 0);
             }
@@ -481,7 +483,7 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     const int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD>, t->mA0, t->mA1, t->mB0,
                                                     t->mB1, t->ld, nimg, (const int *)p->d_p, (const int *)p->d_off,
                                                     p->P, d_coef_chunk, t->BN, t->tmem_cols, nst, nM, nitems,
-                                                    p->d_status));
+                                                    p->d_status, p->wait_budget));
     p->launches++;
     return e;
 }
@@ -542,7 +544,7 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
 
 template <int KIND, int NP>
 __global__ void __launch_bounds__(COV_NT, 1)
-k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
+k_tc_cov(const __grid_constant__ CovGroup g, int *status, long long wb) {
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per 128-byte chunk
     constexpr int KT = 2 * COV_TI;              // K entries per tile
@@ -578,6 +580,7 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
     tc::fence_after_sync();
     const uint32_t tbase = *slot;
     int64_t gt = 0;   // tiles committed by this CTA: buffer gt & 1, mbarrier phase (gt >> 1) & 1
+    int64_t last_commit = -1;   // thread 0: the tile of the newest commit
 
     for (int64_t item = blockIdx.x; item < g.nitems && *okflag; item += gridDim.x) {
         const CovStack &S = g.st[cov_stack_of(g, item)];
@@ -630,15 +633,14 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
         float s0acc[COV_PF];
 #pragma unroll
         for (int u = 0; u < COV_PF; ++u) s0acc[u] = 0.f;
-        for (int t = 0; t < ntiles && *okflag; ++t, ++gt) {
+        for (int t = 0; t < ntiles; ++t, ++gt) {
             const int buf = (int)(gt & 1);
             uint8_t *B0 = sm + buf * BUF_BYTES;
-            if (gt >= 2) {
-                if (!tc::mbar_wait(&bars[buf], (uint32_t)(((gt - 2) >> 1) & 1), TC_BUDGET)) {
-                    ffb_flag(status, FFB_ERR_TIMEOUT);
-                    atomicExch(okflag, 0);
-                }
-            }
+            // buffer buf is free once the MMAs of tile gt - 2 are done.  A wait
+            // that ran out is voted on at the tile's barrier below, so that the
+            // whole CTA leaves the loop together (the tile staged meanwhile may
+            // be garbage; no MMA reads it)
+            const bool fail = gt >= 2 && !tc::mbar_wait(&bars[buf], (uint32_t)(((gt - 2) >> 1) & 1), wb);
             issue_tile(t + COV_RS - 1);               // COV_RS - 1 tiles stay in flight
             tc::cp_async_wait<COV_RS - 1>();
             const float2 *st = raw + (size_t)(t % COV_RS) * COV_NT * COV_PF;
@@ -675,8 +677,14 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
                 }
             }
             tc::fence_async_shared();   // generic-proxy writes -> visible to the tensor core
-            __syncthreads();
-            if (threadIdx.x == 0 && *okflag) {
+            if (__syncthreads_or(fail)) {
+                if (threadIdx.x == 0) {
+                    ffb_flag(status, FFB_ERR_TIMEOUT);
+                    atomicExch(okflag, 0);
+                }
+                break;
+            }
+            if (threadIdx.x == 0) {
                 tc::fence_after_sync();
                 const uint32_t dt = tbase + (uint32_t)((t % COV_NACC) * 128);
 #pragma unroll
@@ -697,6 +705,7 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
                     }
                 }
                 tc::mma_commit(&bars[buf]);
+                last_commit = gt;
             }
         }
         tc::cp_async_wait<0>();   // no copy of this item outstanding (an early exit leaves some)
@@ -711,14 +720,14 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
         }
         __syncthreads();
         // the last commit covers every MMA issued before it
-        if (ntiles > 0 && *okflag) {
-            if (!tc::mbar_wait(&bars[(gt - 1) & 1], (uint32_t)(((gt - 1) >> 1) & 1), TC_BUDGET)) {
+        if (ntiles > 0 && threadIdx.x == 0 && *okflag) {
+            if (!tc::mbar_wait(&bars[(gt - 1) & 1], (uint32_t)(((gt - 1) >> 1) & 1), wb)) {
                 ffb_flag(status, FFB_ERR_TIMEOUT);
                 atomicExch(okflag, 0);
             }
         }
         tc::fence_after_sync();
-        __syncthreads();
+        __syncthreads();   // okflag is read below only after this barrier
         if (ntiles > 0 && *okflag) {
             // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows q); row q of
             // block k keeps columns [rk, rk + pk) of its own k.  The warp loads
@@ -767,6 +776,11 @@ k_tc_cov(const __grid_constant__ CovGroup g, int *status) {
         __syncthreads();
         tc::fence_after_sync();
     }
+    // after a timeout the per-item wait above is skipped: the newest commit
+    // covers every MMA this CTA issued, and they all finish before TMEM is
+    // released (full budget; on the normal path the phase is already done)
+    if (threadIdx.x == 0 && last_commit >= 0)
+        tc::mbar_wait(&bars[last_commit & 1], (uint32_t)((last_commit >> 1) & 1), TC_BUDGET);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, 512u);
@@ -789,7 +803,7 @@ bool ffb_tc_cov_supported(ffb_plan_t p) {
 }
 
 template <int KIND, int NP>
-static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t s) {
+static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t s, long long wb) {
     const size_t smem = tc_cov_smem(KIND == 0 ? FFB_TF32 : FFB_BF16);
     static int attr = 0;
     if (attr < (int)smem) {
@@ -802,20 +816,21 @@ static int launch_tc_cov(const CovGroup &g, int grid, int *status, cudaStream_t 
     // at most 128 images
     for (int i = 0; i < g.S; ++i)
         if (g.st[i].per > 128 * COV_NACC) return FFB_ERR_ARG;
-    k_tc_cov<KIND, NP><<<grid, COV_NT, smem, s>>>(g, status);
+    k_tc_cov<KIND, NP><<<grid, COV_NT, smem, s>>>(g, status, wb);
     return ffb_check_cuda(cudaGetLastError());
 }
 
-int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s) {
+int ffb_launch_cov_group_tc(int precision, const CovGroup &g, int grid, int *status, cudaStream_t s,
+                            long long wb) {
     if (g.nitems <= 0) return FFB_OK;
     if (grid <= 0) grid = ffb_cov_grid_default(precision);
     if ((int64_t)grid > g.nitems) grid = (int)g.nitems;
     int e;
     switch (precision) {
-        case FFB_TF32: e = launch_tc_cov<0, 1>(g, grid, status, s); break;
-        case FFB_TF32X3: e = launch_tc_cov<0, 2>(g, grid, status, s); break;
-        case FFB_BF16: e = launch_tc_cov<1, 1>(g, grid, status, s); break;
-        case FFB_BF16X3: e = launch_tc_cov<1, 2>(g, grid, status, s); break;
+        case FFB_TF32: e = launch_tc_cov<0, 1>(g, grid, status, s, wb); break;
+        case FFB_TF32X3: e = launch_tc_cov<0, 2>(g, grid, status, s, wb); break;
+        case FFB_BF16: e = launch_tc_cov<1, 1>(g, grid, status, s, wb); break;
+        case FFB_BF16X3: e = launch_tc_cov<1, 2>(g, grid, status, s, wb); break;
         default: return FFB_ERR_ARG;
     }
     return e;
@@ -829,7 +844,7 @@ int ffb_launch_cov_tc(ffb_plan_t p, const float *d_coef, int64_t n, cudaStream_t
     g.st[0].item0 = 0;
     g.nitems = (int64_t)g.st[0].nk * ((n + g.st[0].per - 1) / g.st[0].per);
     ProfScope ps(p, FFB_KC_COV, s);
-    const int e = ffb_launch_cov_group_tc(p->precision, g, 0, p->d_status, s);
+    const int e = ffb_launch_cov_group_tc(p->precision, g, 0, p->d_status, s, p->wait_budget);
     p->launches += 1;
     return e;
 }

@@ -40,8 +40,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Waits for the phase with the given parity; gives up after `budget` clock
-// cycles and returns false (the caller latches FFB_ERR_TIMEOUT).
+// cycles and returns false (the caller latches FFB_ERR_TIMEOUT).  A budget
+// of zero or less gives up at once, without looking at the barrier.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget) {
+    if (budget <= 0) return false;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > budget) return false;

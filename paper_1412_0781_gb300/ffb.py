@@ -31,6 +31,7 @@ SIGNATURES = {
     "ffb_plan_sizes": (_i, [_vp, _pi, _pi]),
     "ffb_plan_tables": (_i, [_vp, _pd, _pd, _pd, _pd]),
     "ffb_set_precision": (_i, [_vp, _i]),
+    "ffb_set_wait_budget": (_i, [_vp, ctypes.c_longlong]),
     "ffb_polar": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_polar_noalloc": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_expand": (_i, [_vp, _vp, _i64, _vp, _vp]),
@@ -199,6 +200,11 @@ class Plan:
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
         _check(load().ffb_set_precision(self._h, prec), "ffb_set_precision")
         self.precision = prec
+
+    def set_wait_budget(self, cycles=-1):
+        """Bound of the tensor-core kernels' inter-role waits in clock cycles
+        (tests of the timeout path); negative restores the default."""
+        _check(load().ffb_set_wait_budget(self._h, int(cycles)), "ffb_set_wait_budget")
 
     KERNEL_CLASSES = ["rows_fft", "cols_fft", "interp_ring", "bessel", "covariance", "cov_aux", "jacobi",
                       "adj_bessel", "adj_ring_spread", "adj_cols", "adj_rows", "filter", "setup",

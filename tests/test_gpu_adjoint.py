@@ -63,10 +63,11 @@ def test_adjoint_dot_product(dev, L, n):
 
 
 # --- adjoint / synthesis vs oracle -------------------------------------------
-@pytest.mark.parametrize("L", [32, 64, 128])
+@pytest.mark.parametrize("L", [32, 64, 128, 256])
 def test_adjoint_matches_oracle(dev, L):
     """L = 64 and 128 run the shared-memory spreading of the fused path's
-    plans (unit table, two CTAs per image); L = 32 the global one."""
+    plans (unit table, two CTAs per image); L = 32 and 256 the global one
+    (L = 256 is the differentiation workload's size)."""
     gp, op = gplan(L), fb.make_plan(L, 0.5, L / 2)
     rng = np.random.default_rng(L)
     m = 2 if L >= 128 else 4
@@ -222,3 +223,54 @@ def test_l256_top64_denoise_and_gradient(dev):
     assert rel(x.grad.double().cpu().numpy(), g.double().cpu().numpy()) <= TOL
     dn = gp.denoise(imgs[:256].contiguous(), mode="topk", K=64)
     assert torch.isfinite(dn).all()
+
+
+def test_l256_gradient_matches_oracle_maps(dev):
+    """The differentiation workload (L = 256, R = 128, n = 4096, top-64):
+    covariance and eigenpairs from the whole stack on the GPU, then the loss
+    ||denoised - clean||^2 + lam sum_{k,q} W |a_{k,q}|^2 on two images through
+    the autograd wrappers.  Its gradient is built independently from the FP64
+    oracle's exact maps with the GPU's eigenvectors, mean and gains held
+    fixed (they are detached in the wrappers):
+        a = T* x,  den = T W (M (a - m) + m),  r = 2 (den - clean),
+        grad = T (M W T* r + 2 lam W a),
+    with M = U diag(h) U^T (Eq. sPCAcoeff and the filter of Sec. V) and T the
+    adjoint of T* (Sec. II-B, Eq. transf)."""
+    spec = data.DIFF_L256
+    imgs, clean, _ = data.blob_stack(spec, device=dev)
+    gp = gplan(256)
+    gp.covariance(gp.expand(imgs), reset=True)
+    gp.eig()
+    mean, vecs, hs = _selected_filter(gp, "topk", K=64)
+    op = fb.make_plan(256, 0.5, 128.0)
+    lam = 0.05
+    W = op.weights_W()
+    Wt = torch.tensor(W, device=dev, dtype=torch.float32)
+    m = 2
+    x = imgs[:m].clone().requires_grad_(True)
+    a = fa.expand(x, gp)
+    den = fa.synthesize(fa.steerable_filter(a, gp), gp)
+    loss = ((den - clean[:m]) ** 2).sum() + lam * ((a ** 2).sum(-1) * Wt).sum()
+    loss.backward()
+    grad = x.grad.double().cpu().numpy()
+
+    x0 = imgs[:m].double().cpu().numpy()
+    c0 = clean[:m].double().cpu().numpy()
+    ao = fb.expand(op, x0)
+    den_o = fb.synthesize(op, fb.filter_coefficients(op, ao, mean, vecs, hs))
+    den_g = den.detach().double().cpu().numpy()
+    assert rel(den_g, den_o) <= TOL
+    zero_mean = np.zeros_like(mean)
+
+    def oracle_grad(r):
+        back = fb.filter_coefficients(op, W[None, :] * fb.expand(op, r), zero_mean, vecs, hs)
+        return fb.adjoint(op, back + 2.0 * lam * W[None, :] * ao)
+
+    # the backward maps on the cotangent the GPU's forward produced: the
+    # float32 gate of the scope (relative L2 <= 1e-5)
+    assert rel(grad, oracle_grad(2.0 * (den_g - c0))) <= TOL
+    # end to end, the oracle's own forward: r = 2 (den - clean) is a
+    # difference of close images, so the forward's relative error grows by
+    # ||den|| / ||den - clean|| in it
+    amp = np.linalg.norm(den_o) / np.linalg.norm(den_o - c0)
+    assert rel(grad, oracle_grad(2.0 * (den_o - c0))) <= TOL * max(1.0, amp)
