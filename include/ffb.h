@@ -27,6 +27,10 @@
  *   bounded wait that timed out, Jacobi not converged) are latched in the plan
  *   and returned by the next call that synchronises (ffb_cov_get, ffb_eig,
  *   ffb_sync).  No entry point aborts the process.
+ * - A plan belongs to the CUDA device that was current when ffb_plan built
+ *   it (its tables and scratch live there); every entry point that works on
+ *   a plan's device memory returns FFB_ERR_ARG while another device is
+ *   current.
  * - Every entry point returns an ffb_status; ffb_strerror() names it.
  */
 #ifndef FFB_H

@@ -22,6 +22,7 @@ static int read_status(ffb_plan_t p, cudaStream_t s) {
 }
 
 extern "C" int ffb_sync(ffb_plan_t p, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p) return FFB_ERR_ARG;
     return read_status(p, (cudaStream_t)stream);
 }
@@ -35,6 +36,7 @@ extern "C" int ffb_profile(ffb_plan_t p, int enable) {
 }
 
 extern "C" int ffb_profile_read(ffb_plan_t p, double *h_ms, int64_t *h_calls) {
+    FFB_PLAN_HERE(p);
     if (!p || !h_ms || !h_calls) return FFB_ERR_ARG;
     for (int c = 0; c < FFB_NKC; ++c) {
         h_ms[c] = 0.0;
@@ -60,6 +62,7 @@ extern "C" int ffb_profile_read(ffb_plan_t p, double *h_ms, int64_t *h_calls) {
 }
 
 extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *d_F, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_images || !d_F))) return FFB_ERR_ARG;
     if (n == 0) return FFB_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -113,11 +116,13 @@ int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef,
 }
 
 extern "C" int ffb_expand(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_images || !d_coef))) return FFB_ERR_ARG;
     return ffb_expand_on(p, d_images, n, d_coef, (cudaStream_t)stream);
 }
 
 extern "C" int ffb_covariance(ffb_plan_t p, const float *d_coef, int64_t n, int reset, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && !d_coef)) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (reset) {
@@ -137,6 +142,7 @@ extern "C" int ffb_covariance(ffb_plan_t p, const float *d_coef, int64_t n, int 
 }
 
 extern "C" int ffb_cov_get(ffb_plan_t p, double *d_mean0, double *d_C, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_acc <= 0) return FFB_ERR_STATE;
@@ -149,6 +155,7 @@ extern "C" int ffb_cov_get(ffb_plan_t p, double *d_mean0, double *d_C, void *str
 }
 
 extern "C" int ffb_eig(ffb_plan_t p, double *d_evals, double *d_evecs, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_acc <= 0) return FFB_ERR_STATE;
@@ -163,6 +170,7 @@ extern "C" int ffb_eig(ffb_plan_t p, double *d_evals, double *d_evecs, void *str
 }
 
 extern "C" int ffb_eig_blocks(ffb_plan_t p, const double *d_C, double *d_evals, double *d_evecs, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !d_C) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     CK(ffb_check_cuda(cudaMemcpyAsync(p->d_Cfin, d_C, sizeof(double) * p->cov_total, cudaMemcpyDeviceToDevice, s)));
@@ -176,6 +184,7 @@ extern "C" int ffb_eig_blocks(ffb_plan_t p, const double *d_C, double *d_evals, 
 }
 
 extern "C" int ffb_expand_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_images, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_coef || !d_images))) return FFB_ERR_ARG;
     if (n == 0) return FFB_OK;
     return ffb_launch_adjoint(p, d_coef, n, d_images, (cudaStream_t)stream);
@@ -218,6 +227,7 @@ static void select_gains(ffb_plan_t p, const std::vector<double> &ev, int mode, 
 }
 
 extern "C" int ffb_select(ffb_plan_t p, int mode, int K, double sigma2, int64_t n, double *h_gain, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p) return FFB_ERR_ARG;
     if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_MP_HARD) return FFB_ERR_ARG;
     if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
@@ -239,6 +249,7 @@ extern "C" int ffb_select(ffb_plan_t p, int mode, int K, double sigma2, int64_t 
 }
 
 extern "C" int ffb_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, int flags, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_coef_in || !d_coef_out)) || (flags & ~3)) return FFB_ERR_ARG;
     if (!p->selected) return FFB_ERR_STATE;
     if (n == 0) return FFB_OK;
@@ -246,6 +257,7 @@ extern "C" int ffb_filter(ffb_plan_t p, const float *d_coef_in, int64_t n, float
 }
 
 extern "C" int ffb_weight(ffb_plan_t p, const float *d_coef_in, int64_t n, float *d_coef_out, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_coef_in || !d_coef_out))) return FFB_ERR_ARG;
     if (n == 0) return FFB_OK;
     return ffb_launch_weight(p, d_coef_in, n, d_coef_out, (cudaStream_t)stream);
@@ -253,6 +265,7 @@ extern "C" int ffb_weight(ffb_plan_t p, const float *d_coef_in, int64_t n, float
 
 extern "C" int ffb_denoise(ffb_plan_t p, const float *d_images, int64_t n, int mode, int K, double sigma2,
                            float *d_out, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n <= 0 || !d_images || !d_out) return FFB_ERR_ARG;
     if (mode < FFB_DENOISE_TOPK || mode > FFB_DENOISE_MP_HARD) return FFB_ERR_ARG;
     if (mode == FFB_DENOISE_TOPK && K < 0) return FFB_ERR_ARG;
@@ -288,6 +301,7 @@ static int64_t state_len(const std::vector<int> &p) {
 }
 
 extern "C" int ffb_cov_export(ffb_plan_t p, double *h_state, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !h_state) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->n_acc <= 0) return FFB_ERR_STATE;
@@ -340,6 +354,7 @@ extern "C" int ffb_cov_merge(int k_max, const int *h_p, int nstates, const doubl
 // Loads pooled statistics into the plan's accumulator (shift = rounded mean),
 // after which ffb_cov_get / ffb_eig see the pooled covariance.
 extern "C" int ffb_cov_import(ffb_plan_t p, const double *h_state, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !h_state || !(h_state[0] >= 1.0)) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int p0 = p->p[0];

@@ -64,6 +64,7 @@ __global__ void k_eigenimages(int npairs, const int *__restrict__ pk_list, const
 }
 
 extern "C" int ffb_radial_eigenfunctions(ffb_plan_t p, double *d_f, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !d_f) return FFB_ERR_ARG;
     if (!p->eig_ready) return FFB_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -75,6 +76,7 @@ extern "C" int ffb_radial_eigenfunctions(ffb_plan_t p, double *d_f, void *stream
 
 extern "C" int ffb_eigenimages(ffb_plan_t p, int npairs, const int *h_k, const int *h_l, double *d_out,
                                void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || npairs < 0 || (npairs > 0 && (!h_k || !h_l || !d_out))) return FFB_ERR_ARG;
     if (!p->eig_ready) return FFB_ERR_STATE;
     if (npairs == 0) return FFB_OK;
@@ -152,6 +154,7 @@ __global__ void k_invariants(const float2 *__restrict__ c, int64_t n, int S, int
 
 extern "C" int ffb_invariants(ffb_plan_t p, const float *d_coef, int64_t n, int npow, const int *h_pairs,
                               float *d_pow, int nbis, const int *h_triples, float *d_bis, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !d_coef || n < 0 || npow < 0 || nbis < 0) return FFB_ERR_ARG;
     if ((npow > 0 && (!h_pairs || !d_pow)) || (nbis > 0 && (!h_triples || !d_bis))) return FFB_ERR_ARG;
     if (!p->eig_ready) return FFB_ERR_STATE;

@@ -116,6 +116,7 @@ static int cut(const std::vector<double> &v, const std::vector<double> &wt, doub
 
 extern "C" int ffb_estimate_support(ffb_plan_t p, const float *d_images, int64_t n, double frac, double sigma2,
                                     double *h_out, double *h_radvar, double *h_radpow, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !d_images || !h_out || n < 1 || !(frac > 0.0 && frac <= 1.0)) return FFB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int L = p->L, npix = L * L, nh = p->n_theta / 2, n_xi = p->n_xi;

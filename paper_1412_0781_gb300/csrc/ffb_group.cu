@@ -91,7 +91,7 @@ extern "C" int ffb_group_create(ffb_group_t *out, int S, const ffb_plan_t *plans
     if (!out || !plans || S < 1 || S > FFB_GROUP_MAX) return FFB_ERR_ARG;
     *out = nullptr;
     for (int i = 0; i < S; ++i) {
-        if (!plans[i]) return FFB_ERR_ARG;
+        FFB_PLAN_HERE(plans[i]);   // every member lives on the current device
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return FFB_ERR_ARG;   // a plan's scratch serves one stack
         if (plans[i]->precision != plans[0]->precision) return FFB_ERR_ARG;
@@ -332,6 +332,8 @@ static int make_key(ffb_group_t g, int mode, const float *const *images, const i
 
 extern "C" int ffb_group_expand_cov(ffb_group_t g, const float *const *h_images, const int64_t *h_n,
                                     float *const *h_coef, int reset, void *stream) {
+    if (!g) return FFB_ERR_ARG;
+    FFB_PLAN_HERE(g->plans[0]);
     Key k;
     CKG(make_key(g, 1, h_images, h_n, h_coef, reset, &k));
     return call(g, k, (cudaStream_t)stream);
@@ -339,6 +341,8 @@ extern "C" int ffb_group_expand_cov(ffb_group_t g, const float *const *h_images,
 
 extern "C" int ffb_group_covariance(ffb_group_t g, const float *const *h_coef, const int64_t *h_n, int reset,
                                     void *stream) {
+    if (!g) return FFB_ERR_ARG;
+    FFB_PLAN_HERE(g->plans[0]);
     Key k;
     CKG(make_key(g, 2, nullptr, h_n, const_cast<float *const *>(h_coef), reset, &k));
     return call(g, k, (cudaStream_t)stream);
@@ -346,6 +350,7 @@ extern "C" int ffb_group_covariance(ffb_group_t g, const float *const *h_coef, c
 
 extern "C" int ffb_group_sync(ffb_group_t g, void *stream) {
     if (!g) return FFB_ERR_ARG;
+    FFB_PLAN_HERE(g->plans[0]);
     cudaStream_t s = (cudaStream_t)stream;
     int st = 0;
     CKG(ffb_check_cuda(cudaMemcpyAsync(&st, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)));

@@ -106,6 +106,7 @@ struct ffb_plan_s {
     // tensor-core kernels (ffb_set_wait_budget); the drains of copies and
     // MMAs already issued always keep FFB_WAIT_BUDGET
     long long wait_budget = FFB_WAIT_BUDGET;
+    int device = -1;     // the CUDA device the plan's tables live on
     int64_t launches = 0;
     // tensor-core operand tables and TMA descriptors (ffb_tc.cu)
     void *tc = nullptr;
@@ -115,6 +116,16 @@ struct ffb_plan_s {
     std::vector<ProfEv> prof;
     int64_t prof_calls[16] = {};     // launches per class since profiling was enabled
 };
+
+// FFB_OK when `p` is a plan and the current device is the one it was built
+// on (its tables, scratch and the kernels' per-device state belong there);
+// FFB_ERR_ARG otherwise.
+int ffb_plan_here(ffb_plan_t p);
+#define FFB_PLAN_HERE(p)                      \
+    do {                                      \
+        const int _here = ffb_plan_here(p);   \
+        if (_here != FFB_OK) return _here;    \
+    } while (0)
 
 // Brackets one launch with events when profiling is on (host side).
 struct ProfScope {

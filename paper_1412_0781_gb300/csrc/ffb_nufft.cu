@@ -340,6 +340,7 @@ static int noalloc_smem(const void *fn, size_t bytes) {
 }
 
 extern "C" int ffb_polar_noalloc(ffb_plan_t p, const float *d_images, int64_t n, float *d_F, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || n < 0 || (n > 0 && (!d_images || !d_F))) return FFB_ERR_ARG;
     const int N = p->N, L = p->L, Nh = N / 2 + 1;
     const size_t h_bytes = (sizeof(float2) * (size_t)Nh * L + 255) / 256 * 256;

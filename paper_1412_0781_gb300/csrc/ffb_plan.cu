@@ -437,7 +437,8 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
         return FFB_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int st = ffb_check_cuda(cudaMalloc(&p->d_status, sizeof(int)));
+    int st = ffb_check_cuda(cudaGetDevice(&p->device));
+    if (st == FFB_OK) st = ffb_check_cuda(cudaMalloc(&p->d_status, sizeof(int)));
     if (st == FFB_OK) st = ffb_check_cuda(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     if (st == FFB_OK) st = build_plan(p, s);
     if (st == FFB_OK && p->precision != FFB_FP32 && !ffb_tc_supported(p)) st = FFB_ERR_UNSUPPORTED;
@@ -506,6 +507,16 @@ extern "C" int ffb_set_precision(ffb_plan_t p, int precision) {
         return FFB_ERR_UNSUPPORTED;
     }
     return FFB_OK;
+}
+
+int ffb_plan_here(ffb_plan_t p) {
+    if (!p) return FFB_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FFB_ERR_CUDA;
+    }
+    return dev == p->device ? FFB_OK : FFB_ERR_ARG;
 }
 
 extern "C" int ffb_set_wait_budget(ffb_plan_t p, long long cycles) {

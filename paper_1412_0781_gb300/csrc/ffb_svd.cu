@@ -171,6 +171,7 @@ __global__ void k_mean0_final(int p0, double n, double *__restrict__ mean) {
 }
 
 extern "C" int ffb_svd(ffb_plan_t p, const float *d_coef, int64_t n, double *d_evals, double *d_evecs, void *stream) {
+    FFB_PLAN_HERE(p);
     if (!p || !d_coef || n < 1) return FFB_ERR_ARG;
     if (p->pmax > TSQR_MB / 2) return FFB_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
