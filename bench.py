@@ -519,15 +519,21 @@ def run_ours(args):
             stages[c] = {"bound": "alu", "achieved": rate, "peak": peak, "unit": "TFLOP/s", "frac": rate / peak,
                          "ms_per_step": ms_c / args.steps}
             if c == "grid_interp" and plan.polar_variant > 0:
-                # what actually bounds it: the L1 / shared-memory pipe.  Per
-                # polar node, algorithmically: 36 complex grid gathers (one
-                # 8 x 9 window per node pair) and half a 144-byte unit record
-                pts = plan.n_xi * (plan.n_theta // 2)
-                l1_bytes = pts * (36 * 8 + 72)
+                # what the interpolation moves through the L1 / shared-memory
+                # pipe: per unit of the plan's table, the 9 x 9 union of
+                # complex grid values (81 gathers of 8 bytes) and its record
+                # (19 float4 = 304 bytes), counted from the table itself
+                from paper_1412_0781_gb300 import ffb as ffb_mod
+                import numpy as np
+                _, xi_t, _, _ = plan.tables()
+                rec, _, _, _, _, _ = ffb_mod.interp_units(plan.N, plan.w, 2.30 * plan.w, plan.n_theta, xi_t)
+                units = int(np.count_nonzero((rec[:, 18, :, 1].copy().view(np.uint32) & 0xFFFF) != 0xFFFF))
+                l1_bytes = units * (81 * 8 + 19 * 16)
                 l1_rate = l1_bytes * n * args.steps / (ms_c / 1e3) / 1e12
                 l1_peak = sms * 128 * max_mhz * 1e6 / 1e12
                 stages[c]["l1"] = {"achieved": l1_rate, "peak": l1_peak, "unit": "TB/s", "frac": l1_rate / l1_peak,
                                    "bytes_per_image": l1_bytes,
+                                   "units_per_image": units,
                                    "note": "interpolation gathers + unit records through L1 / shared memory; peak "
                                            "%d SMs x 128 B/clk x %.0f MHz (derived); the FFT phases add more" % (
                                                sms, max_mhz)}

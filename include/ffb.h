@@ -105,15 +105,20 @@ int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
  *   N in {128, 256}, w = 8 (FFB_ERR_UNSUPPORTED otherwise), beta > 0 (the
  *   plan uses 2.30 w), h_xi[n_xi] the radii on [0, c] (the plan's
  *   Gauss-Legendre nodes), n_theta even.
- * h_counts[7] (out): float4 records, blocks, blocks of half 0, blocks of
- *   half 1, units per block GU, half-grid size MH, its row pitch SLD.
- * h_rec (may be NULL: sizing call): float[4 h_counts[0]], per block 9 fields
- *   of GU float4 ([block][field][unit]): fields 0-1 the 8 row weights of node
- *   A, 2-3 those of node B, 4-5 A's column weights 0..7 over the unit's
- *   9-column union, 6-7 B's, field 8 = (B's column 8, bits of r0 | cu << 16
- *   with cu the union's first column, bits of the block-local node slots
- *   A | B << 16 as unsigned halves, B = 0xFFFF for a single node, A's column
- *   8); an empty unit has slots 0xFFFFFFFF.
+ * h_counts[9] (out): float4 records, blocks, blocks of half 0, blocks of
+ *   half 1, units per block GU, half-grid size MH, its row pitch SLD, fields
+ *   per unit record F (19), nodes per unit at most (at most 4).
+ * h_rec (may be NULL: sizing call): float[4 h_counts[0]], per block F fields
+ *   of GU float4 ([block][field][unit]).  A unit is up to four nodes whose
+ *   window origins lie in one 2 x 2 box, read from the 9 x 9 union of their
+ *   windows: field q < 9 holds the column weights of union column q, one per
+ *   node slot (x, y, z, w = slots 0..3); field 9 + r those of union row r;
+ *   field 18 = (bits of ru | cu << 16, the union's first row and column,
+ *   bits of slot0 | slot1 << 16, bits of slot2 | slot3 << 16, 0), the slots
+ *   being block-local node indices as unsigned halves, 0xFFFF for none.  A
+ *   node's weights are zero outside its own window (rows r0 - ru .. + 7,
+ *   columns c0 - cu .. + 7, each offset 0 or 1); an empty unit has slot0 =
+ *   0xFFFF.
  * h_blk (may be NULL): int[2 h_counts[1]], per block (first node t0, node
  *   count), nodes numbered t = j nl + (l - l0) within the half (nl nodes per
  *   ring of the half, l0 its first angle); half 0's blocks come first. */

@@ -28,21 +28,23 @@
 // transformed in phase 2).
 //
 // Node order in phase 3.  A node gathers the W x W window of S at
-// S[r0][c0] (W = 8).  Two nodes with the same r0 and window origins c0, c0 + d
-// (d in {0, 1}) form a unit: one thread reads the 8 x 9 union of their
-// windows once and forms both results, 36 gathers per node instead of 64
-// (phase 3 is bound by the shared-memory pipe).  One 8-byte load of a half
-// warp takes a single wavefront when the 16 unit origins r0 * SLD + c0 fall in
-// distinct 8-byte bank slots (the origin mod 16) or coincide, so the units are
-// ordered into half warps with distinct slots; a unit whose nodes share their
-// column origin (or a single node) may start its union one column to the
-// left, which the plan uses to even out the slots' unit counts.  Everything here depends on
-// the geometry alone and is built by the plan in float64
-// (ffb_fused_prepare): blocks of consecutive nodes t = j nl + l, at most
-// FUS_GU units each, and per unit the origin, both
-// nodes' 8 row weights and 9 column weights over the union (144 bytes, about
-// 2.6 MB at N = 256, read from L2 by every CTA).  The kernel stages a block's
-// results in shared memory and stores them in natural order.
+// S[r0][c0] (W = 8).  Up to four nodes whose window origins lie in one 2 x 2
+// box (r0 or r0 + 1, c0 or c0 + 1) form a unit: one thread reads the 9 x 9
+// union of their windows once and forms all their results, 81 gathers for
+// about 3.4 nodes instead of 64 per node (phase 3 is bound by the
+// shared-memory pipe).  One 8-byte load of a half warp takes a single
+// wavefront when the 16 union origins r0 * SLD + c0 fall in distinct 8-byte
+// bank slots (the origin mod 16), so the units are ordered into half warps
+// with distinct slots; a unit whose nodes all sit in the union's first
+// column (row) may start its union one column (row) earlier, which the plan
+// uses to even out the slots' unit counts.  Everything here depends on the
+// geometry alone and is built by the plan in float64 (ffb_fused_prepare):
+// blocks of consecutive nodes t = j nl + l, at most one unit per thread, and
+// per unit the origin, the node slots and every node's weights over the
+// union's 9 columns and 9 rows (zero outside its own window; 304 bytes per
+// unit, about 3 MB at N = 256, read from L2 by every CTA).  The kernel
+// stages a block's results in shared memory and stores them in natural
+// order.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -51,16 +53,23 @@
 
 #include "ffb_fft.cuh"
 
-#define FUS_WARPS 32                 // warps per CTA, each with an N-entry FFT buffer
+// 24 warps: 80 registers per thread hold a four-node unit's 36 column
+// weights and accumulators without spills (at 32 warps, 64 registers, they
+// spill; measured slower)
+#define FUS_WARPS 24                 // warps per CTA, each with an N-entry FFT buffer
 #define FUS_NT (32 * FUS_WARPS)      // threads per CTA
-#define FUS_GU 2048   // units per phase-3 block (at most; two per thread)
-#define FUS_REC 9     // float4 fields of a unit record
+#define FUS_GU FUS_NT  // units per phase-3 block (at most; one per thread)
+#define FUS_NU 4       // nodes per unit (at most)
+#define FUS_UW 9       // union side: W + 1
+#define FUS_REC 19     // float4 planes of a unit record: 9 column, 9 row, 1 meta
 
-// rows of the shared-memory grid block and its row pitch (complex entries):
-// MH (odd) columns hold the half plane, two more zero columns let a unit's
-// 9-column union start at the last window origin; the pitch stays odd
+// rows and columns of the shared-memory grid block: MH (odd) rows and
+// columns hold the half plane; one more zero row and two more zero columns
+// let a unit's 9 x 9 union start at the last window origin (its extra row or
+// column then carries zero weights); the row pitch SLD stays odd
 __host__ __device__ constexpr int fus_mh(int N, int W) { return N / 2 + 1 + 2 * ((W + 1) / 2); }
 __host__ __device__ constexpr int fus_sld(int N, int W) { return fus_mh(N, W) + 2; }
+__host__ __device__ constexpr int fus_rows(int N, int W) { return fus_mh(N, W) + 1; }
 
 // ---------------------------------------------------------------------------
 // Length-N forward DFT of a sequence whose only nonzeros are the L = N/2
@@ -177,14 +186,17 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
     constexpr int SLD = fus_sld(N, W);            // row length of S
     constexpr int GN = FUS_WARPS * N / 2;         // nodes per block at most (two staged blocks)
+    constexpr int SR = fus_rows(N, W);            // rows of S including the zero row
     extern __shared__ float2 smz[];
-    float2 *S = smz;                               // [MH][SLD]
+    float2 *S = smz;                               // [SR][SLD]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *buf = smz + MH * SLD + warp * N;   // this warp's FFT buffer
+    float2 *buf = smz + SR * SLD + warp * N;   // this warp's FFT buffer
     const int half = blockIdx.x;
     const int img = blockIdx.y;
     const float *im = images + (size_t)img * L * L;
     pdl_trigger();
+    // the zero row below the half plane (no transform writes it)
+    for (int i = threadIdx.x; i < SLD; i += FUS_NT) S[MH * SLD + i] = make_float2(0.f, 0.f);
     // cluster: the peer's S in the cluster window, this CTA's share of the
     // transforms (every second one)
     unsigned peerS = 0;
@@ -270,81 +282,86 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     pdl_wait();
 
     // ---- phase 3: interpolation of this half's nodes -----------------------
-    // block b of the half covers the nodes t in [t0, t0 + cnt);
-    // unit record s holds, as FUS_REC planes of FUS_GU float4,
-    //   0, 1  row weights of node A    2, 3  row weights of node B
-    //   4, 5  column weights of A, columns 0..7 of the union; 8.w: column 8
-    //   6, 7  column weights of B, columns 0..7; 8.x: column 8
-    //   8.y   r0 | c0 << 16 (union origin in S)   8.z  slotA | slotB << 16
-    // slots index the block's nodes (0xFFFF: none; node B of a single unit
-    // carries zero weights).  Results are staged in the (now idle) warp
+    // block b of the half covers the nodes t in [t0, t0 + cnt); unit record s
+    // holds, as FUS_REC planes of GU float4:
+    //   plane q      (q < 9)  the column weights of union column q, one per
+    //                         node slot: (wx_0[q], wx_1[q], wx_2[q], wx_3[q])
+    //   plane 9 + r  (r < 9)  the row weights of union row r, likewise
+    //   plane 18              (r0 | c0 << 16, slot0 | slot1 << 16,
+    //                          slot2 | slot3 << 16, 0): union origin in S and
+    //                          the block-local node index of each slot
+    // A node's weights are zero outside its own 8 x 8 window; slot 0xFFFF:
+    // no node (zero weights).  Results are staged in the (now idle) warp
     // buffers, two blocks deep so that one barrier per block suffices.
-    static_assert(W == 8, "unit records hold 8 + 8 row and 9 + 9 column weights");
+    static_assert(W == 8 && FUS_UW == W + 1, "unit records hold 9 + 9 weights per node");
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
     const int nl = (half == 0) ? nq0 : nh - nq0;
     const int nblk = (half == 0) ? nblk0 : nblk1;
     const int gb0 = (half == 0) ? 0 : nblk0;
     float2 *Fout = Fpol + (size_t)img * n_xi * nh;
-    float2 *stage0 = smz + MH * SLD;
+    float2 *stage0 = smz + SR * SLD;
     // t / nl as a multiply-high: exact for t < 2^32 / nl (nl >= 31 on this
     // path, so the multiplier does not overflow)
     const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;
-    constexpr int GU = (FUS_GU < GN / 2) ? FUS_GU : GN / 2;   // units per block
+    constexpr int GU = FUS_GU;   // the plan keeps a block's nodes within GN (one staging buffer)
     for (int b = 0; b < nblk; ++b) {
         const int2 tb = __ldg(&blocks[gb0 + b]);
         const int t0 = tb.x, cnt = tb.y;
         float2 *stage = stage0 + (b & 1) * GN;
         const float4 *rec = units + (size_t)(gb0 + b) * FUS_REC * GU;
-#pragma unroll 1
-        for (int s = threadIdx.x; s < GU; s += FUS_NT) {
-            const float4 meta = __ldg(&rec[8 * GU + s]);
-            const int locs = __float_as_int(meta.z);
-            const int la = locs & 0xFFFF, lb = (int)((unsigned)locs >> 16);   // 0xFFFF: no node B
-            if (la >= cnt) continue;
-            const int rc = __float_as_int(meta.y);
+        const int s = threadIdx.x;                 // one unit per thread
+        const float4 meta = __ldg(&rec[18 * GU + s]);
+        const unsigned s01 = __float_as_uint(meta.y), s23 = __float_as_uint(meta.z);
+        const int sl[4] = {(int)(s01 & 0xFFFFu), (int)(s01 >> 16), (int)(s23 & 0xFFFFu), (int)(s23 >> 16)};
+        if (sl[0] < cnt) {
+            const int rc = __float_as_int(meta.x);
             const int r0 = rc & 0xFFFF, c0 = rc >> 16;
-            const float4 xa0 = __ldg(&rec[4 * GU + s]), xa1 = __ldg(&rec[5 * GU + s]);
-            const float4 xb0 = __ldg(&rec[6 * GU + s]), xb1 = __ldg(&rec[7 * GU + s]);
-            if (r0 + W > MH || c0 + W + 1 > SLD) {
+            float2 acc[FUS_NU];
+#pragma unroll
+            for (int n = 0; n < FUS_NU; ++n) acc[n] = make_float2(0.f, 0.f);
+            if (r0 + FUS_UW > SR || c0 + FUS_UW > SLD) {
                 ffb_flag(status, FFB_ERR_ARG);
-                stage[la] = make_float2(0.f, 0.f);
-                if (lb < cnt) stage[lb] = make_float2(0.f, 0.f);
-                continue;
-            }
-            const float wxa[9] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w, meta.w};
-            const float wxb[9] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w, meta.x};
-            // row by row: the 9 values of the union row, interpolated along
-            // the row with each node's column weights, then weighted by the
-            // node's row weight (rows 0..3, then 4..7, four row weights of
-            // each node at a time)
-            const float2 *base = S + r0 * SLD + c0;
-            float2 aa = make_float2(0.f, 0.f), ab = make_float2(0.f, 0.f);
+            } else {
+                float wx[FUS_UW][FUS_NU];
 #pragma unroll
-            for (int h4 = 0; h4 < 2; ++h4) {
-                const float4 ya = __ldg(&rec[h4 * GU + s]), yb = __ldg(&rec[(2 + h4) * GU + s]);
-                const float wya[4] = {ya.x, ya.y, ya.z, ya.w};
-                const float wyb[4] = {yb.x, yb.y, yb.z, yb.w};
+                for (int q = 0; q < FUS_UW; ++q) {
+                    const float4 v = __ldg(&rec[q * GU + s]);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int b4 = 0; b4 < 4; ++b4) {
-                    const float2 *row = base + (4 * h4 + b4) * SLD;
-                    float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+                    for (int n = 0; n < FUS_NU; ++n) wx[q][n] = vv[n];
+                }
+                // row by row: the 9 values of the union row, interpolated
+                // along the row with each node's column weights, then
+                // weighted by the node's row weight
+                const float2 *base = S + r0 * SLD + c0;
+#pragma unroll 1
+                for (int r = 0; r < FUS_UW; ++r) {
+                    const float4 wv = __ldg(&rec[(FUS_UW + r) * GU + s]);
+                    const float wy[4] = {wv.x, wv.y, wv.z, wv.w};
+                    const float2 *row = base + r * SLD;
+                    float2 u[FUS_NU];
 #pragma unroll
-                    for (int q = 0; q <= W; ++q) {
+                    for (int n = 0; n < FUS_NU; ++n) u[n] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < FUS_UW; ++q) {
                         const float2 g = row[q];
-                        ra.x = fmaf(wxa[q], g.x, ra.x);
-                        ra.y = fmaf(wxa[q], g.y, ra.y);
-                        rb.x = fmaf(wxb[q], g.x, rb.x);
-                        rb.y = fmaf(wxb[q], g.y, rb.y);
+#pragma unroll
+                        for (int n = 0; n < FUS_NU; ++n) {
+                            u[n].x = fmaf(wx[q][n], g.x, u[n].x);
+                            u[n].y = fmaf(wx[q][n], g.y, u[n].y);
+                        }
                     }
-                    aa.x = fmaf(wya[b4], ra.x, aa.x);
-                    aa.y = fmaf(wya[b4], ra.y, aa.y);
-                    ab.x = fmaf(wyb[b4], rb.x, ab.x);
-                    ab.y = fmaf(wyb[b4], rb.y, ab.y);
+#pragma unroll
+                    for (int n = 0; n < FUS_NU; ++n) {
+                        acc[n].x = fmaf(wy[n], u[n].x, acc[n].x);
+                        acc[n].y = fmaf(wy[n], u[n].y, acc[n].y);
+                    }
                 }
             }
-            stage[la] = aa;
-            if (lb < cnt) stage[lb] = ab;
+#pragma unroll
+            for (int n = 0; n < FUS_NU; ++n)
+                if (sl[n] < cnt) stage[sl[n]] = acc[n];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += FUS_NT) {
@@ -361,7 +378,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
 // ---------------------------------------------------------------------------
 template <int N, int W>
 static size_t fused_smem() {
-    return sizeof(float2) * ((size_t)fus_mh(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * N);
+    return sizeof(float2) * ((size_t)fus_rows(N, W) * fus_sld(N, W) + (size_t)FUS_WARPS * N);
 }
 
 // 1 when the cluster variant keeps every SM busy: clusters of two CTAs (one
@@ -402,9 +419,10 @@ static int fused_cluster_ok() {
 // Adjoint of phase 3 (step a10): spreading.  One CTA per (image, half): the
 // half's polar values g (from the inverse ring DFT, layout of the polar
 // buffer) are spread into the half grid held in shared memory with the
-// forward's unit table, S[r0 + b][c0 + q] += wy_b wx_q g for both nodes of a
-// unit (shared-memory atomics; the unit order that keeps the forward's
-// gathers on distinct banks does the same for these adds), and the half grid
+// forward's unit table, S[r0 + r][c0 + q] += sum_n wy_n[r] wx_n[q] g_n over
+// the nodes of a unit (one shared-memory atomic per value of the 9 x 9 union
+// and component; the unit order that keeps the forward's gathers on distinct
+// banks does the same for these adds), and the half grid
 // is then added into the extended grid Gext[m2 + h][m1 mod N] (global
 // atomics: both halves overlap near m1 = 0 and m1 = +-N/2).  Gext is zeroed
 // by the caller.  This is the transpose of phase 3 with the same weights, so
@@ -418,14 +436,14 @@ k_adj_spread_half(const float2 *__restrict__ Gpol, int n_xi, int n_theta, int nq
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);
     constexpr int SLD = fus_sld(N, W);
-    constexpr int GN = FUS_WARPS * N / 2;
-    constexpr int GU = (FUS_GU < GN / 2) ? FUS_GU : GN / 2;
-    static_assert(W == 8, "unit records hold 8 + 8 row and 9 + 9 column weights");
+    constexpr int SR = fus_rows(N, W);
+    constexpr int GU = FUS_GU;
+    static_assert(W == 8 && FUS_UW == W + 1, "unit records hold 9 + 9 weights per node");
     extern __shared__ float2 smz[];
-    float *S = (float *)smz;                      // [MH][SLD] complex, as float pairs
+    float *S = (float *)smz;                      // [SR][SLD] complex, as float pairs
     const int half = blockIdx.x;
     const int img = blockIdx.y;
-    for (int i = threadIdx.x; i < MH * SLD; i += FUS_NT) smz[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < SR * SLD; i += FUS_NT) smz[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const int nh = n_theta / 2;
     const int lbeg = (half == 0) ? 0 : nq0;
@@ -434,57 +452,55 @@ k_adj_spread_half(const float2 *__restrict__ Gpol, int n_xi, int n_theta, int nq
     const int gb0 = (half == 0) ? 0 : nblk0;
     const float2 *Gp = Gpol + (size_t)img * n_xi * nh;
     const unsigned nl_magic = 0xFFFFFFFFu / (unsigned)nl + 1u;   // t / nl, as in phase 3
+    // the polar value of the node in block slot sl (zero for an empty slot)
+    auto value = [&](int t0, int cnt, int sl) {
+        if (sl >= cnt) return make_float2(0.f, 0.f);
+        const int t = t0 + sl;
+        const int j = (int)__umulhi((unsigned)t, nl_magic);
+        return __ldg(&Gp[(size_t)j * nh + lbeg + (t - j * nl)]);
+    };
     for (int b = 0; b < nblk; ++b) {
         const int2 tb = __ldg(&blocks[gb0 + b]);
         const int t0 = tb.x, cnt = tb.y;
         const float4 *rec = units + (size_t)(gb0 + b) * FUS_REC * GU;
-        for (int s = threadIdx.x; s < GU; s += FUS_NT) {
-            const float4 meta = __ldg(&rec[8 * GU + s]);
-            const int locs = __float_as_int(meta.z);
-            const int la = locs & 0xFFFF, lb = (int)((unsigned)locs >> 16);   // 0xFFFF: no node B
-            if (la >= cnt) continue;
-            const int rc = __float_as_int(meta.y);
-            const int r0 = rc & 0xFFFF, c0 = rc >> 16;
-            if (r0 + W > MH || c0 + W + 1 > SLD) {
-                ffb_flag(status, FFB_ERR_ARG);
-                continue;
-            }
-            const int ta = t0 + la;
-            const int ja = (int)__umulhi((unsigned)ta, nl_magic);
-            const float2 va = __ldg(&Gp[(size_t)ja * nh + lbeg + (ta - ja * nl)]);
-            float2 vb = make_float2(0.f, 0.f);
-            if (lb < cnt) {
-                const int tbn = t0 + lb;
-                const int jb = (int)__umulhi((unsigned)tbn, nl_magic);
-                vb = __ldg(&Gp[(size_t)jb * nh + lbeg + (tbn - jb * nl)]);
-            }
-            const float4 xa0 = __ldg(&rec[4 * GU + s]), xa1 = __ldg(&rec[5 * GU + s]);
-            const float4 xb0 = __ldg(&rec[6 * GU + s]), xb1 = __ldg(&rec[7 * GU + s]);
-            const float wxa[9] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w, meta.w};
-            const float wxb[9] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w, meta.x};
-            float *base = S + 2 * (r0 * SLD + c0);
+        const int s = threadIdx.x;                 // one unit per thread
+        const float4 meta = __ldg(&rec[18 * GU + s]);
+        const unsigned s01 = __float_as_uint(meta.y), s23 = __float_as_uint(meta.z);
+        const int sl0 = (int)(s01 & 0xFFFFu);
+        if (sl0 >= cnt) continue;
+        const int rc = __float_as_int(meta.x);
+        const int r0 = rc & 0xFFFF, c0 = rc >> 16;
+        if (r0 + FUS_UW > SR || c0 + FUS_UW > SLD) {
+            ffb_flag(status, FFB_ERR_ARG);
+            continue;
+        }
+        const float2 v0 = value(t0, cnt, sl0), v1 = value(t0, cnt, (int)(s01 >> 16));
+        const float2 v2 = value(t0, cnt, (int)(s23 & 0xFFFFu)), v3 = value(t0, cnt, (int)(s23 >> 16));
+        float4 wx[FUS_UW];
 #pragma unroll
-            for (int h4 = 0; h4 < 2; ++h4) {
-                const float4 ya = __ldg(&rec[h4 * GU + s]), yb = __ldg(&rec[(2 + h4) * GU + s]);
-                const float wya[4] = {ya.x, ya.y, ya.z, ya.w};
-                const float wyb[4] = {yb.x, yb.y, yb.z, yb.w};
+        for (int q = 0; q < FUS_UW; ++q) wx[q] = __ldg(&rec[q * GU + s]);
+        float *base = S + 2 * (r0 * SLD + c0);
+        // S[r0 + r][c0 + q] += sum_n wy_n[r] wx_n[q] v_n: the transpose of the
+        // forward's row-by-row interpolation, one shared atomic per grid
+        // value and component
+#pragma unroll 1
+        for (int r = 0; r < FUS_UW; ++r) {
+            const float4 wy = __ldg(&rec[(FUS_UW + r) * GU + s]);
+            const float2 u0 = make_float2(wy.x * v0.x, wy.x * v0.y), u1 = make_float2(wy.y * v1.x, wy.y * v1.y);
+            const float2 u2 = make_float2(wy.z * v2.x, wy.z * v2.y), u3 = make_float2(wy.w * v3.x, wy.w * v3.y);
+            float *row = base + 2 * r * SLD;
 #pragma unroll
-                for (int b4 = 0; b4 < 4; ++b4) {
-                    const float2 ua = make_float2(wya[b4] * va.x, wya[b4] * va.y);
-                    const float2 ub = make_float2(wyb[b4] * vb.x, wyb[b4] * vb.y);
-                    float *row = base + 2 * (4 * h4 + b4) * SLD;
-#pragma unroll
-                    for (int q = 0; q <= W; ++q) {
-                        atomicAdd(&row[2 * q], fmaf(wxa[q], ua.x, wxb[q] * ub.x));
-                        atomicAdd(&row[2 * q + 1], fmaf(wxa[q], ua.y, wxb[q] * ub.y));
-                    }
-                }
+            for (int q = 0; q < FUS_UW; ++q) {
+                const float re = fmaf(wx[q].x, u0.x, fmaf(wx[q].y, u1.x, fmaf(wx[q].z, u2.x, wx[q].w * u3.x)));
+                const float im = fmaf(wx[q].x, u0.y, fmaf(wx[q].y, u1.y, fmaf(wx[q].z, u2.y, wx[q].w * u3.y)));
+                atomicAdd(&row[2 * q], re);
+                atomicAdd(&row[2 * q + 1], im);
             }
         }
     }
     __syncthreads();
     // the half grid into Gext: row e is m2 = e - H (Gext's own offset), column
-    // c is m1 = c + m1lo
+    // c is m1 = c + m1lo (the zero row and columns past MH are not copied)
     const int m1lo = (half == 0) ? -H : -(N / 2) - H;
     float2 *Gi = Gext + (size_t)img * MH * N;
     for (int i = threadIdx.x; i < MH * MH; i += FUS_NT) {
@@ -497,7 +513,7 @@ k_adj_spread_half(const float2 *__restrict__ Gpol, int n_xi, int n_theta, int nq
 int ffb_launch_fused_spread(ffb_plan_t p, const float2 *Gpol, int m, float2 *Gext, cudaStream_t s) {
     if (p->N != 256 && p->N != 128) return FFB_ERR_UNSUPPORTED;
     const int N = p->N;
-    const size_t smem = sizeof(float2) * (size_t)fus_mh(N, 8) * fus_sld(N, 8);
+    const size_t smem = sizeof(float2) * (size_t)fus_rows(N, 8) * fus_sld(N, 8);
     static int attr256 = 0, attr128 = 0;
     int &done = (N == 256) ? attr256 : attr128;
     const void *fn = (N == 256) ? (const void *)k_adj_spread_half<256, 8> : (const void *)k_adj_spread_half<128, 8>;
@@ -587,24 +603,25 @@ bool ffb_fused_supported(ffb_plan_t p) {
 // starts at m = ceil(p - W/2) and the weights are phi(f - b), f = p - m,
 // b = 0..7, phi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) the ES kernel
 // (Sec. III, type-2 NUFFT), in float64.  A block takes the longest run of
-// consecutive nodes, at most GN, that pairs into at most GU units.  Pairing within a
-// block: nodes sorted by (r0, c0), each joined with the next when that has the
-// same r0 and c0 at most one larger (left to right, a maximum matching of
-// this interval structure); the rest are single units.  Units are ordered per
-// half warp with distinct bank slots (r0 SLD + c0) mod 16: one unit from every
-// nonempty slot, fullest slot first, then fill from the fullest.
+// consecutive nodes, at most GN, that groups into at most GU units.
+// Grouping within a block: nodes sorted by (r0, c0); the first node not yet
+// taken anchors a unit and takes up to three more untaken nodes whose window
+// origins lie in the 2 x 2 box (r0 .. r0 + 1, c0 .. c0 + 1), in the order
+// same origin, right, below, below right.  Units are ordered per half warp
+// with distinct bank slots (union row * SLD + union column) mod 16: one unit
+// from every nonempty slot, fullest slot first, then fill from the fullest.
 static int build_units(int N, int W, double beta, int n_xi, int n_theta, const double *xi,
                        std::vector<float4> &rec, std::vector<int2> &blk, int nb[2]) {
     if (W != 8 || !(N == 128 || N == 256) || n_xi < 1 || n_theta < 4 || (n_theta & 1) || !xi)
         return FFB_ERR_UNSUPPORTED;
-    const int H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W);
-    const int GN = FUS_WARPS * N / 2, GU = std::min(FUS_GU, GN / 2);
+    const int H = (W + 1) / 2, SLD = fus_sld(N, W), MH = fus_mh(N, W), SR = fus_rows(N, W);
+    const int GN = FUS_WARPS * N / 2, GU = FUS_GU;
     const int nh = n_theta / 2, nq0 = n_theta / 4 + 1;
     auto phi = [&](double x) {
         const double z = 2.0 * x / W, u = 1.0 - z * z;
         return (u > 0.0) ? std::exp(beta * (std::sqrt(u) - 1.0)) : 0.0;
     };
-    auto bits = [](int v) {
+    auto bits = [](unsigned v) {
         float f;
         std::memcpy(&f, &v, sizeof f);
         return f;
@@ -612,6 +629,10 @@ static int build_units(int N, int W, double beta, int n_xi, int n_theta, const d
     struct Node {
         int r0, c0;
         double f1, f2;
+    };
+    struct Unit {
+        int n;
+        int idx[4];   // block-local node indices (FUS_NU used)
     };
     rec.clear();
     blk.clear();
@@ -621,7 +642,6 @@ static int build_units(int N, int W, double beta, int n_xi, int n_theta, const d
         const int nl = (half == 0) ? nq0 : nh - nq0;
         const int npts = n_xi * nl;
         const int m1lo = (half == 0) ? -H : -(N / 2) - H;
-        if (nl > GN) return FFB_ERR_UNSUPPORTED;
         std::vector<Node> nd(npts);
         for (int t = 0; t < npts; ++t) {
             const int j = t / nl, l = lbeg + t % nl;
@@ -632,112 +652,128 @@ static int build_units(int N, int W, double beta, int n_xi, int n_theta, const d
             if (c0 < 0 || c0 + W > MH || r0 < 0 || r0 + W > MH) return FFB_ERR_UNSUPPORTED;
             nd[t] = {r0, c0, p1 - m1, p2 - m2};
         }
-        // units of the nodes [t0, t1): (A, B) block-local, B = -1 for a single
-        auto pair_up = [&](int t0, int t1) {
-            std::vector<int> ord(t1 - t0);
-            for (int i = 0; i < t1 - t0; ++i) ord[i] = i;
+        // units of the nodes [t0, t1), node indices block-local
+        auto group = [&](int t0, int t1) {
+            const int n = t1 - t0;
+            std::vector<int> ord(n);
+            for (int i = 0; i < n; ++i) ord[i] = i;
+            auto key = [&](int i) { return (int64_t)nd[t0 + i].r0 * 65536 + nd[t0 + i].c0; };
             std::sort(ord.begin(), ord.end(), [&](int x, int y) {
-                const Node &u = nd[t0 + x], &v = nd[t0 + y];
-                return (u.r0 != v.r0) ? u.r0 < v.r0 : (u.c0 != v.c0) ? u.c0 < v.c0 : x < y;
+                const int64_t kx = key(x), ky = key(y);
+                return (kx != ky) ? kx < ky : x < y;
             });
-            std::vector<std::pair<int, int>> un;
-            for (size_t i = 0; i < ord.size();) {
-                if (i + 1 < ord.size()) {
-                    const Node &u = nd[t0 + ord[i]], &v = nd[t0 + ord[i + 1]];
-                    if (u.r0 == v.r0 && v.c0 - u.c0 <= 1) {
-                        un.push_back({ord[i], ord[i + 1]});
-                        i += 2;
-                        continue;
-                    }
+            std::vector<char> used(n, 0);
+            std::vector<Unit> un;
+            // position in ord of the first node at or after origin (r, c)
+            auto first_at = [&](int r, int c) {
+                const int64_t k = (int64_t)r * 65536 + c;
+                return (int)(std::lower_bound(ord.begin(), ord.end(), k,
+                                              [&](int i, int64_t kk) { return key(i) < kk; }) -
+                             ord.begin());
+            };
+            for (int a = 0; a < n; ++a) {
+                const int ia = ord[a];
+                if (used[ia]) continue;
+                Unit u{1, {ia, -1, -1, -1}};
+                used[ia] = 1;
+                const int r = nd[t0 + ia].r0, c = nd[t0 + ia].c0;
+                const int cells[4][2] = {{r, c}, {r, c + 1}, {r + 1, c}, {r + 1, c + 1}};
+                for (int cc = 0; cc < 4 && u.n < FUS_NU; ++cc) {
+                    const int64_t k = (int64_t)cells[cc][0] * 65536 + cells[cc][1];
+                    for (int p = first_at(cells[cc][0], cells[cc][1]); p < n && key(ord[p]) == k && u.n < FUS_NU; ++p)
+                        if (!used[ord[p]]) {
+                            used[ord[p]] = 1;
+                            u.idx[u.n++] = ord[p];
+                        }
                 }
-                un.push_back({ord[i], -1});
-                ++i;
+                un.push_back(u);
             }
             return un;
         };
         for (int t0 = 0; t0 < npts;) {
-            // the longest node range whose units fit (the unit count of a
-            // range never decreases as it grows): full blocks of GU units
+            // a long node range whose units fit: full blocks of GU units (the
+            // search keeps only ranges that were checked to fit)
             int lo = t0 + 1, hi = std::min(npts, t0 + GN);
             while (lo < hi) {
                 const int mid = (lo + hi + 1) / 2;
-                if ((int)pair_up(t0, mid).size() <= GU) lo = mid;
+                if ((int)group(t0, mid).size() <= GU) lo = mid;
                 else hi = mid - 1;
             }
             const int t1 = lo;
-            std::vector<std::pair<int, int>> un = pair_up(t0, t1);
+            std::vector<Unit> un = group(t0, t1);
             const int cnt = t1 - t0;
+            if ((int)un.size() > GU) return FFB_ERR_UNSUPPORTED;
             blk.push_back(make_int2(t0, cnt));
             const size_t base = rec.size();
             rec.resize(base + (size_t)FUS_REC * GU, make_float4(0.f, 0.f, 0.f, 0.f));
             float4 *R = rec.data() + base;
-            for (int sl = 0; sl < GU; ++sl) R[8 * GU + sl] = make_float4(0.f, 0.f, bits((int)0xFFFFFFFFu), 0.f);
-            // union origin of each unit: A's window origin, or one column to
-            // its left where both nodes' windows still fit (the same column
-            // origin, or a single node), chosen to even out the bank slots:
-            // the fixed units first, then each movable one into the emptier
-            // of its two slots
-            const int nu0 = (int)un.size();
-            std::vector<int> ucol(nu0);
+            for (int sl = 0; sl < GU; ++sl) R[18 * GU + sl] = make_float4(0.f, bits(0xFFFFFFFFu), bits(0xFFFFFFFFu), 0.f);
+            // union origin of each unit: the box origin (minimum row and column
+            // of its nodes), or one row / column earlier where every node sits
+            // in the box's first row / column and the union still fits,
+            // chosen to even out the bank slots: fixed units first, then each
+            // movable one into its emptiest candidate slot
+            const int nu = (int)un.size();
+            std::vector<int> urow(nu), ucol(nu);
             int cnt16[16] = {};
-            std::vector<char> movable(nu0);
-            for (int u = 0; u < nu0; ++u) {
-                const Node &a = nd[t0 + un[u].first];
-                movable[u] = (un[u].second < 0 || nd[t0 + un[u].second].c0 == a.c0) && a.c0 >= 1;
-                ucol[u] = a.c0;
-                if (!movable[u]) cnt16[(a.r0 * SLD + a.c0) & 15]++;
+            std::vector<std::vector<std::pair<int, int>>> cand(nu);
+            for (int u = 0; u < nu; ++u) {
+                int rmin = 1 << 30, cmin = 1 << 30, rmax = -1, cmax = -1;
+                for (int i = 0; i < un[u].n; ++i) {
+                    const Node &v = nd[t0 + un[u].idx[i]];
+                    rmin = std::min(rmin, v.r0);
+                    rmax = std::max(rmax, v.r0);
+                    cmin = std::min(cmin, v.c0);
+                    cmax = std::max(cmax, v.c0);
+                }
+                const bool mr = (rmax == rmin) && rmin >= 1, mc = (cmax == cmin) && cmin >= 1;
+                cand[u].push_back({rmin, cmin});
+                if (mc) cand[u].push_back({rmin, cmin - 1});
+                if (mr) cand[u].push_back({rmin - 1, cmin});
+                if (mr && mc) cand[u].push_back({rmin - 1, cmin - 1});
+                urow[u] = rmin;
+                ucol[u] = cmin;
+                if (cand[u].size() == 1) cnt16[(rmin * SLD + cmin) & 15]++;
             }
-            for (int u = 0; u < nu0; ++u) {
-                if (!movable[u]) continue;
-                const Node &a = nd[t0 + un[u].first];
-                const int s0 = (a.r0 * SLD + a.c0) & 15, s1 = (s0 + 15) & 15;
-                if (cnt16[s1] < cnt16[s0]) ucol[u] = a.c0 - 1;
-                cnt16[(a.r0 * SLD + ucol[u]) & 15]++;
+            for (int u = 0; u < nu; ++u) {
+                if (cand[u].size() == 1) continue;
+                int best = 0;
+                for (int k = 1; k < (int)cand[u].size(); ++k)
+                    if (cnt16[(cand[u][k].first * SLD + cand[u][k].second) & 15] <
+                        cnt16[(cand[u][best].first * SLD + cand[u][best].second) & 15])
+                        best = k;
+                urow[u] = cand[u][best].first;
+                ucol[u] = cand[u][best].second;
+                cnt16[(urow[u] * SLD + ucol[u]) & 15]++;
             }
             std::vector<int> bucket[16];
-            for (int u = nu0 - 1; u >= 0; --u) {
-                const Node &a = nd[t0 + un[u].first];
-                bucket[(a.r0 * SLD + ucol[u]) & 15].push_back(u);
-            }
+            for (int u = nu - 1; u >= 0; --u) bucket[(urow[u] * SLD + ucol[u]) & 15].push_back(u);
             int pos = 0;
             auto put = [&](int u) {
-                const int ia = un[u].first, ib = un[u].second;
-                const Node &a = nd[t0 + ia];
-                const int cu = ucol[u];
-                float w[36] = {};   // row A (8), row B (8), column A (9), column B (9)
-                for (int q = 0; q < W; ++q) {
-                    w[q] = (float)phi(a.f2 - q);
-                    w[16 + (a.c0 - cu) + q] = (float)phi(a.f1 - q);
-                }
-                if (ib >= 0) {
-                    const Node &bn = nd[t0 + ib];
-                    const int d = bn.c0 - cu;   // 0, 1
+                const int ru = urow[u], cu = ucol[u];
+                if (ru < 0 || cu < 0 || ru + FUS_UW > SR || cu + FUS_UW > SLD) return false;
+                float wx[FUS_UW][4] = {}, wy[FUS_UW][4] = {};
+                unsigned slot[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu};
+                for (int i = 0; i < un[u].n; ++i) {
+                    const Node &v = nd[t0 + un[u].idx[i]];
+                    const int dr = v.r0 - ru, dc = v.c0 - cu;   // 0 or 1
                     for (int q = 0; q < W; ++q) {
-                        w[8 + q] = (float)phi(bn.f2 - q);
-                        w[25 + d + q] = (float)phi(bn.f1 - q);
+                        wx[dc + q][i] = (float)phi(v.f1 - q);
+                        wy[dr + q][i] = (float)phi(v.f2 - q);
                     }
+                    slot[i] = (unsigned)un[u].idx[i];
                 }
-                // fields: rows A, rows B, columns A 0..7, columns B 0..7,
-                // (column B 8, origin, slots, column A 8)
-                const float4 f0 = make_float4(w[0], w[1], w[2], w[3]), f1 = make_float4(w[4], w[5], w[6], w[7]);
-                const float4 f2 = make_float4(w[8], w[9], w[10], w[11]), f3 = make_float4(w[12], w[13], w[14], w[15]);
-                const float4 f4 = make_float4(w[16], w[17], w[18], w[19]), f5 = make_float4(w[20], w[21], w[22], w[23]);
-                const float4 f6 = make_float4(w[25], w[26], w[27], w[28]), f7 = make_float4(w[29], w[30], w[31], w[32]);
-                R[0 * GU + pos] = f0;
-                R[1 * GU + pos] = f1;
-                R[2 * GU + pos] = f2;
-                R[3 * GU + pos] = f3;
-                R[4 * GU + pos] = f4;
-                R[5 * GU + pos] = f5;
-                R[6 * GU + pos] = f6;
-                R[7 * GU + pos] = f7;
-                // slots as unsigned halves (0xFFFF: no node B); the kernels
-                // decode them with logical shifts
-                const unsigned locs = (unsigned)ia | ((unsigned)(ib >= 0 ? ib : 0xFFFF) << 16);
-                R[8 * GU + pos] = make_float4(w[33], bits(a.r0 | (cu << 16)), bits((int)locs), w[24]);
+                for (int q = 0; q < FUS_UW; ++q) {
+                    R[q * GU + pos] = make_float4(wx[q][0], wx[q][1], wx[q][2], wx[q][3]);
+                    R[(FUS_UW + q) * GU + pos] = make_float4(wy[q][0], wy[q][1], wy[q][2], wy[q][3]);
+                }
+                // slots as unsigned halves (0xFFFF: none); the kernels decode
+                // them with logical shifts
+                R[18 * GU + pos] = make_float4(bits((unsigned)ru | ((unsigned)cu << 16)),
+                                               bits(slot[0] | (slot[1] << 16)), bits(slot[2] | (slot[3] << 16)), 0.f);
                 ++pos;
+                return true;
             };
-            const int nu = (int)un.size();
             while (pos < nu) {
                 int order[16];
                 for (int r = 0; r < 16; ++r) order[r] = r;
@@ -745,7 +781,7 @@ static int build_units(int N, int W, double beta, int n_xi, int n_theta, const d
                 int taken = 0;
                 for (int r : order) {
                     if (bucket[r].empty()) continue;
-                    put(bucket[r].back());
+                    if (!put(bucket[r].back())) return FFB_ERR_UNSUPPORTED;
                     bucket[r].pop_back();
                     ++taken;
                 }
@@ -753,7 +789,7 @@ static int build_units(int N, int W, double beta, int n_xi, int n_theta, const d
                     int rb = 0;
                     for (int r = 1; r < 16; ++r)
                         if (bucket[r].size() > bucket[rb].size()) rb = r;
-                    put(bucket[rb].back());
+                    if (!put(bucket[rb].back())) return FFB_ERR_UNSUPPORTED;
                     bucket[rb].pop_back();
                     ++taken;
                 }
@@ -820,9 +856,11 @@ extern "C" int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta
     h_counts[1] = (int64_t)blk.size();
     h_counts[2] = nb[0];
     h_counts[3] = nb[1];
-    h_counts[4] = std::min(FUS_GU, FUS_WARPS * N / 4);
+    h_counts[4] = FUS_GU;
     h_counts[5] = fus_mh(N, w);
     h_counts[6] = fus_sld(N, w);
+    h_counts[7] = FUS_REC;
+    h_counts[8] = FUS_NU;
     if (h_rec) std::memcpy(h_rec, rec.data(), sizeof(float4) * rec.size());
     if (h_blk) std::memcpy(h_blk, blk.data(), sizeof(int2) * blk.size());
     return FFB_OK;

@@ -88,12 +88,12 @@ def load(path=LIB_PATH):
 
 def interp_units(N, w, beta, n_theta, xi):
     """Host-only: the shared-memory grid path's interpolation table for radii
-    ``xi`` (see ffb_interp_units).  Returns (records float32 (blocks, 9, GU,
+    ``xi`` (see ffb_interp_units).  Returns (records float32 (blocks, F, GU,
     4), blocks int32 (blocks, 2), (blocks of half 0, blocks of half 1), MH,
-    SLD)."""
+    SLD, nodes per unit at most)."""
     import numpy as np
     x = np.ascontiguousarray(xi, dtype=np.float64)
-    cnt = (ctypes.c_int64 * 7)()
+    cnt = (ctypes.c_int64 * 9)()
     lib = load()
     _check(lib.ffb_interp_units(int(N), int(w), float(beta), len(x), int(n_theta), x.ctypes.data_as(_pd), cnt,
                                 None, None), "ffb_interp_units")
@@ -103,7 +103,8 @@ def interp_units(N, w, beta, n_theta, xi):
                                 rec.ctypes.data_as(ctypes.c_void_p), blk.ctypes.data_as(_pi)),
            "ffb_interp_units")
     gu = int(cnt[4])
-    return rec.reshape(int(cnt[1]), 9, gu, 4), blk.reshape(-1, 2), (int(cnt[2]), int(cnt[3])), int(cnt[5]), int(cnt[6])
+    return (rec.reshape(int(cnt[1]), int(cnt[7]), gu, 4), blk.reshape(-1, 2), (int(cnt[2]), int(cnt[3])),
+            int(cnt[5]), int(cnt[6]), int(cnt[8]))
 
 
 def cov_merge(p, states):

@@ -7,8 +7,9 @@ origin with ES-kernel weights.  Checked here against the geometry restated
 from that definition:
   * every node of each half lies in exactly one unit of one block;
   * interpolating a random half grid through the records, the way the kernel
-    reads them (one 8 x 9 union per unit, 9 column weights per node), equals
-    the direct 8 x 8 sum of phi(f2 - r) phi(f1 - q) over the node's window;
+    reads them (one 9 x 9 union per unit, 9 row and 9 column weights per
+    node), equals the direct 8 x 8 sum of phi(f2 - r) phi(f1 - q) over the
+    node's window, and the node's window lies inside its unit's union;
   * blocks stay within their unit and node budgets, and each half warp of a
     block holds one unit of every bank slot (origin mod 16) that still has
     units when it is formed."""
@@ -42,31 +43,29 @@ def radii(n_xi, c):
 
 
 def decode(rec, blk, nb, n_xi, n_theta, N):
-    """Per half: list of (node t, union row r0, union column cu, row weights (8,),
-    column weights over the union (9,))."""
+    """Per half: list of (node t, union row ru, union column cu, row weights
+    (9,), column weights (9,)) over the unit's 9 x 9 union."""
     nq0 = n_theta // 4 + 1
     out = [[], []]
     gu = rec.shape[2]
     for b in range(rec.shape[0]):
         half = 0 if b < nb[0] else 1
         t0, cnt = int(blk[b, 0]), int(blk[b, 1])
-        f8 = rec[b, 8]
-        origin = f8[:, 1].copy().view(np.int32)
-        slots = f8[:, 2].copy().view(np.uint32)
+        meta = rec[b, 18]
+        origin = meta[:, 0].copy().view(np.int32)
+        s01 = meta[:, 1].copy().view(np.uint32)
+        s23 = meta[:, 2].copy().view(np.uint32)
         for u in range(gu):
-            if slots[u] == 0xFFFFFFFF:
+            slots = [int(s01[u]) & 0xFFFF, int(s01[u]) >> 16, int(s23[u]) & 0xFFFF, int(s23[u]) >> 16]
+            if slots[0] == 0xFFFF:
                 continue
-            r0, cu = int(origin[u]) & 0xFFFF, int(origin[u]) >> 16
-            ia, ib = int(slots[u]) & 0xFFFF, int(slots[u]) >> 16
-            rowsA = np.concatenate([rec[b, 0, u], rec[b, 1, u]])
-            colsA = np.concatenate([rec[b, 4, u], rec[b, 5, u], [f8[u, 3]]])
-            assert ia < cnt
-            out[half].append((t0 + ia, r0, cu, rowsA, colsA))
-            if ib != 0xFFFF:
-                assert ib < cnt
-                rowsB = np.concatenate([rec[b, 2, u], rec[b, 3, u]])
-                colsB = np.concatenate([rec[b, 6, u], rec[b, 7, u], [f8[u, 0]]])
-                out[half].append((t0 + ib, r0, cu, rowsB, colsB))
+            ru, cu = int(origin[u]) & 0xFFFF, int(origin[u]) >> 16
+            for i, sl in enumerate(slots):
+                if sl == 0xFFFF:
+                    assert not rec[b, :18, u, i].any()          # an empty slot carries zero weights
+                    continue
+                assert sl < cnt
+                out[half].append((t0 + sl, ru, cu, rec[b, 9:18, u, i].copy(), rec[b, 0:9, u, i].copy()))
     return out, nq0
 
 
@@ -80,8 +79,8 @@ def test_units_cover_every_node_and_interpolate_like_the_direct_sum(ffb, L, c, R
     n_theta = int(math.ceil(16 * c * R - 1e-9))
     n_theta += n_theta & 1
     xi = radii(n_xi, c)
-    rec, blk, nb, MH, SLD = ffb.interp_units(N, W, BETA, n_theta, xi)
-    assert rec.shape[0] == nb[0] + nb[1] == blk.shape[0]
+    rec, blk, nb, MH, SLD, nu = ffb.interp_units(N, W, BETA, n_theta, xi)
+    assert rec.shape[0] == nb[0] + nb[1] == blk.shape[0] and nu <= 4
     units, nq0 = decode(rec, blk, nb, n_xi, n_theta, N)
     rng = np.random.default_rng(L + int(10 * c))
     for half in (0, 1):
@@ -89,8 +88,9 @@ def test_units_cover_every_node_and_interpolate_like_the_direct_sum(ffb, L, c, R
         nl = nq0 if half == 0 else n_theta // 2 - nq0
         ts = sorted(u[0] for u in units[half])
         assert ts == list(range(n_xi * nl))                 # each node exactly once
-        S = rng.standard_normal((MH, SLD)) + 1j * rng.standard_normal((MH, SLD))
+        S = rng.standard_normal((MH + 1, SLD)) + 1j * rng.standard_normal((MH + 1, SLD))
         S[:, MH:] = 0.0                                     # the two zero pad columns
+        S[MH, :] = 0.0                                      # and the zero pad row
         m1lo = -H if half == 0 else -(N // 2) - H
         err, scale = 0.0, 0.0
         for (t, r0, cu, rows, cols) in units[half]:
@@ -99,11 +99,12 @@ def test_units_cover_every_node_and_interpolate_like_the_direct_sum(ffb, L, c, R
             p1, p2 = N * xi[j] * math.cos(th), N * xi[j] * math.sin(th)
             m1, m2 = math.ceil(p1 - 0.5 * W), math.ceil(p2 - 0.5 * W)
             c0, r0e = m1 - m1lo, m2 + H
-            assert r0 == r0e and 0 <= c0 - cu <= 1
-            assert 0 <= r0 and r0 + W <= MH and 0 <= c0 and c0 + W <= MH
+            assert 0 <= r0e - r0 <= 1 and 0 <= c0 - cu <= 1     # the window inside the 9 x 9 union
+            assert 0 <= r0e and r0e + W <= MH and 0 <= c0 and c0 + W <= MH
+            assert r0 + 9 <= MH + 1 and cu + 9 <= SLD
             wy, wx = phi((p2 - m2) - np.arange(W)), phi((p1 - m1) - np.arange(W))
-            direct = wy @ S[r0:r0 + W, c0:c0 + W] @ wx
-            table = rows.astype(np.float64) @ S[r0:r0 + W, cu:cu + 9] @ cols.astype(np.float64)
+            direct = wy @ S[r0e:r0e + W, c0:c0 + W] @ wx
+            table = rows.astype(np.float64) @ S[r0:r0 + 9, cu:cu + 9] @ cols.astype(np.float64)
             err = max(err, abs(table - direct))
             scale = max(scale, float(np.abs(wy).sum() * np.abs(wx).sum()))
         assert err <= 1e-6 * scale, (half, err, scale)
@@ -113,18 +114,26 @@ def test_units_cover_every_node_and_interpolate_like_the_direct_sum(ffb, L, c, R
 def test_blocks_budgets_and_bank_slots(ffb, L, c, R):
     N = 2 * L
     n_xi, n_theta = int(4 * c * R), int(16 * c * R)
-    rec, blk, nb, MH, SLD = ffb.interp_units(N, W, BETA, n_theta, radii(n_xi, c))
-    gu = rec.shape[2]
-    gn = 32 * N // 2                                   # nodes per block: one staging entry each
+    rec, blk, nb, MH, SLD, nu_max = ffb.interp_units(N, W, BETA, n_theta, radii(n_xi, c))
+    gu = rec.shape[2]                                  # one unit per thread of the CTA
+    gn = (gu // 32) * N // 2                           # nodes per block: one staging entry each (N/2 per warp)
+    total_units = total_nodes = 0
     for b in range(rec.shape[0]):
         assert 1 <= blk[b, 1] <= gn
-        slots = rec[b, 8, :, 2].copy().view(np.uint32)
-        used = np.nonzero(slots != 0xFFFFFFFF)[0]
+        s01 = rec[b, 18, :, 1].copy().view(np.uint32)
+        s23 = rec[b, 18, :, 2].copy().view(np.uint32)
+        slot0 = s01 & 0xFFFF
+        used = np.nonzero(slot0 != 0xFFFF)[0]
         nu = len(used)
         assert nu <= gu and np.array_equal(used, np.arange(nu))   # empty units only at the end
-        nodes = nu + int(np.sum((slots[:nu] >> 16) != 0xFFFF))
+        filled = [(s01[:nu] & 0xFFFF) != 0xFFFF, (s01[:nu] >> 16) != 0xFFFF,
+                  (s23[:nu] & 0xFFFF) != 0xFFFF, (s23[:nu] >> 16) != 0xFFFF]
+        nodes = int(sum(np.count_nonzero(f) for f in filled[:nu_max]))
+        assert not any(np.count_nonzero(f) for f in filled[nu_max:])
         assert nodes == blk[b, 1]
-        origin = rec[b, 8, :nu, 1].copy().view(np.int32)
+        total_units += nu
+        total_nodes += nodes
+        origin = rec[b, 18, :nu, 0].copy().view(np.int32)
         bank = ((origin & 0xFFFF) * SLD + (origin >> 16)) % 16
         # half warp h reads units 16 h .. 16 h + 15: it holds one unit of
         # every slot that still has units left when it is formed (at most 16)
@@ -134,6 +143,8 @@ def test_blocks_budgets_and_bank_slots(ffb, L, c, R):
             assert len(set(grp.tolist())) >= min(int(np.count_nonzero(left)), len(grp))
             left -= np.bincount(grp, minlength=16)
         assert not left.any()
+    # the grouping pays: well above two nodes per unit on these polar grids
+    assert total_nodes / total_units > 2.2
 
 
 def test_rejects_unsupported_geometry(ffb):
