@@ -38,6 +38,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-post", action="store_true", help="skip the a8-a10 timings after the step")
+    ap.add_argument("--no-batching", action="store_true", help="skip the 48-stack batching workload after the step")
     return ap.parse_args()
 
 
@@ -223,6 +224,62 @@ def measured_tensor_peak(precision):
 def fp32_peak_tflops(sms, sm_mhz):
     """SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# the batching workload after the step: 48 stacks of uneven L and n
+# ---------------------------------------------------------------------------
+def batching_run(dev, precision, reps=3):
+    """a1-a7 over the 48-stack batching workload (L in {64, 96, 128, 180, 256},
+    n in [500, 20000], about 53 GB of images resident in HBM) through one
+    group call per step: per-stack expansion branches, one grouped covariance
+    launch, a CUDA graph replayed after the eager and the capturing call.
+    Returns images/s over ``reps`` replays timed with CUDA events."""
+    import torch
+    from paper_1412_0781_gb300 import Group, Plan, data
+    specs = data.batching_stacks()
+    plans = [Plan(sp.L, sp.c, sp.R, eps=EPS, precision=precision) for sp in specs]
+    imgs = [data.blob_stack(sp, device=dev)[0] for sp in specs]
+    coefs = [torch.empty((sp.n, p.P, 2), device=dev, dtype=torch.float32) for sp, p in zip(specs, plans)]
+    g = Group(plans)
+    t0 = time.perf_counter()
+    g.expand_cov(imgs, coefs, reset=True)          # eager call (tunes the grouped covariance once)
+    g.sync()
+    eager_s = time.perf_counter() - t0
+    g.expand_cov(imgs, coefs, reset=True)          # captures the CUDA graph
+    g.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        g.expand_cov(imgs, coefs, reset=True)      # graph replays
+    b.record()
+    torch.cuda.synchronize()
+    g.sync()
+    ms = a.elapsed_time(b) / reps
+    n_img = sum(sp.n for sp in specs)
+    img_bytes = sum(sp.n * sp.L * sp.L * 4 for sp in specs)
+    by_L = {}
+    for sp in specs:
+        by_L.setdefault(sp.L, [0, 0])
+        by_L[sp.L][0] += 1
+        by_L[sp.L][1] += sp.n
+    info = g.info()
+    out = {"stacks": len(specs), "images": n_img, "image_bytes": img_bytes,
+           "coef_bytes": sum(sp.n * p.P * 8 for sp, p in zip(specs, plans)),
+           "stacks_and_images_by_L": {str(k): v for k, v in sorted(by_L.items())},
+           "precision": precision, "ms_per_call": ms, "images_per_s": n_img / (ms / 1e3),
+           "eager_call_s": eager_s, "graph_replays_timed": reps,
+           "grouped_covariance_item": {"images_per_item": info["per"], "tile": info["tile"], "grid": info["grid"],
+                                       "candidates_timed": info["candidates"]},
+           "launches_per_call": info["launches"],
+           "note": "a1-a7 of every stack in one group call (expansion branches, one grouped covariance launch), "
+                   "replayed CUDA graph; inputs resident in HBM"}
+    g.close()
+    for p in plans:
+        p.close()
+    del imgs, coefs
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -499,6 +556,11 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d images of the n=100000 L=128 stack (%.1f s), FP64 direct NDFT + ring DFT + "
                          "quadrature + covariance; numpy BLAS threads" % (m, dt)}
+
+    if post is not None and not args.no_batching:
+        r["coef"] = coef = None
+        torch.cuda.empty_cache()
+        post["batching"] = batching_run(dev, head)
 
     # every stage against its own roof: the FFT / NUFFT stages against the FP32
     # FFMA peak, the contractions against the tensor-core peak of their input

@@ -43,6 +43,23 @@ PRECISION_L128 = StackSpec(n=100000, L=128, R=64.0, n_blobs=12, width=(2.0, 8.0)
 DIFF_L256 = StackSpec(n=4096, L=256, R=128.0, n_blobs=12, width=(4.0, 16.0), snr=1 / 10, seed=20141207)
 
 
+def batching_stacks(S=48, n_range=(500, 20000), sizes=(64, 96, 128, 180, 256), seed=20141206):
+    """The batching workload: S independent stacks, stack s drawn from a
+    numpy generator seeded with ``seed``: L uniform in ``sizes``, R = L/2,
+    c = 1/2, n uniform in ``n_range`` (inclusive), SNR uniform in [1/50, 1/5];
+    12 blobs of widths [2, 8] L/128 px; the stack's own images use seed
+    ``seed + 1000 s``.  Returns a list of StackSpec."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(S):
+        L = int(rng.choice(sizes))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        snr = float(rng.uniform(1 / 50, 1 / 5))
+        out.append(StackSpec(n, L, L / 2, 12, (2.0 * L / 128, 8.0 * L / 128), snr, seed + 1000 * s))
+    return out
+
+
 def pixel_index(L, device="cpu", dtype=torch.float64):
     return torch.arange(L, device=device, dtype=dtype) - (L // 2)
 

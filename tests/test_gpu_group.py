@@ -7,6 +7,8 @@ coefficients (Eqs. ck, ck_0); the expansion of sampled images of every stack
 against the oracle; the group's coefficients equal to ffb_expand's bit for
 bit, on the eager call and on the graph replays; the covariance equal to the
 single-plan path within float32 accumulation error."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -152,3 +154,46 @@ def test_group_rejects_bad_membership(dev):
         g.expand_cov([x, None], [c, None])
     assert ei.value.status == -7          # FFB_ERR_STATE
     g.close()
+
+
+def test_batching_workload_48_stacks_against_oracle(dev):
+    """The batching workload's 48 stacks (seeded recipe: L drawn from
+    {64, 96, 128, 180, 256}, R = L/2, SNR uniform in [1/50, 1/5]) with every
+    stack's n cut to 1/100 of the recipe's (5 to 200 images), BF16x3 (float32
+    path with compensated tensor-core GEMMs): one group call eager, one
+    capturing, one replayed.  Every stack's first and last image against the
+    FP64 oracle's expansion; every coefficient of the replay bit-equal to
+    ffb_expand's; the grouped covariance against the oracle's covariance of
+    the group's own coefficients (Eqs. ck, ck_0)."""
+    from dataclasses import replace
+    specs = [replace(sp, n=max(5, sp.n // 100)) for sp in data.batching_stacks()]
+    assert len(specs) == 48 and {sp.L for sp in specs} == {64, 96, 128, 180, 256}
+    imgs = [data.blob_stack(sp, device=dev)[0] for sp in specs]
+    plans = [Plan(sp.L, sp.c, sp.R, eps=1e-6, precision="bf16x3") for sp in specs]
+    coefs = [torch.empty((sp.n, p.P, 2), device=dev) for sp, p in zip(specs, plans)]
+    g = Group(plans)
+    for _ in range(3):
+        g.expand_cov(imgs, coefs, reset=True)
+    g.sync()
+    info = g.info()
+    assert info["eager"] == 1 and info["graphs"] == 1 and info["replays"] == 2
+    for s, (sp, p, x, c) in enumerate(zip(specs, plans, imgs, coefs)):
+        ref = Plan(sp.L, sp.c, sp.R, eps=1e-6, precision="bf16x3")
+        assert torch.equal(c, ref.expand(x)), "stack %d: group != ffb_expand" % s
+        ref.close()
+        op = fb.make_plan(sp.L, sp.c, sp.R)
+        a = torch.view_as_complex(c.cpu()).numpy().astype(np.complex128)
+        pick = [0, sp.n - 1]
+        ao = fb.expand(op, x[pick].double().cpu().numpy())
+        err = np.linalg.norm(a[pick] - ao) / np.linalg.norm(ao)
+        assert err <= 1e-5, "stack %d (L = %d): coefficients vs oracle %.2e" % (s, sp.L, err)
+        m_ref, blocks = fb.covariance(op, a)
+        m, C = p.cov_get()
+        Cb = [b.numpy() for b in p.unpack_blocks(C.cpu())]
+        num = sum(np.linalg.norm(x1 - x2) ** 2 for x1, x2 in zip(Cb, blocks))
+        den = sum(np.linalg.norm(x2) ** 2 for x2 in blocks)
+        assert math.sqrt(num / den) <= 1e-5, "stack %d: covariance vs oracle" % s
+        assert np.linalg.norm(m.cpu().numpy() - m_ref) <= 1e-5 * np.linalg.norm(m_ref)
+    g.close()
+    for p in plans:
+        p.close()
