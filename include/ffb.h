@@ -377,7 +377,14 @@ int64_t ffb_launch_count(ffb_plan_t plan);
  * Sec. IV notes that the expansion and the covariance are sums over images
  * that may be split among workers.  A group runs S independent stacks
  * (1 <= S <= 64), each with its own plan, through a1-a7 in one call:
- *   - each stack's expansion (a1-a5) runs on its own branch stream;
+ *   - each stack's expansion (a1-a4) runs on its own branch stream; with a
+ *     tensor-core precision the call proceeds in rounds, round r taking the
+ *     r-th group of chunks of every stack that has one (the chunks one
+ *     quadrature launch of ffb_expand would take), and the radial quadrature
+ *     (a5, Eq. a) of a round is ONE persistent launch over the (stack, k,
+ *     M tile) items of all its stacks: a grouped GEMM over the uneven
+ *     p_k x n_xi blocks of every stack, the stacks' TMA descriptors in
+ *     device memory (FFB_FP32 plans run a5 per stack on their branches);
  *   - the covariance of all stacks (a6/a7) is ONE persistent launch over the
  *     (stack, k block, image range) items of every stack: a grouped SYRK over
  *     the uneven per-k block sizes p_k (tensor cores in the plans' precision,
@@ -386,7 +393,9 @@ int64_t ffb_launch_count(ffb_plan_t plan);
  *     eagerly; once per group it also times the candidate item shapes of the
  *     grouped launch (images per item, images per tensor-core tile, grid) on
  *     that call's coefficients, accumulating into scratch, and keeps the
- *     fastest (ffb_group_tuning lists them); the second call with the same
+ *     fastest (ffb_group_tuning lists them), and times the launch shapes of
+ *     the grouped quadrature (CTAs per SM, pipeline stages) on the call's
+ *     first round (ffb_group_quad_tuning); the second call with the same
  *     arguments captures the launches into a CUDA graph; later ones replay it.
  * Results are those of ffb_expand + ffb_covariance on each plan: the same
  * coefficients bit for bit; the covariance accumulated in another order.
@@ -421,10 +430,19 @@ int ffb_group_covariance(ffb_group_t group, const float *const *h_coef, const in
  * of the grouped launches or of any member plan. */
 int ffb_group_sync(ffb_group_t group, void *stream);
 
-/* ffb_group_info -- h_info[10]: S, precision, tuned images per item, tuned
+/* ffb_group_info -- h_info[14]: S, precision, tuned images per item, tuned
  * images per tensor-core tile, tuned grid (CTAs), graphs instantiated, graph
- * replays, eager calls, kernel launches of the last call, tuning candidates. */
+ * replays, eager calls, kernel launches of the last call, tuning candidates;
+ * then for the grouped quadrature: tuned CTAs per SM, tuned pipeline stages,
+ * its tuning candidates, grouped quadrature launches (rounds) of the last
+ * call shape (0 for FFB_FP32 groups). */
 int ffb_group_info(ffb_group_t group, int64_t *h_info);
+
+/* ffb_group_quad_tuning -- the timed launch shapes of the grouped quadrature
+ * (up to max): CTAs per SM, pipeline stages, milliseconds of one launch on
+ * the first round of the tuning call.  Returns the number written (a
+ * negative ffb_status on error). */
+int ffb_group_quad_tuning(ffb_group_t group, int max, int *h_per_sm, int *h_stages, float *h_ms);
 
 /* ffb_group_tuning -- the timed candidates (up to max): images per item,
  * images per tile, grid, milliseconds of one grouped launch.  Returns the

@@ -81,35 +81,44 @@ extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *
 }
 
 // a1-a5 launches for n images on stream s (arguments already validated)
+// a1-a4 of the images [g0, g1), one group of at most ffb_tc_group chunks,
+// into the operands of the radial quadrature (the tensor-core planes, or the
+// float32 spectra of the FP32 path)
+int ffb_expand_part(ffb_plan_t p, const float *d_images, int64_t g0, int64_t g1, cudaStream_t s) {
+    RingOut ring{FFB_FMT_F32, p->d_Fhat, nullptr, p->n_xi, p->chunk};
+    if (p->precision != FFB_FP32) CK(ffb_tc_prepare(p, s, &ring));
+    const size_t es = (ring.fmt == FFB_FMT_BF16 || ring.fmt == FFB_FMT_BF16X2) ? 2 : 4;
+    for (int64_t i0 = g0; i0 < g1; i0 += p->chunk) {
+        int m = (int)std::min<int64_t>(p->chunk, g1 - i0);
+        if (p->fused) {
+            // chunks after the first follow this call's own kernels
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0));
+            RingOut r = ring;   // this chunk's images in the group's planes
+            const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
+            r.p0 = (char *)ring.p0 + off;
+            if (ring.p1) r.p1 = (char *)ring.p1 + off;
+            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
+        } else {
+            CK(ffb_launch_grid(p, d_images, i0, m, s));
+            CK(ffb_launch_interp_ring(p, m, s));
+        }
+    }
+    return FFB_OK;
+}
+
 int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef, cudaStream_t s) {
     if (n == 0) return FFB_OK;
     CK(ffb_ensure_scratch(p));
-    RingOut ring{FFB_FMT_F32, p->d_Fhat, nullptr, p->n_xi, p->chunk};
     int grp = 1;
     if (p->precision != FFB_FP32) {
-        CK(ffb_tc_prepare(p, s, &ring));
+        CK(ffb_tc_prepare(p, s, nullptr));
         grp = ffb_tc_group(p);
     }
-    const size_t es = (ring.fmt == FFB_FMT_BF16 || ring.fmt == FFB_FMT_BF16X2) ? 2 : 4;
     // groups of grp chunks: polar transform and ring FFT per chunk, one
     // quadrature launch per group
     for (int64_t g0 = 0; g0 < n; g0 += (int64_t)grp * p->chunk) {
         const int64_t g1 = std::min<int64_t>(n, g0 + (int64_t)grp * p->chunk);
-        for (int64_t i0 = g0; i0 < g1; i0 += p->chunk) {
-            int m = (int)std::min<int64_t>(p->chunk, g1 - i0);
-            if (p->fused) {
-                // chunks after the first follow this call's own kernels
-                CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0));
-                RingOut r = ring;   // this chunk's images in the group's planes
-                const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
-                r.p0 = (char *)ring.p0 + off;
-                if (ring.p1) r.p1 = (char *)ring.p1 + off;
-                CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
-            } else {
-                CK(ffb_launch_grid(p, d_images, i0, m, s));
-                CK(ffb_launch_interp_ring(p, m, s));
-            }
-        }
+        CK(ffb_expand_part(p, d_images, g0, g1, s));
         CK(ffb_launch_bessel(p, (int)(g1 - g0), d_coef + (size_t)g0 * p->P * 2, p->fused != 0, s));
     }
     return FFB_OK;

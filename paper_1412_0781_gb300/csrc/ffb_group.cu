@@ -39,12 +39,20 @@ struct Key {
     }
 };
 
+struct Round {
+    int S = 0;                          // stacks with images in this round
+    int nitems = 0;                     // (stack, k, M tile) items of the grouped quadrature
+    size_t first = 0;                   // index of the round's first stack descriptor
+};
+
 struct Entry {
     Key key;
     int seen = 0;                       // calls so far with this key
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> plan_launches; // kernel launches per call, per plan
-    int64_t group_launches = 0;         // the grouped covariance launches per call
+    int64_t group_launches = 0;         // the grouped launches per call
+    std::vector<Round> rounds;          // grouped quadrature rounds (tensor-core groups)
+    void *d_desc = nullptr;             // their stack descriptors, device memory
 };
 
 struct Cand {
@@ -68,14 +76,24 @@ struct ffb_group_s {
     // autotuner
     int tuned = 0, per = 0, tile = 32, grid = 0;
     std::vector<Cand> cands;
+    // grouped quadrature: widest block of the members, launch shape (CTAs per
+    // SM, pipeline stages) chosen by the tuner, and its timings
+    int BNmax = 0, q_tuned = 0, q_per_sm = 1, q_nst = 0;
+    std::vector<Cand> qcands;           // per = CTAs per SM, tile = stages
     // graph cache
     std::vector<Entry> cache;
     int64_t graphs = 0, replays = 0, eager = 0, last_launches = 0;
 };
 
+static void drop_entry(Entry &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.d_desc) cudaFree(e.d_desc);
+    e.exec = nullptr;
+    e.d_desc = nullptr;
+}
+
 static void release(ffb_group_t g) {
-    for (Entry &e : g->cache)
-        if (e.exec) cudaGraphExecDestroy(e.exec);
+    for (Entry &e : g->cache) drop_entry(e);
     for (cudaStream_t s : g->br)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : g->join)
@@ -123,6 +141,15 @@ extern "C" int ffb_group_create(ffb_group_t *out, int S, const ffb_plan_t *plans
         for (ffb_plan_t p : g->plans) len = std::max(len, (size_t)p->cov_total + p->p[0]);
         g->scratch_len = len;
         e = ffb_check_cuda(cudaMalloc(&g->d_scratch, sizeof(double) * len));
+    }
+    if (!e && prec != FFB_FP32) {
+        for (ffb_plan_t p : g->plans) g->BNmax = std::max(g->BNmax, ffb_tc_bn(p));
+        int per_sm[4], nst[4];
+        if (ffb_tc_group_shapes(prec, g->BNmax, per_sm, nst) <= 0) e = FFB_ERR_UNSUPPORTED;
+        else {
+            g->q_per_sm = per_sm[0];
+            g->q_nst = nst[0];
+        }
     }
     if (!e) e = ffb_check_cuda(cudaStreamSynchronize(s));
     if (e) {
@@ -202,12 +229,91 @@ static int tune(ffb_group_t g, const Key &k, cudaStream_t s) {
     return FFB_OK;
 }
 
+// images per round of stack i: one group of chunks of its plan
+static int64_t round_images(ffb_plan_t p) { return (int64_t)ffb_tc_group(p) * p->chunk; }
+
+// the rounds of a tensor-core group call: round r holds the r-th group of
+// chunks of every stack that has one, its stacks' descriptors packed with
+// rising item numbers; built once per call shape (outside any capture)
+static int build_rounds(ffb_group_t g, const Key &k, Entry *ent) {
+    const size_t sb = ffb_tc_stack_bytes();
+    std::vector<unsigned char> host;
+    int nr = 0;
+    for (int i = 0; i < g->S; ++i)
+        if (k.n[i] > 0) nr = std::max<int64_t>(nr, (k.n[i] + round_images(g->plans[i]) - 1) / round_images(g->plans[i]));
+    ent->rounds.assign(nr, Round());
+    for (int r = 0; r < nr; ++r) {
+        Round &R = ent->rounds[r];
+        R.first = host.size() / sb;
+        for (int i = 0; i < g->S; ++i) {
+            ffb_plan_t p = g->plans[i];
+            const int64_t per = round_images(p), g0 = (int64_t)r * per;
+            if (k.n[i] <= g0) continue;
+            const int64_t g1 = std::min<int64_t>(k.n[i], g0 + per);
+            host.resize(host.size() + sb);
+            int items = 0;
+            CKG(ffb_tc_stack_fill(p, (float *)k.coef[i] + (size_t)g0 * p->P * 2, (int)(g1 - g0), R.nitems,
+                                  host.data() + host.size() - sb, &items));
+            R.nitems += items;
+            R.S++;
+        }
+    }
+    if (host.empty()) return FFB_OK;
+    CKG(ffb_check_cuda(cudaMalloc(&ent->d_desc, host.size())));
+    return ffb_check_cuda(cudaMemcpy(ent->d_desc, host.data(), host.size(), cudaMemcpyHostToDevice));
+}
+
+static int quad_launch(ffb_group_t g, const Entry *ent, int r, int per_sm, int nst, cudaStream_t s) {
+    const Round &R = ent->rounds[r];
+    const char *d = (const char *)ent->d_desc + R.first * ffb_tc_stack_bytes();
+    return ffb_tc_group_bessel(g->precision, d, R.S, R.nitems, g->BNmax, per_sm, nst, g->d_status,
+                               g->plans[0]->wait_budget, s);
+}
+
+// times the launch shapes of the grouped quadrature on round r of this call
+// (its operands are ready; every run writes the same coefficients) and keeps
+// the fastest
+static int tune_quad(ffb_group_t g, const Entry *ent, int r, cudaStream_t s) {
+    int per_sm[4], nst[4];
+    const int nc = ffb_tc_group_shapes(g->precision, g->BNmax, per_sm, nst);
+    cudaEvent_t a, b;
+    CKG(ffb_check_cuda(cudaEventCreate(&a)));
+    CKG(ffb_check_cuda(cudaEventCreate(&b)));
+    std::vector<Cand> cands;
+    for (int c = 0; c < nc; ++c) cands.push_back({per_sm[c], nst[c], 0, 0.f});
+    int e = FFB_OK;
+    for (int c = 0; c <= nc && !e; ++c) {
+        const Cand &cd = cands[c == 0 ? 0 : c - 1];   // the first shape runs twice (warm-up)
+        e = ffb_check_cuda(cudaEventRecord(a, s));
+        if (!e) e = quad_launch(g, ent, r, cd.per, cd.tile, s);
+        if (!e) e = ffb_check_cuda(cudaEventRecord(b, s));
+        if (!e) e = ffb_check_cuda(cudaEventSynchronize(b));
+        float ms = 0.f;
+        if (!e) e = ffb_check_cuda(cudaEventElapsedTime(&ms, a, b));
+        if (c > 0) cands[c - 1].ms = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e) return e;
+    size_t best = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+        if (cands[c].ms < cands[best].ms) best = c;
+    g->q_per_sm = cands[best].per;
+    g->q_nst = cands[best].tile;
+    g->qcands = cands;
+    g->q_tuned = 1;
+    return FFB_OK;
+}
+
 // the launches of one call on stream `main` (the user's stream, or the
-// capture stream); each stack's expansion on its branch
-static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent) {
+// capture stream); each stack's expansion on its branch.  Tensor-core groups
+// run in rounds: every stack's next group of chunks through a1-a4 on its
+// branch, then one grouped quadrature launch over all of them
+static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent, bool count) {
     std::vector<int64_t> before(g->S);
     for (int i = 0; i < g->S; ++i) before[i] = g->plans[i]->launches;
-    if (k.mode == 1) {
+    int64_t gl = 0;
+    if (k.mode == 1 && g->precision == FFB_FP32) {
         CKG(ffb_check_cuda(cudaEventRecord(g->fork, main)));
         for (int i = 0; i < g->S; ++i) {
             if (k.n[i] <= 0) continue;
@@ -215,6 +321,24 @@ static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent) {
             CKG(ffb_expand_on(g->plans[i], (const float *)k.images[i], k.n[i], (float *)k.coef[i], g->br[i]));
             CKG(ffb_check_cuda(cudaEventRecord(g->join[i], g->br[i])));
             CKG(ffb_check_cuda(cudaStreamWaitEvent(main, g->join[i], 0)));
+        }
+    } else if (k.mode == 1) {
+        for (size_t r = 0; r < ent->rounds.size(); ++r) {
+            CKG(ffb_check_cuda(cudaEventRecord(g->fork, main)));
+            for (int i = 0; i < g->S; ++i) {
+                ffb_plan_t p = g->plans[i];
+                const int64_t per = round_images(p), g0 = (int64_t)r * per;
+                if (k.n[i] <= g0) continue;
+                const int64_t g1 = std::min<int64_t>(k.n[i], g0 + per);
+                CKG(ffb_check_cuda(cudaStreamWaitEvent(g->br[i], g->fork, 0)));
+                CKG(ffb_expand_part(p, (const float *)k.images[i], g0, g1, g->br[i]));
+                if (!p->fused) CKG(ffb_tc_split_planes(p, g->br[i]));
+                CKG(ffb_check_cuda(cudaEventRecord(g->join[i], g->br[i])));
+                CKG(ffb_check_cuda(cudaStreamWaitEvent(main, g->join[i], 0)));
+            }
+            if (!g->q_tuned) CKG(tune_quad(g, ent, (int)r, main));
+            CKG(quad_launch(g, ent, (int)r, g->q_per_sm, g->q_nst, main));
+            ++gl;
         }
     }
     for (int i = 0; i < g->S; ++i) {
@@ -227,12 +351,11 @@ static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent) {
     if (!g->tuned) CKG(tune(g, k, main));
     CovGroup cg;
     build_table(g, k, g->per, g->tile, false, &cg);
-    int64_t gl = 0;
     if (cg.nitems > 0) {
         CKG(ffb_launch_cov_group(g->precision, cg, g->grid, g->d_status, main));
-        gl = 1;
+        ++gl;
     }
-    if (ent) {
+    if (count) {
         ent->plan_launches.resize(g->S);
         for (int i = 0; i < g->S; ++i) ent->plan_launches[i] = g->plans[i]->launches - before[i];
         ent->group_launches = gl;
@@ -252,17 +375,20 @@ static int call(ffb_group_t g, Key &k, cudaStream_t s) {
         if (e.key == k) ent = &e;
     if (!ent) {
         if (g->cache.size() >= 8) {   // keep the cache small: drop the oldest
-            if (g->cache.front().exec) cudaGraphExecDestroy(g->cache.front().exec);
+            drop_entry(g->cache.front());
             g->cache.erase(g->cache.begin());
         }
         g->cache.push_back(Entry());
         ent = &g->cache.back();
         ent->key = k;
+        // the grouped quadrature's rounds and descriptors (allocated here,
+        // never inside a capture)
+        if (k.mode == 1 && g->precision != FFB_FP32) CKG(build_rounds(g, k, ent));
     }
     int e = FFB_OK;
     if (ent->seen == 0) {
         // first call with this key: eager (sets kernel attributes, tunes once)
-        e = run(g, k, s, ent);
+        e = run(g, k, s, ent, true);
         g->eager++;
     } else {
         if (!ent->exec) {
@@ -276,7 +402,7 @@ static int call(ffb_group_t g, Key &k, cudaStream_t s) {
             cudaGraph_t graph = nullptr;
             e = ffb_check_cuda(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
             if (!e) {
-                const int er = run(g, k, g->cap, nullptr);
+                const int er = run(g, k, g->cap, ent, false);
                 const int ee = ffb_check_cuda(cudaStreamEndCapture(g->cap, &graph));
                 e = er ? er : ee;
             }
@@ -375,7 +501,22 @@ extern "C" int ffb_group_info(ffb_group_t g, int64_t *h_info) {
     h_info[7] = g->eager;
     h_info[8] = g->last_launches;
     h_info[9] = (int64_t)g->cands.size();
+    h_info[10] = g->q_per_sm;
+    h_info[11] = g->q_nst;
+    h_info[12] = (int64_t)g->qcands.size();
+    h_info[13] = g->cache.empty() ? 0 : (int64_t)g->cache.back().rounds.size();
     return FFB_OK;
+}
+
+extern "C" int ffb_group_quad_tuning(ffb_group_t g, int max, int *h_per_sm, int *h_stages, float *h_ms) {
+    if (!g || max < 0) return FFB_ERR_ARG;
+    const int n = std::min<int>(max, (int)g->qcands.size());
+    for (int i = 0; i < n; ++i) {
+        if (h_per_sm) h_per_sm[i] = g->qcands[i].per;
+        if (h_stages) h_stages[i] = g->qcands[i].tile;
+        if (h_ms) h_ms[i] = g->qcands[i].ms;
+    }
+    return n;
 }
 
 extern "C" int ffb_group_tuning(ffb_group_t g, int max, int *h_per, int *h_tile, int *h_grid, float *h_ms) {

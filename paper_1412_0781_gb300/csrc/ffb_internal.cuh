@@ -369,6 +369,19 @@ int ffb_tc_prepare(ffb_plan_t plan, cudaStream_t s, RingOut *out);
 // chunks whose ring spectra one tensor-core quadrature launch takes (>= 1;
 // valid after ffb_tc_prepare)
 int ffb_tc_group(ffb_plan_t plan);
+// grouped tensor-core quadrature over several plans (ffb_tc.cu): descriptor
+// size, the plan's padded block width, one stack's descriptor (host memory),
+// the launch shapes to tune over, the launch
+size_t ffb_tc_stack_bytes();
+int ffb_tc_bn(ffb_plan_t plan);
+int ffb_tc_stack_fill(ffb_plan_t plan, float *coef, int nimg, int item0, void *dst, int *nitems);
+int ffb_tc_group_shapes(int precision, int BNmax, int *per_sm, int *nst);
+int ffb_tc_group_bessel(int precision, const void *d_stacks, int S, int nitems, int BNmax, int per_sm, int nst,
+                        int *status, long long wait_budget, cudaStream_t s);
+int ffb_tc_split_planes(ffb_plan_t plan, cudaStream_t s);
+// a1-a4 of images [g0, g1) (one group of chunks) into the plan's quadrature
+// operands, without the quadrature (ffb_api.cu)
+int ffb_expand_part(ffb_plan_t plan, const float *d_images, int64_t g0, int64_t g1, cudaStream_t s);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);

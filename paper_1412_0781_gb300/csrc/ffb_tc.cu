@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "ffb_internal.cuh"
 #include "ffb_tc.cuh"
@@ -94,25 +95,52 @@ __global__ void k_split_planes(const float *__restrict__ src, int64_t total, int
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TCB_EPI) : "memory"); }
 
-// Persistent: CTA b takes items b, b + gridDim.x, ... of the (k, M tile)
-// list (item = k nM + m; M tile m = images 64 m .. 64 m + 63, rows image x
-// re/im).  For every item the producer streams the K chunks of A and B
-// (hi/lo planes) through a ring of nst stages (full/empty mbarriers); the MMA
-// thread accumulates each item into one of two TMEM accumulators and commits
-// it to the epilogue (accf), which drains it with tcgen05.ld into a padded
-// [64 images][BN q][re, im] stage, releases the accumulator (acce) and
-// writes the coefficients as contiguous runs per image.
-template <int KIND, int NPA, int NPB, int NPROD>
+// One stack of a quadrature launch: the TMA maps of its ring-spectrum planes
+// (A, hi and lo) and of its padded radial table (B, hi and lo), and where its
+// items' coefficients go.  A single plan's launch passes one as a kernel
+// parameter; a group's launch reads an array of them from device memory
+// (written once per group call shape), stack s owning items
+// item0 .. item0 + (k_max + 1) nM - 1.
+struct TcStack {
+    CUtensorMap mA0, mA1, mB0, mB1;
+    const int *pk, *off;   // p_k and coefficient offsets of the stack's plan (device)
+    float *coef;           // coefficients of the launch's first image of the stack
+    int P, nimg, nM, NCH;  // coefficients per image, images, M tiles, 128-byte K chunks
+    int item0;
+    int BN;                // rows of the B map's box (<= the launch's BNmax)
+    int pad_[2];
+};
+
+// the stack of `item`: the launch's one stack, or, in a group, the last stack
+// whose first item is <= item (a CTA's items rise, so the search only moves on)
+template <bool GROUP>
+__device__ __forceinline__ const TcStack *tc_stack_of(const TcStack &one, const TcStack *__restrict__ many, int S,
+                                                      int item, int &s) {
+    if constexpr (!GROUP) {
+        return &one;
+    } else {
+        while (s + 1 < S && item >= __ldg(&many[s + 1].item0)) ++s;
+        return &many[s];
+    }
+}
+
+// Persistent: CTA b takes items b, b + gridDim.x, ... of the (stack, k, M
+// tile) list (item = item0 + k nM + m; M tile m = images 64 m .. 64 m + 63,
+// rows image x re/im).  For every item the producer streams the K chunks of
+// A and B (hi/lo planes) through a ring of nst stages (full/empty
+// mbarriers); the MMA thread accumulates each item into one of two TMEM
+// accumulators and commits it to the epilogue (accf), which drains it with
+// tcgen05.ld into a padded [64 images][BN q][re, im] stage, releases the
+// accumulator (acce) and writes the coefficients as contiguous runs per
+// image.  BNmax and acc_cols cover the widest stack of the launch.
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
 __global__ void __launch_bounds__(32 * TCB_WARPS)
-k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-            const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, int ld,
-            int nimg, const int *__restrict__ pk_, const int *__restrict__ off_, int P, float *__restrict__ coef,
-            int BNmax, int acc_cols, int nst, int nM, int nitems, int *status, long long wb) {
+k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ many, int S, int BNmax, int acc_cols,
+            int nst, int nitems, int *status, long long wb) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     constexpr int ES = (KIND == 0) ? 4 : 2;
     constexpr int KCH = 128 / ES;               // K elements per 128-byte row
-    const int NCH = ld / KCH;
     const uint32_t a_bytes = 128u * 128u;       // one plane, one K chunk, 128 rows
     const uint32_t b_bytes = (uint32_t)BNmax * 128u;
     const uint32_t st_bytes = NPA * a_bytes + NPB * b_bytes;   // one stage: every plane of one K chunk
@@ -150,21 +178,32 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             pdl_wait();   // the operand planes come from the previous kernels
             int64_t g = 0;
             bool ok = true;
+            int si = 0, seen = -1;
             for (int it = 0; it < myitems && ok && *(volatile int *)okflag; ++it) {
                 const int item = blockIdx.x + it * gridDim.x;
-                const int k = item / nM, m = item - k * nM;
+                const TcStack *st = tc_stack_of<GROUP>(one, many, S, item, si);
+                if (GROUP && si != seen) {   // maps written to device memory before the launch
+                    tc::tmap_acquire(&st->mA0);
+                    tc::tmap_acquire(&st->mA1);
+                    tc::tmap_acquire(&st->mB0);
+                    tc::tmap_acquire(&st->mB1);
+                    seen = si;
+                }
+                const int local = item - st->item0, nM = st->nM, NCH = st->NCH;
+                const int k = local / nM, m = local - k * nM;
                 for (int ch = 0; ch < NCH; ++ch, ++g) {
-                    const int si = (int)(g % nst);
-                    if (g >= nst && !tc::mbar_wait(&empty[si], (uint32_t)(((g / nst) - 1) & 1), wb)) {
+                    const int stg = (int)(g % nst);
+                    if (g >= nst && !tc::mbar_wait(&empty[stg], (uint32_t)(((g / nst) - 1) & 1), wb)) {
                         ok = false;
                         break;
                     }
-                    uint8_t *st = sm + (size_t)si * st_bytes;
-                    tc::mbar_arrive_expect_tx(&full[si], st_bytes);
-                    tc::tma_load_3d(st, &mapA0, &full[si], ch * KCH, 128 * m, k);
-                    if (NPA > 1) tc::tma_load_3d(st + a_bytes, &mapA1, &full[si], ch * KCH, 128 * m, k);
-                    tc::tma_load_3d(st + NPA * a_bytes, &mapB0, &full[si], ch * KCH, 0, k);
-                    if (NPB > 1) tc::tma_load_3d(st + NPA * a_bytes + b_bytes, &mapB1, &full[si], ch * KCH, 0, k);
+                    uint8_t *sb = sm + (size_t)stg * st_bytes;
+                    // the stage holds BNmax rows of B; this stack's box fills BN of them
+                    tc::mbar_arrive_expect_tx(&full[stg], NPA * a_bytes + NPB * (uint32_t)st->BN * 128u);
+                    tc::tma_load_3d(sb, &st->mA0, &full[stg], ch * KCH, 128 * m, k);
+                    if (NPA > 1) tc::tma_load_3d(sb + a_bytes, &st->mA1, &full[stg], ch * KCH, 128 * m, k);
+                    tc::tma_load_3d(sb + NPA * a_bytes, &st->mB0, &full[stg], ch * KCH, 0, k);
+                    if (NPB > 1) tc::tma_load_3d(sb + NPA * a_bytes + b_bytes, &st->mB1, &full[stg], ch * KCH, 0, k);
                 }
             }
             if (!ok) {
@@ -180,11 +219,23 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             int64_t g = 0;
             bool ok = true;
             int it = 0;
-            // p_k of the next item is loaded one item ahead, off the MMA stream
-            int pk_next = (myitems > 0) ? __ldg(&pk_[blockIdx.x / nM]) : 0;
+            int si = 0;
+            // p_k and the K chunks of the next item are loaded one item ahead,
+            // off the MMA stream
+            int pk_next = 0, nch_next = 0;
+            if (myitems > 0) {
+                const TcStack *st = tc_stack_of<GROUP>(one, many, S, blockIdx.x, si);
+                pk_next = __ldg(&st->pk[(blockIdx.x - st->item0) / st->nM]);
+                nch_next = st->NCH;
+            }
             for (; it < myitems && ok; ++it) {
-                const int pk = pk_next;
-                if (it + 1 < myitems) pk_next = __ldg(&pk_[(blockIdx.x + (it + 1) * gridDim.x) / nM]);
+                const int pk = pk_next, NCH = nch_next;
+                if (it + 1 < myitems) {
+                    const int item1 = blockIdx.x + (it + 1) * gridDim.x;
+                    const TcStack *st = tc_stack_of<GROUP>(one, many, S, item1, si);
+                    pk_next = __ldg(&st->pk[(item1 - st->item0) / st->nM]);
+                    nch_next = st->NCH;
+                }
                 const int BN = max(16, (pk + 15) & ~15);
                 const uint32_t id = tc::idesc(KIND == 0 ? 2 : 1, 128, BN);
                 const int a = it & 1;
@@ -195,13 +246,13 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                 tc::fence_after_sync();
                 const uint32_t dt = tbase + (uint32_t)(a * acc_cols);
                 for (int ch = 0; ch < NCH; ++ch, ++g) {
-                    const int si = (int)(g % nst);
-                    if (!tc::mbar_wait(&full[si], (uint32_t)((g / nst) & 1), wb)) {
+                    const int stg = (int)(g % nst);
+                    if (!tc::mbar_wait(&full[stg], (uint32_t)((g / nst) & 1), wb)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t sa = tc::smem_u32(sm + (size_t)si * st_bytes);
+                    const uint32_t sa = tc::smem_u32(sm + (size_t)stg * st_bytes);
 #pragma unroll
                     for (int pr = 0; pr < NPROD; ++pr) {
                         const int pa = (pr == 2) ? 1 : 0;   // products (0,0), (0,1), (1,0)
@@ -217,7 +268,7 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
                             else tc::mma_bf16(dt, ad, bd, id, accf_);
                         }
                     }
-                    tc::mma_commit(&empty[si]);
+                    tc::mma_commit(&empty[stg]);
                 }
                 if (!ok) break;
                 tc::mma_commit(&accf[a]);
@@ -234,10 +285,13 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
         const int cg = (warp - 2) >> 2;                   // which column groups of 16
         const int r = 32 * q4 + lane;                     // accumulator row: image r/2, part r%2
         const int et = threadIdx.x - 64;                  // 0 .. 32 TCB_EPI - 1
+        int si = 0;
         for (int it = 0; it < myitems; ++it) {
             const int item = blockIdx.x + it * gridDim.x;
-            const int k = item / nM, m = item - k * nM;
-            const int pk = pk_[k], o = off_[k];
+            const TcStack *st = tc_stack_of<GROUP>(one, many, S, item, si);
+            const int local = item - st->item0, nM = st->nM;
+            const int k = local / nM, m = local - k * nM;
+            const int pk = __ldg(&st->pk[k]), o = __ldg(&st->off[k]);
             const int BN = max(16, (pk + 15) & ~15);
             const int a = it & 1;
             // after a failure elsewhere, stop waiting long (the loop count stays
@@ -263,8 +317,9 @@ k_tc_bessel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ C
             epi_bar();                                    // the stage holds the item
             if (ok) {
                 const int i0 = 64 * m;
-                const int nimg_t = min(64, nimg - i0);
-                float2 *out = (float2 *)coef;
+                const int nimg_t = min(64, st->nimg - i0);
+                const int P = st->P;
+                float2 *out = (float2 *)st->coef;
                 // t / pk as a multiply-high (exact for t < 2^32 / pk); pk = 1
                 // would overflow the multiplier and is taken as is
                 const unsigned magic = (pk > 1) ? 0xFFFFFFFFu / (unsigned)pk + 1u : 0u;
@@ -322,7 +377,7 @@ struct TcState {
     int grp = 1;                           // chunks per quadrature launch
     void *bhi = nullptr, *blo = nullptr;   // padded radial tables [k][BN][ld]
     void *ahi = nullptr, *alo = nullptr;   // ring spectra planes [k][2 grp chunk][ld]
-    CUtensorMap mA0, mA1, mB0, mB1;
+    TcStack one;                           // maps and plan fields of this plan's launches
 };
 
 static TcState *tc_state(ffb_plan_t p) {
@@ -420,10 +475,17 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
         p->launches++;
         if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
         const uint64_t rows = 2ull * t->grp * p->chunk;
-        if ((e = make_map(&t->mA0, t->ahi, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
-        if ((e = make_map(&t->mA1, t->alo, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
-        if ((e = make_map(&t->mB0, t->bhi, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
-        if ((e = make_map(&t->mB1, t->blo, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
+        TcStack &o = t->one;
+        std::memset(&o, 0, sizeof o);
+        if ((e = make_map(&o.mA0, t->ahi, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
+        if ((e = make_map(&o.mA1, t->alo, bf16, t->ld, rows, p->k_max + 1, 128))) return e;
+        if ((e = make_map(&o.mB0, t->bhi, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
+        if ((e = make_map(&o.mB1, t->blo, bf16, t->ld, t->BN, p->k_max + 1, t->BN))) return e;
+        o.pk = p->d_p;
+        o.off = p->d_off;
+        o.P = p->P;
+        o.NCH = t->ld / kch;
+        o.BN = t->BN;
         t->prepared = p->precision;
     }
     if (out) {
@@ -443,33 +505,37 @@ int ffb_tc_prepare(ffb_plan_t p, cudaStream_t s, RingOut *out) {
 
 int ffb_tc_group(ffb_plan_t p) { return p->tc ? ((TcState *)p->tc)->grp : 1; }
 
-template <int KIND, int NPA, int NPB, int NPROD>
-static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {
-    // two CTAs per SM when a two-stage ring fits in half the shared memory
-    // (their epilogues then overlap each other's loads), else one with the
-    // deepest ring that fits
-    int dev = 0, sms = 0, optin = 0;
+// launch shape of the quadrature: two CTAs per SM when a two-stage ring fits
+// in half the shared memory (their epilogues then overlap each other's
+// loads), else one with the deepest ring that fits
+static void tc_launch_shape(int prec, int BN, int *per_sm, int *nst) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    *per_sm = 1;
+    *nst = tc_stages(prec, 0, BN);
+    if (*nst > 0 && 2 * tc_smem_bytes(prec, BN, 2) + 2048 <= (size_t)optin) {
+        *per_sm = 2;
+        *nst = 2;
+    }
+}
+
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
+static int launch_tc_kernel(int prec, const TcStack &one, const TcStack *many, int S, int nitems, int BNmax,
+                            int acc_cols, int per_sm, int nst, int *status, long long wb, cudaStream_t s) {
+    if (nst <= 0 || nitems <= 0) return nitems <= 0 ? FFB_OK : FFB_ERR_UNSUPPORTED;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    int per_sm = 1, nst = tc_stages(p->precision, t->ld, t->BN);
-    if (nst <= 0) return FFB_ERR_UNSUPPORTED;
-    if (2 * tc_smem_bytes(p->precision, t->BN, 2) + 2048 <= (size_t)optin) {
-        per_sm = 2;
-        nst = 2;
-    }
-    const size_t smem = tc_smem_bytes(p->precision, t->BN, nst);
+    const size_t smem = tc_smem_bytes(prec, BNmax, nst);
     static int attr = 0;
     if (attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD>,
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         attr = (int)smem;
     }
-    const int nM = (2 * nimg + 127) / 128;
-    const int nitems = nM * (p->k_max + 1);
     const int grid = nitems < per_sm * sms ? nitems : per_sm * sms;   // persistent CTAs
-    ProfScope ps(p, FFB_KC_BESSEL, s);
     // launched with programmatic serialization: the prologue (barriers, TMEM)
     // overlaps the previous kernel's tail; the producer waits before its loads
     cudaLaunchConfig_t cfg = {};
@@ -480,19 +546,46 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const int e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD>, t->mA0, t->mA1, t->mB0,
-                                                    t->mB1, t->ld, nimg, (const int *)p->d_p, (const int *)p->d_off,
-                                                    p->P, d_coef_chunk, t->BN, t->tmem_cols, nst, nM, nitems,
-                                                    p->d_status, p->wait_budget));
+    return ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>, one, many, S, BNmax,
+                                             acc_cols, nst, nitems, status, wb));
+}
+
+template <bool GROUP>
+static int launch_tc_prec(int prec, const TcStack &one, const TcStack *many, int S, int nitems, int BNmax,
+                          int acc_cols, int per_sm, int nst, int *status, long long wb, cudaStream_t s) {
+    switch (prec) {
+        case FFB_TF32: return launch_tc_kernel<0, 1, 1, 1, GROUP>(prec, one, many, S, nitems, BNmax, acc_cols, per_sm, nst, status, wb, s);
+        case FFB_TF32X3: return launch_tc_kernel<0, 2, 2, 3, GROUP>(prec, one, many, S, nitems, BNmax, acc_cols, per_sm, nst, status, wb, s);
+        case FFB_BF16: return launch_tc_kernel<1, 1, 1, 1, GROUP>(prec, one, many, S, nitems, BNmax, acc_cols, per_sm, nst, status, wb, s);
+        case FFB_BF16X3: return launch_tc_kernel<1, 2, 2, 3, GROUP>(prec, one, many, S, nitems, BNmax, acc_cols, per_sm, nst, status, wb, s);
+        default: return FFB_ERR_ARG;
+    }
+}
+
+static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cudaStream_t s) {
+    int per_sm = 1, nst = 0;
+    tc_launch_shape(p->precision, t->BN, &per_sm, &nst);
+    if (nst <= 0) return FFB_ERR_UNSUPPORTED;
+    TcStack one = t->one;
+    one.coef = d_coef_chunk;
+    one.nimg = nimg;
+    one.nM = (2 * nimg + 127) / 128;
+    one.item0 = 0;
+    const int nitems = one.nM * (p->k_max + 1);
+    ProfScope ps(p, FFB_KC_BESSEL, s);
+    const int e = launch_tc_prec<false>(p->precision, one, nullptr, 1, nitems, t->BN, t->tmem_cols, per_sm, nst,
+                                        p->d_status, p->wait_budget, s);
     p->launches++;
     return e;
 }
 
-int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s) {
+// the separate-kernel path's float32 ring spectra of one chunk -> the
+// operand planes of the tensor-core quadrature
+int ffb_tc_split_planes(ffb_plan_t p, cudaStream_t s) {
     int e = ffb_tc_prepare(p, s, nullptr);
     if (e) return e;
     TcState *t = tc_state(p);
-    if (!planes_ready) {
+    {
         const int64_t total = (int64_t)(p->k_max + 1) * p->chunk * 2 * p->n_xi;
         const unsigned g = (unsigned)((total + 255) / 256);
         ProfScope ps(p, FFB_KC_BESSEL, s);
@@ -505,13 +598,70 @@ int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool plane
         p->launches++;
         if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
     }
-    switch (p->precision) {
-        case FFB_TF32: return launch_tc<0, 1, 1, 1>(p, t, nimg, d_coef_chunk, s);
-        case FFB_TF32X3: return launch_tc<0, 2, 2, 3>(p, t, nimg, d_coef_chunk, s);
-        case FFB_BF16: return launch_tc<1, 1, 1, 1>(p, t, nimg, d_coef_chunk, s);
-        case FFB_BF16X3: return launch_tc<1, 2, 2, 3>(p, t, nimg, d_coef_chunk, s);
-        default: return FFB_ERR_ARG;
+    return FFB_OK;
+}
+
+int ffb_launch_bessel_tc(ffb_plan_t p, int nimg, float *d_coef_chunk, bool planes_ready, cudaStream_t s) {
+    int e = ffb_tc_prepare(p, s, nullptr);
+    if (e) return e;
+    if (!planes_ready && (e = ffb_tc_split_planes(p, s))) return e;
+    return launch_tc(p, tc_state(p), nimg, d_coef_chunk, s);
+}
+
+// ---- grouped quadrature: the (stack, k, M tile) items of several plans in
+// one launch, the stacks' descriptors in device memory
+size_t ffb_tc_stack_bytes() { return sizeof(TcStack); }
+
+int ffb_tc_bn(ffb_plan_t p) { return p->tc ? ((TcState *)p->tc)->BN : 0; }
+
+// stack descriptor of plan p for nimg images whose coefficients start at
+// coef, its items numbered from item0 (host memory at dst); returns the
+// stack's item count through *nitems
+int ffb_tc_stack_fill(ffb_plan_t p, float *coef, int nimg, int item0, void *dst, int *nitems) {
+    if (!p->tc || ((TcState *)p->tc)->prepared != p->precision) return FFB_ERR_STATE;
+    TcStack st = ((TcState *)p->tc)->one;
+    st.coef = coef;
+    st.nimg = nimg;
+    st.nM = (2 * nimg + 127) / 128;
+    st.item0 = item0;
+    std::memcpy(dst, &st, sizeof st);
+    *nitems = st.nM * (p->k_max + 1);
+    return FFB_OK;
+}
+
+// launch shapes the group's tuner may time for stacks of width BNmax:
+// (CTAs per SM, pipeline stages); returns the count written (at most 4)
+int ffb_tc_group_shapes(int prec, int BNmax, int *per_sm, int *nst) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int deep = tc_stages(prec, 0, BNmax);
+    int n = 0;
+    for (int st = deep; st >= 2 && n < 3; --st) {
+        per_sm[n] = 1;
+        nst[n++] = st;
     }
+    if (deep >= 2 && 2 * tc_smem_bytes(prec, BNmax, 2) + 2048 <= (size_t)optin) {
+        per_sm[n] = 2;
+        nst[n++] = 2;
+    }
+    if (n == 0 && deep == 1) {
+        per_sm[0] = 1;
+        nst[0] = 1;
+        n = 1;
+    }
+    return n;
+}
+
+int ffb_tc_group_bessel(int prec, const void *d_stacks, int S, int nitems, int BNmax, int per_sm, int nst,
+                        int *status, long long wb, cudaStream_t s) {
+    if (S <= 0 || nitems <= 0) return FFB_OK;
+    int acc_cols = 32;
+    while (acc_cols < BNmax) acc_cols <<= 1;
+    TcStack none;
+    std::memset(&none, 0, sizeof none);
+    return launch_tc_prec<true>(prec, none, (const TcStack *)d_stacks, S, nitems, BNmax, acc_cols, per_sm, nst,
+                                status, wb, s);
 }
 
 // ---------------------------------------------------------------------------

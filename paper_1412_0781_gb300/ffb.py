@@ -63,6 +63,7 @@ SIGNATURES = {
     "ffb_group_covariance": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int64), _i, _vp]),
     "ffb_group_sync": (_i, [_vp, _vp]),
     "ffb_group_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "ffb_group_quad_tuning": (_i, [_vp, _i, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
     "ffb_group_tuning": (_i, [_vp, _i, _pi, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
     "ffb_interp_units": (_i, [_i, _i, _d, _i, _i, _pd, ctypes.POINTER(ctypes.c_int64), _vp, _pi]),
     "ffb_strerror": (ctypes.c_char_p, [_i]),
@@ -415,7 +416,8 @@ class Group:
     batching section of include/ffb.h).  ``plans`` are distinct Plans of one
     precision; they must outlive the group."""
 
-    INFO = ("S", "precision", "per", "tile", "grid", "graphs", "replays", "eager", "launches", "candidates")
+    INFO = ("S", "precision", "per", "tile", "grid", "graphs", "replays", "eager", "launches", "candidates",
+            "quad_per_sm", "quad_stages", "quad_candidates", "quad_rounds")
 
     def __init__(self, plans, stream=None):
         lib = load()
@@ -475,7 +477,7 @@ class Group:
         _check(load().ffb_group_sync(self._h, _stream(stream)), "ffb_group_sync")
 
     def info(self):
-        out = (ctypes.c_int64 * 10)()
+        out = (ctypes.c_int64 * 14)()
         _check(load().ffb_group_info(self._h, out), "ffb_group_info")
         return dict(zip(self.INFO, list(out)))
 
@@ -487,3 +489,13 @@ class Group:
         if k < 0:
             raise FFBError(k, "ffb_group_tuning")
         return [{"per": per[i], "tile": tile[i], "grid": grid[i], "ms": ms[i]} for i in range(k)]
+
+    def quad_tuning(self):
+        """Timed launch shapes of the grouped quadrature: CTAs per SM, stages, ms."""
+        m = 8
+        per, st = (ctypes.c_int * m)(), (ctypes.c_int * m)()
+        ms = (ctypes.c_float * m)()
+        k = load().ffb_group_quad_tuning(self._h, m, per, st, ms)
+        if k < 0:
+            raise FFBError(k, "ffb_group_quad_tuning")
+        return [{"per_sm": per[i], "stages": st[i], "ms": ms[i]} for i in range(k)]

@@ -64,6 +64,14 @@ def test_group_equals_single_plans_and_replays(dev, stacks, prec):
     info = g.info()
     assert info["eager"] == 1 and info["graphs"] == 1 and info["replays"] == 3
     assert info["launches"] > 0 and info["candidates"] > 0
+    if prec == "fp32":
+        assert info["quad_rounds"] == 0
+    else:
+        # one grouped quadrature launch per round, its launch shape tuned once
+        assert info["quad_rounds"] >= 1 and info["quad_candidates"] >= 1
+        qc = g.quad_tuning()
+        assert any(c["per_sm"] == info["quad_per_sm"] and c["stages"] == info["quad_stages"] for c in qc)
+        assert all(c["ms"] > 0 for c in qc)
     cands = g.tuning()
     assert any(c["per"] == info["per"] and c["tile"] == info["tile"] and c["grid"] == info["grid"] for c in cands)
     refs = _plans(prec)
@@ -177,6 +185,7 @@ def test_batching_workload_48_stacks_against_oracle(dev):
     g.sync()
     info = g.info()
     assert info["eager"] == 1 and info["graphs"] == 1 and info["replays"] == 2
+    assert info["quad_rounds"] >= 1
     for s, (sp, p, x, c) in enumerate(zip(specs, plans, imgs, coefs)):
         ref = Plan(sp.L, sp.c, sp.R, eps=1e-6, precision="bf16x3")
         assert torch.equal(c, ref.expand(x)), "stack %d: group != ffb_expand" % s
