@@ -125,6 +125,32 @@ int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps,
 int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta, const double *h_xi,
                      int64_t *h_counts, float *h_rec, int *h_blk);
 
+/* ffb_tile_units -- the interpolation table that ffb_plan builds for the
+ * separate-kernel path (plan_info[10] = 0, w = 8), computed on the host for
+ * inspection and tests; no GPU work.  Same node geometry and ES weights as
+ * ffb_interp_units, but the polar nodes (xi_j, theta_l), l < n_theta/2, of
+ * one image form a single set: node t = j n_theta/2 + l has its window at
+ * G row r0 = ceil(p2 - w/2) + h and unwrapped column u = ceil(p1 - w/2) +
+ * N/2 + h (h = (w+1)/2; column u maps to m1 = u - N/2 - h, stored mod N),
+ * and belongs to the tile (r0 / TR, u / TC).  A tile's nodes form units of up
+ * to four whose origins lie in one 2 x 2 box, split into blocks of at most
+ * GU units.
+ *   N even >= 16, w = 8 (FFB_ERR_UNSUPPORTED otherwise), beta > 0, h_xi[n_xi]
+ *   the radii on [0, c], n_theta even.
+ * h_counts[9] (out): blocks, entries of all node lists, fields per unit
+ *   record F (19), units per block GU, tile rows TR, tile columns TC, rows RS
+ *   and columns CS of a tile in shared memory, its row pitch.
+ * h_rec (may be NULL: sizing call): float[4 F GU h_counts[0]], per block F
+ *   fields of GU float4 laid out as in ffb_interp_units, with the union origin
+ *   (ru, cu) relative to the tile's first row and column and the slots
+ *   indexing the block's node list.
+ * h_blk (may be NULL): int[4 h_counts[0]], per block (first G row e0 of the
+ *   tile, first unwrapped column u0, first entry of its node list, node
+ *   count).
+ * h_nodes (may be NULL): int[h_counts[1]], the node lists (values t). */
+int ffb_tile_units(int N, int w, double beta, int n_xi, int n_theta, const double *h_xi,
+                   int64_t *h_counts, float *h_rec, int *h_blk, int *h_nodes);
+
 /* Releases everything the plan owns.  NULL is accepted. */
 int ffb_plan_destroy(ffb_plan_t plan);
 

@@ -78,6 +78,10 @@ struct ffb_plan_s {
     float2 *d_Fpol = nullptr;    // [chunk][n_xi][n_theta/2] (fused path)
     float4 *d_nodes = nullptr;   // [blocks][9][units] phase-3 unit records (fused path)
     int2 *d_node_blk = nullptr;  // [blocks] (first node, node count), half 0 then half 1
+    float4 *d_tunits = nullptr;  // separate-kernel path: tile unit records [blocks][19][256] (ffb_tile.cu)
+    int4 *d_tblk = nullptr;      // [blocks] (first G row, first unwrapped column, first node, count)
+    int *d_tnodes = nullptr;     // node lists of the tile blocks (t = j n_theta/2 + l)
+    int ntblk = 0;               // tile blocks (0: the per-node interpolation kernel)
     float2 *d_twA = nullptr;     // [n_theta/32][32] ring FFT twiddles W^{j k1} (fused path)
     float2 *d_twG = nullptr;     // [N/32][32] grid FFT twiddles W_N^{j k1} (fused path)
     int node_nblk[2] = {0, 0};   // blocks per half
@@ -382,6 +386,9 @@ int ffb_tc_split_planes(ffb_plan_t plan, cudaStream_t s);
 // a1-a4 of images [g0, g1) (one group of chunks) into the plan's quadrature
 // operands, without the quadrature (ffb_api.cu)
 int ffb_expand_part(ffb_plan_t plan, const float *d_images, int64_t g0, int64_t g1, cudaStream_t s);
+// tiled interpolation of the separate-kernel path (ffb_tile.cu)
+int ffb_tile_prepare(ffb_plan_t plan, cudaStream_t s);
+int ffb_launch_tile_polar(ffb_plan_t plan, int nimg, float2 *F, cudaStream_t s);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);

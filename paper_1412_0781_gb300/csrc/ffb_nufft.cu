@@ -131,7 +131,9 @@ k_cols(const float2 *__restrict__ H, int L, int off, int N, int h, int Mh,
 // accuracy even where t ~ N/2: rounding xi to float32 alone would move the
 // node by ~3e-8 and the phase of F by 2 pi * 3e-8 * |i|.
 // ---------------------------------------------------------------------------
-template <bool POLAR, int RB>
+// FROM_POLAR: the half rings come from the polar buffer Fpolar (written by
+// the tiled interpolation of ffb_tile.cu) instead of being interpolated here.
+template <bool POLAR, int RB, bool FROM_POLAR = false>
 __global__ void __launch_bounds__(RING_NT)
 k_interp_ring(const float2 *__restrict__ G, int N, int h, int Mh, int w, float beta,
               const float2 *__restrict__ rad, const float4 *__restrict__ ang, int n_xi, int n_theta,
@@ -150,7 +152,9 @@ k_interp_ring(const float2 *__restrict__ G, int N, int h, int Mh, int w, float b
         const int jj = t / nh, l = t - jj * nh;
         const int j = j0 + jj;
         float2 val = make_float2(0.f, 0.f);
-        if (j < n_xi) {
+        if (FROM_POLAR) {
+            if (j < n_xi) val = __ldg(&Fpolar[((size_t)img * n_xi + j) * nh + l]);
+        } else if (j < n_xi) {
             const float2 r = __ldg(&rad[j]);
             const float4 a = __ldg(&ang[l]);
             float p1 = r.x * a.x;
@@ -187,7 +191,7 @@ k_interp_ring(const float2 *__restrict__ G, int N, int h, int Mh, int w, float b
                 }
             }
         }
-        if (POLAR) {
+        if (POLAR && !FROM_POLAR) {
             if (j < n_xi) Fpolar[((size_t)img * n_xi + j) * nh + l] = val;
         } else {
             ringA[jj * n_theta + l] = val;
@@ -250,29 +254,41 @@ int ffb_launch_grid(ffb_plan_t p, const float *d_images, int64_t i0, int nimg, c
     return ffb_check_cuda(cudaGetLastError());
 }
 
-template <bool POLAR, int RB>
+template <bool POLAR, int RB, bool FROM_POLAR = false>
 static int launch_interp_rb(ffb_plan_t p, int nimg, float2 *d_F, cudaStream_t s) {
-    size_t smem = POLAR ? 0 : sizeof(float2) * 2 * RB * (size_t)p->n_theta;
+    size_t smem = (POLAR && !FROM_POLAR) ? 0 : sizeof(float2) * 2 * RB * (size_t)p->n_theta;
     static int attr = 0;
     if (smem > 48 * 1024 && attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_interp_ring<POLAR, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem));
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_interp_ring<POLAR, RB, FROM_POLAR>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         attr = (int)smem;
     }
     dim3 g((p->n_xi + RB - 1) / RB, nimg);
-    ProfScope ps(p, FFB_KC_INTERP, s);
-    k_interp_ring<POLAR, RB><<<g, RING_NT, smem, s>>>(p->d_G, p->N, p->h, p->Mh, p->w, (float)p->beta, p->d_rad,
-                                                      p->d_ang, p->n_xi, p->n_theta, p->d_twT, p->fftT, p->k_max,
-                                                      p->chunk, p->d_Fhat, d_F, p->d_status);
+    ProfScope ps(p, FROM_POLAR ? FFB_KC_RING_FFT : FFB_KC_INTERP, s);
+    k_interp_ring<POLAR, RB, FROM_POLAR><<<g, RING_NT, smem, s>>>(p->d_G, p->N, p->h, p->Mh, p->w, (float)p->beta,
+                                                                  p->d_rad, p->d_ang, p->n_xi, p->n_theta, p->d_twT,
+                                                                  p->fftT, p->k_max, p->chunk, p->d_Fhat, d_F,
+                                                                  p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
 
 // RING_RB rings per CTA, or half as many where their two ring buffers would
-// not fit in shared memory (n_theta > 1816 at 227 KB: L > 454 when R = L/2)
+// not fit in shared memory (n_theta > 1816 at 227 KB: L > 454 when R = L/2).
+// Plans with a tile table interpolate with the tiled kernel (ffb_tile.cu)
+// into the polar buffer, then take the ring DFTs from it.
 template <bool POLAR>
 static int launch_interp(ffb_plan_t p, int nimg, float2 *d_F, cudaStream_t s) {
+    if (p->ntblk > 0) {
+        if (POLAR) return ffb_launch_tile_polar(p, nimg, d_F, s);
+        int e = ffb_launch_tile_polar(p, nimg, p->d_Fpol, s);
+        if (e) return e;
+        if (ffb_ring_buffers_fit(p->n_theta, RING_RB)) return launch_interp_rb<false, RING_RB, true>(p, nimg, p->d_Fpol, s);
+        if (ffb_ring_buffers_fit(p->n_theta, RING_RB / 2))
+            return launch_interp_rb<false, RING_RB / 2, true>(p, nimg, p->d_Fpol, s);
+        return FFB_ERR_UNSUPPORTED;
+    }
     if (POLAR || ffb_ring_buffers_fit(p->n_theta, RING_RB)) return launch_interp_rb<POLAR, RING_RB>(p, nimg, d_F, s);
     if (ffb_ring_buffers_fit(p->n_theta, RING_RB / 2)) return launch_interp_rb<POLAR, RING_RB / 2>(p, nimg, d_F, s);
     return FFB_ERR_UNSUPPORTED;

@@ -194,7 +194,8 @@ static void free_plan(ffb_plan_t p) {
                     p->d_cov_off, p->d_corr, p->d_twN, p->d_twT, p->d_rad, p->d_ang,
                     p->d_cov_work, p->d_cov_sb, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
-                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA, p->d_twG};
+                    p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA, p->d_twG,
+                    p->d_tunits, p->d_tblk, p->d_tnodes};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (ProfEv &e : p->prof) {
@@ -389,9 +390,10 @@ bool ffb_ring_buffers_fit(int n_theta, int rb) {
 }
 
 int ffb_ensure_scratch_grid(ffb_plan_t p) {
-    if (p->d_H) return FFB_OK;
-    CK(dalloc(&p->d_H, (size_t)p->chunk * (p->N / 2 + 1) * p->L));
-    CK(dalloc(&p->d_G, (size_t)p->chunk * p->Mh * p->N));
+    if (!p->d_H) CK(dalloc(&p->d_H, (size_t)p->chunk * (p->N / 2 + 1) * p->L));
+    if (!p->d_G) CK(dalloc(&p->d_G, (size_t)p->chunk * p->Mh * p->N));
+    // the tiled interpolation writes polar samples before the ring DFTs
+    if (p->ntblk > 0 && !p->d_Fpol) CK(dalloc(&p->d_Fpol, (size_t)p->chunk * p->n_xi * (p->n_theta / 2)));
     return FFB_OK;
 }
 
@@ -448,6 +450,7 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
         st = ffb_fused_prepare(p, s);
         if (st == FFB_OK) st = ffb_ring_prepare(p, s);
     }
+    if (st == FFB_OK && !p->fused) st = ffb_tile_prepare(p, s);
     if (st != FFB_OK) {
         cudaStreamSynchronize(s);
         free_plan(p);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "ffb_group_quad_tuning": (_i, [_vp, _i, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
     "ffb_group_tuning": (_i, [_vp, _i, _pi, _pi, _pi, ctypes.POINTER(ctypes.c_float)]),
     "ffb_interp_units": (_i, [_i, _i, _d, _i, _i, _pd, ctypes.POINTER(ctypes.c_int64), _vp, _pi]),
+    "ffb_tile_units": (_i, [_i, _i, _d, _i, _i, _pd, ctypes.POINTER(ctypes.c_int64), _vp, _pi, _pi]),
     "ffb_strerror": (ctypes.c_char_p, [_i]),
 }
 
@@ -106,6 +107,28 @@ def interp_units(N, w, beta, n_theta, xi):
     gu = int(cnt[4])
     return (rec.reshape(int(cnt[1]), int(cnt[7]), gu, 4), blk.reshape(-1, 2), (int(cnt[2]), int(cnt[3])),
             int(cnt[5]), int(cnt[6]), int(cnt[8]))
+
+
+def tile_units(N, w, beta, n_theta, xi):
+    """Host-only: the separate-kernel path's tile interpolation table for
+    radii ``xi`` (see ffb_tile_units).  Returns (records float32 (blocks, F,
+    GU, 4), blocks int32 (blocks, 4), node lists int32, dict of the tile
+    geometry: TR, TC, RS, CS, pitch)."""
+    import numpy as np
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    cnt = (ctypes.c_int64 * 9)()
+    lib = load()
+    _check(lib.ffb_tile_units(int(N), int(w), float(beta), len(x), int(n_theta), x.ctypes.data_as(_pd), cnt,
+                              None, None, None), "ffb_tile_units")
+    nb, nn, F, GU = int(cnt[0]), int(cnt[1]), int(cnt[2]), int(cnt[3])
+    rec = np.zeros(nb * F * GU * 4, dtype=np.float32)
+    blk = np.zeros(4 * nb, dtype=np.int32)
+    nodes = np.zeros(max(nn, 1), dtype=np.int32)
+    _check(lib.ffb_tile_units(int(N), int(w), float(beta), len(x), int(n_theta), x.ctypes.data_as(_pd), cnt,
+                              rec.ctypes.data_as(ctypes.c_void_p), blk.ctypes.data_as(_pi),
+                              nodes.ctypes.data_as(_pi)), "ffb_tile_units")
+    geo = {"TR": int(cnt[4]), "TC": int(cnt[5]), "RS": int(cnt[6]), "CS": int(cnt[7]), "pitch": int(cnt[8])}
+    return rec.reshape(nb, F, GU, 4), blk.reshape(nb, 4), nodes[:nn], geo
 
 
 def cov_merge(p, states):
