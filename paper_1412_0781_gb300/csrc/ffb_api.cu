@@ -98,6 +98,16 @@ int ffb_expand_part(ffb_plan_t p, const float *d_images, int64_t g0, int64_t g1,
             r.p0 = (char *)ring.p0 + off;
             if (ring.p1) r.p1 = (char *)ring.p1 + off;
             CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
+        } else if (p->ring_direct) {
+            // tiled interpolation into the polar buffer, then the register
+            // ring FFT straight into this chunk's quadrature operands
+            CK(ffb_launch_grid(p, d_images, i0, m, s));
+            CK(ffb_launch_tile_polar(p, m, p->d_Fpol, s));
+            RingOut r = ring;
+            const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
+            r.p0 = (char *)ring.p0 + off;
+            if (ring.p1) r.p1 = (char *)ring.p1 + off;
+            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
         } else {
             CK(ffb_launch_grid(p, d_images, i0, m, s));
             CK(ffb_launch_interp_ring(p, m, s));
@@ -119,7 +129,7 @@ int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef,
     for (int64_t g0 = 0; g0 < n; g0 += (int64_t)grp * p->chunk) {
         const int64_t g1 = std::min<int64_t>(n, g0 + (int64_t)grp * p->chunk);
         CK(ffb_expand_part(p, d_images, g0, g1, s));
-        CK(ffb_launch_bessel(p, (int)(g1 - g0), d_coef + (size_t)g0 * p->P * 2, p->fused != 0, s));
+        CK(ffb_launch_bessel(p, (int)(g1 - g0), d_coef + (size_t)g0 * p->P * 2, p->ring_direct != 0, s));
     }
     return FFB_OK;
 }

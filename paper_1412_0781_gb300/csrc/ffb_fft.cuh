@@ -1,12 +1,13 @@
-// ffb_fft.cuh -- in-register DFTs of one thread (lengths 2, 4, 8, 16 and a
-// real-input length 2, 4, 8) and the constant twiddles they use; shared by the
+// ffb_fft.cuh -- in-register DFTs of one thread (lengths 2, 4, 8, 16, 32 and
+// a real-input length 2, 4, 8, 16) and the constant twiddles they use; shared by the
 // shared-memory grid kernel (ffb_grid.cu) and the ring FFT (ffb_ring.cu).
 #pragma once
 #include "ffb_internal.cuh"
 
 // ---------------------------------------------------------------------------
 // Register FFTs.  dft_reg<M>: a length-M DFT held in one thread's registers
-// (M = 4, 8, 16; radix 4 with constant twiddles).
+// (M = 4, 8, 16: radix 4 with constant twiddles; M = 32: radix 2 over two
+// length-16 DFTs).
 // ---------------------------------------------------------------------------
 template <int M>
 __host__ __device__ constexpr int bitrev_c(int i) {
@@ -31,6 +32,24 @@ __device__ __forceinline__ float2 w16(int e) {
     }
 }
 
+// cos / sin (2 pi e / 16), e = 0..15
+__device__ __forceinline__ float cos16(int e) {
+    constexpr float c[16] = {1.f, FFB_C1, FFB_R2, FFB_S1, 0.f, -FFB_S1, -FFB_R2, -FFB_C1,
+                             -1.f, -FFB_C1, -FFB_R2, -FFB_S1, 0.f, FFB_S1, FFB_R2, FFB_C1};
+    return c[e & 15];
+}
+__device__ __forceinline__ float sin16(int e) { return cos16(e + 12); }
+// cos / sin (2 pi e / 32), e = 0..31
+__device__ __forceinline__ float cos32(int e) {
+    constexpr float c1 = 0.98078528040323044913f, c3 = 0.83146961230254523708f;
+    constexpr float c5 = 0.55557023301960222474f, c7 = 0.19509032201612826785f;
+    constexpr float c[32] = {1.f, c1, FFB_C1, c3, FFB_R2, c5, FFB_S1, c7, 0.f, -c7, -FFB_S1, -c5, -FFB_R2, -c3,
+                             -FFB_C1, -c1, -1.f, -c1, -FFB_C1, -c3, -FFB_R2, -c5, -FFB_S1, -c7, 0.f, c7,
+                             FFB_S1, c5, FFB_R2, c3, FFB_C1, c1};
+    return c[e & 31];
+}
+__device__ __forceinline__ float sin32(int e) { return cos32(e + 24); }
+
 // in-register length-M DFT, natural order in and out (forward)
 template <int M>
 __device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
@@ -52,8 +71,25 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[M]) {
             x[k] = cadd(e[k], t);
             x[k + 4] = csub(e[k], t);
         }
+    } else if constexpr (M == 32) {
+        // radix 2 over two length-16 DFTs of the even and odd samples
+        float2 e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            e[i] = x[2 * i];
+            o[i] = x[2 * i + 1];
+        }
+        dft_reg<16>(e);
+        dft_reg<16>(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            // W_32^k = (cos, -sin)(2 pi k / 32)
+            const float2 t = (k == 0) ? o[0] : cmul(o[k], make_float2(cos32(k), -sin32(k)));
+            x[k] = cadd(e[k], t);
+            x[k + 16] = csub(e[k], t);
+        }
     } else {
-        static_assert(M == 16, "M in {2, 4, 8, 16}");
+        static_assert(M == 16, "M in {2, 4, 8, 16, 32}");
         float2 y[4][4];   // y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times W16^{n2 k1}
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) {
@@ -84,8 +120,13 @@ __device__ __forceinline__ void dft_real(const float (&u)[H], float2 (&E)[H]) {
         E[1] = make_float2(t1, -t3);
         E[2] = make_float2(t0 - t2, 0.f);
         E[3] = make_float2(t1, t3);
+    } else if constexpr (H == 16) {
+        // the complex length-16 DFT of the real sequence
+#pragma unroll
+        for (int i = 0; i < 16; ++i) E[i] = make_float2(u[i], 0.f);
+        dft_reg<16>(E);
     } else {
-        static_assert(H == 8, "H in {2, 4, 8}");
+        static_assert(H == 8, "H in {2, 4, 8, 16}");
         // even / odd samples: real length-4 DFTs A, B; E[j] = A[j] + W8^j B[j]
         const float a0 = u[0] + u[4], a1 = u[0] - u[4], a2 = u[2] + u[6], a3 = u[2] - u[6];
         const float b0 = u[1] + u[5], b1 = u[1] - u[5], b2 = u[3] + u[7], b3 = u[3] - u[7];
@@ -103,20 +144,3 @@ __device__ __forceinline__ void dft_real(const float (&u)[H], float2 (&E)[H]) {
     }
 }
 
-// cos / sin (2 pi e / 16), e = 0..15
-__device__ __forceinline__ float cos16(int e) {
-    constexpr float c[16] = {1.f, FFB_C1, FFB_R2, FFB_S1, 0.f, -FFB_S1, -FFB_R2, -FFB_C1,
-                             -1.f, -FFB_C1, -FFB_R2, -FFB_S1, 0.f, FFB_S1, FFB_R2, FFB_C1};
-    return c[e & 15];
-}
-__device__ __forceinline__ float sin16(int e) { return cos16(e + 12); }
-// cos / sin (2 pi e / 32), e = 0..31
-__device__ __forceinline__ float cos32(int e) {
-    constexpr float c1 = 0.98078528040323044913f, c3 = 0.83146961230254523708f;
-    constexpr float c5 = 0.55557023301960222474f, c7 = 0.19509032201612826785f;
-    constexpr float c[32] = {1.f, c1, FFB_C1, c3, FFB_R2, c5, FFB_S1, c7, 0.f, -c7, -FFB_S1, -c5, -FFB_R2, -c3,
-                             -FFB_C1, -c1, -1.f, -c1, -FFB_C1, -c3, -FFB_R2, -c5, -FFB_S1, -c7, 0.f, c7,
-                             FFB_S1, c5, FFB_R2, c3, FFB_C1, c1};
-    return c[e & 31];
-}
-__device__ __forceinline__ float sin32(int e) { return cos32(e + 24); }

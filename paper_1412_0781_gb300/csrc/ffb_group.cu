@@ -332,7 +332,7 @@ static int run(ffb_group_t g, const Key &k, cudaStream_t main, Entry *ent, bool 
                 const int64_t g1 = std::min<int64_t>(k.n[i], g0 + per);
                 CKG(ffb_check_cuda(cudaStreamWaitEvent(g->br[i], g->fork, 0)));
                 CKG(ffb_expand_part(p, (const float *)k.images[i], g0, g1, g->br[i]));
-                if (!p->fused) CKG(ffb_tc_split_planes(p, g->br[i]));
+                if (!p->ring_direct) CKG(ffb_tc_split_planes(p, g->br[i]));
                 CKG(ffb_check_cuda(cudaEventRecord(g->join[i], g->br[i])));
                 CKG(ffb_check_cuda(cudaStreamWaitEvent(main, g->join[i], 0)));
             }

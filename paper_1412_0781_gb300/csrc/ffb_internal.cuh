@@ -82,6 +82,9 @@ struct ffb_plan_s {
     int4 *d_tblk = nullptr;      // [blocks] (first G row, first unwrapped column, first node, count)
     int *d_tnodes = nullptr;     // node lists of the tile blocks (t = j n_theta/2 + l)
     int ntblk = 0;               // tile blocks (0: the per-node interpolation kernel)
+    int ring_direct = 0;         // 1: the register ring FFT (ffb_ring.cu) writes the quadrature
+                                 //    operands from the polar buffer (fused path, and tiled plans
+                                 //    with n_theta in {64, ..., 1024})
     float2 *d_twA = nullptr;     // [n_theta/32][32] ring FFT twiddles W^{j k1} (fused path)
     float2 *d_twG = nullptr;     // [N/32][32] grid FFT twiddles W_N^{j k1} (fused path)
     int node_nblk[2] = {0, 0};   // blocks per half

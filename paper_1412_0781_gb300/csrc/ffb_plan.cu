@@ -449,8 +449,16 @@ extern "C" int ffb_plan(ffb_plan_t *out, int L, double c, double R, double eps, 
         p->chunk = 152;   // 2 x 152 CTAs of one per SM: two full waves on 152 SMs
         st = ffb_fused_prepare(p, s);
         if (st == FFB_OK) st = ffb_ring_prepare(p, s);
+        p->ring_direct = 1;
     }
     if (st == FFB_OK && !p->fused) st = ffb_tile_prepare(p, s);
+    // tiled plans whose ring length the register ring FFT takes
+    const int nt = p->n_theta;
+    if (st == FFB_OK && p->ntblk > 0 && (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 1024) &&
+        p->k_max < nt / 2) {
+        st = ffb_ring_prepare(p, s);
+        p->ring_direct = (st == FFB_OK);
+    }
     if (st != FFB_OK) {
         cudaStreamSynchronize(s);
         free_plan(p);

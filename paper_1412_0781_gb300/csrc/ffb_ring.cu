@@ -7,13 +7,22 @@
 
 #include "ffb_fft.cuh"
 
-#define RFFT_RB 32   // rings per ring-FFT CTA (one warp each)
+// rings per ring-FFT CTA (one warp each): 32, or 8 at n_theta = 1024 where a
+// warp's transpose buffer holds 32 x 32 values
+template <int NTH>
+constexpr int rfft_rb() { return NTH > 512 ? 8 : 32; }
+
+// cos / sin (2 pi m / M) for M = 2 .. 32
+template <int M>
+__device__ __forceinline__ float wcos(int m) { return (M <= 16) ? cos16((16 / (M <= 16 ? M : 16)) * m) : cos32(m); }
+template <int M>
+__device__ __forceinline__ float wsin(int m) { return (M <= 16) ? sin16((16 / (M <= 16 ? M : 16)) * m) : sin32(m); }
 
 // ---------------------------------------------------------------------------
 // ring FFT: F[img][j][l] (l < n_theta/2) -> Fhat[k][img][c][j], k <= k_max,
 // with the conjugate completion of the ring and the 2 pi / n_theta weight.
 //
-// One warp per ring, four-step in registers: with n_theta = 32 M, sample
+// One warp per ring, four-step in registers: with n_theta = 32 M (M <= 32), sample
 // l = 32 m + j (lane j) and k = k1 + M k2,
 //   X_k = sum_j W^{j k1} [sum_m s_{32m+j} W_M^{m k1}] W_32^{j k2},  W = e^{-2 pi i / n_theta}.
 // Pass A: each lane loads its M/2 samples x_m (m < M/2) from the polar
@@ -34,7 +43,7 @@
 // format, two rings per store.
 // grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
 // ---------------------------------------------------------------------------
-template <int NTH, int FMT>
+template <int NTH, int FMT, int RFFT_RB = rfft_rb<NTH>()>
 __global__ void __launch_bounds__(32 * RFFT_RB, 1)
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const float2 *__restrict__ twT,
            const float2 *__restrict__ twA,
@@ -42,7 +51,7 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
     constexpr int M = NTH / 32;      // samples per lane
     constexpr int R = 32 / M;        // lanes per length-32 DFT of pass B
     constexpr int NH = NTH / 2;
-    static_assert(M >= 2 && M <= 16 && M * R == 32, "n_theta in {64, 128, 256, 512}");
+    static_assert(M >= 2 && M <= 32 && M * R == 32, "n_theta in {64, 128, 256, 512, 1024}");
     extern __shared__ float2 smr[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 *tb = smr + warp * (M * 32);                  // this warp's transpose buffer [M][32]
@@ -67,7 +76,7 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
         for (int m = 0; m < M / 2; ++m) {
             const float2 xm = src[32 * m + lane];
             u[m] = xm.x;
-            v[m] = make_float2(xm.y * sin16((16 / M) * m), xm.y * cos16((16 / M) * m));
+            v[m] = make_float2(xm.y * wsin<M>(m), xm.y * wcos<M>(m));
         }
         dft_real<M / 2>(u, E);
         dft_reg<M / 2>(v);
@@ -113,6 +122,16 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
                 if (k <= kmax) {
                     row[2 * k + r] = scale * (r ? val.y : val.x);
                     row[2 * k + 1 - r] = scale * (r ? val.x : val.y);
+                }
+            }
+        } else if constexpr (R == 1) {
+            // one lane per k1: the length-32 DFT over i gave k = g + 32 k2
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int k = g + M * k2;
+                if (k <= kmax) {
+                    row[2 * k] = scale * y[k2].x;
+                    row[2 * k + 1] = scale * y[k2].y;
                 }
             }
         } else {
@@ -213,6 +232,7 @@ int ffb_ring_prepare(ffb_plan_t p, cudaStream_t s) {
 
 template <int NTH, int FMT>
 static int launch_ring_fmt(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &o, cudaStream_t s) {
+    constexpr int RFFT_RB = rfft_rb<NTH>();
     static int attr = 0;
     const size_t smem = sizeof(float2) * RFFT_RB * (size_t)NTH + sizeof(float) * RFFT_RB * ((2 * (p->k_max + 1)) | 1);
     if (smem > 48 * 1024 && attr < (int)smem) {
@@ -256,6 +276,7 @@ int ffb_launch_ring_fft(ffb_plan_t p, int m, const float2 *Fpol, const RingOut &
         case 128: return launch_ring<128>(p, m, Fpol, o, s);
         case 256: return launch_ring<256>(p, m, Fpol, o, s);
         case 512: return launch_ring<512>(p, m, Fpol, o, s);
+        case 1024: return launch_ring<1024>(p, m, Fpol, o, s);
         default: return FFB_ERR_UNSUPPORTED;
     }
 }
