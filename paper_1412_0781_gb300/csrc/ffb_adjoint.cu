@@ -322,9 +322,16 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
     const size_t sm_ring = sizeof(float2) * 2 * rb * (size_t)p->n_theta;
     const size_t sm_cols = sizeof(float2) * (size_t)ACOL_WARPS * 2 * N;
     const size_t sm_rows = sizeof(float2) * (size_t)AROW_WARPS * 2 * N;
+    static int a_ringp4 = 0;
+    // plans with a polar buffer and a spreading table (fused path, tiled
+    // separate-kernel path): inverse ring DFT to the polar buffer, then the
+    // spreading in shared memory
+    const bool polar = p->fused || p->ntblk > 0;
     if ((e = set_smem((const void *)k_adj_bessel, sm_bes, &a_bes))) return e;
-    if (p->fused) {
+    if (polar && rb == ADJ_RB) {
         if ((e = set_smem((const void *)k_adj_ring_polar<ADJ_RB>, sm_ring, &a_ringp))) return e;
+    } else if (polar) {
+        if ((e = set_smem((const void *)k_adj_ring_polar<ADJ_RB / 2>, sm_ring, &a_ringp4))) return e;
     } else if (rb == ADJ_RB) {
         if ((e = set_smem((const void *)k_adj_ring_spread<ADJ_RB>, sm_ring, &a_ring))) return e;
     } else {
@@ -343,18 +350,27 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
         }
         e = ffb_check_cuda(cudaMemsetAsync(p->d_G, 0, sizeof(float2) * (size_t)m * p->Mh * N, s));
         if (e) return e;
-        if (p->fused) {
+        if (polar) {
             // inverse ring DFT to the polar buffer, then the half grids in
-            // shared memory with the forward's unit table
+            // shared memory with the forward's unit or tile table
             {
                 ProfScope ps(p, FFB_KC_ADJ_RING, s);
-                dim3 g((p->n_xi + ADJ_RB - 1) / ADJ_RB, m);
-                k_adj_ring_polar<ADJ_RB><<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT,
-                                                                    p->fftT, p->k_max, p->chunk, p->d_Fpol);
+                dim3 g((p->n_xi + rb - 1) / rb, m);
+                if (rb == ADJ_RB)
+                    k_adj_ring_polar<ADJ_RB><<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta, p->d_twT,
+                                                                        p->fftT, p->k_max, p->chunk, p->d_Fpol);
+                else
+                    k_adj_ring_polar<ADJ_RB / 2><<<g, ADJ_NT, sm_ring, s>>>(p->d_Fhat, p->n_xi, p->n_theta,
+                                                                            p->d_twT, p->fftT, p->k_max,
+                                                                            p->chunk, p->d_Fpol);
                 p->launches++;
                 if ((e = ffb_check_cuda(cudaGetLastError()))) return e;
             }
-            if ((e = ffb_launch_fused_spread(p, p->d_Fpol, m, p->d_G, s))) return e;
+            if (p->fused) {
+                if ((e = ffb_launch_fused_spread(p, p->d_Fpol, m, p->d_G, s))) return e;
+            } else if ((e = ffb_launch_tile_spread(p, m, p->d_Fpol, p->d_G, s))) {
+                return e;
+            }
         } else {
             ProfScope ps(p, FFB_KC_ADJ_RING, s);
             dim3 g((p->n_xi + rb - 1) / rb, m);

@@ -392,6 +392,7 @@ int ffb_expand_part(ffb_plan_t plan, const float *d_images, int64_t g0, int64_t 
 // tiled interpolation of the separate-kernel path (ffb_tile.cu)
 int ffb_tile_prepare(ffb_plan_t plan, cudaStream_t s);
 int ffb_launch_tile_polar(ffb_plan_t plan, int nimg, float2 *F, cudaStream_t s);
+int ffb_launch_tile_spread(ffb_plan_t plan, int nimg, const float2 *Gpol, float2 *Gext, cudaStream_t s);
 
 // Launchers implemented in ffb_nufft.cu / ffb_gemm.cu / ffb_eig.cu.
 int ffb_launch_grid(ffb_plan_t plan, const float *d_images, int64_t i0, int nimg, cudaStream_t s);

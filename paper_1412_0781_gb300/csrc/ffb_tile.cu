@@ -129,6 +129,77 @@ k_interp_tile(const float2 *__restrict__ G, int N, int h, int Mh, int nh, int n_
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of k_interp_tile (step a10): the polar values g (inverse ring DFT,
+// layout of the polar buffer) spread into the block's tile in shared memory,
+// T[ru + r][cu + q] += sum_n wy_n[r] wx_n[q] g_n over a unit's nodes (one
+// shared-memory atomic per value of the 9 x 9 union and component), then the
+// tile added into the half grid Gext (zeroed by the caller) at G row e0 + r,
+// column (u0 + c - N/2 - h) mod N with global atomics (tiles overlap in their
+// halos, and a tile may have several blocks); cells no unit touched are
+// skipped.  The transpose of the forward with the same weights, so the
+// adjoint stays exact against it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TIL_NT, 3)
+k_adj_spread_tile(const float2 *__restrict__ Gpol, int N, int h, int Mh, int nh, int n_xi,
+                  const float4 *__restrict__ units, const int4 *__restrict__ blocks, const int *__restrict__ nodes,
+                  float2 *__restrict__ Gext, int *status) {
+    __shared__ float2 T[TIL_RS * TIL_CP];
+    float *Tf = (float *)T;
+    for (int i = threadIdx.x; i < TIL_RS * TIL_CP; i += TIL_NT) T[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int4 blk = __ldg(&blocks[blockIdx.x]);
+    const int e0 = blk.x, u0 = blk.y, nb0 = blk.z, cnt = blk.w;
+    const int img = blockIdx.y;
+    const float2 *Gp = Gpol + (size_t)img * n_xi * nh;
+    const int s = threadIdx.x;
+    const float4 *rec = units + (size_t)blockIdx.x * TIL_REC * TIL_GU;
+    const float4 meta = __ldg(&rec[18 * TIL_GU + s]);
+    const unsigned s01 = __float_as_uint(meta.y), s23 = __float_as_uint(meta.z);
+    const int sl[4] = {(int)(s01 & 0xFFFFu), (int)(s01 >> 16), (int)(s23 & 0xFFFFu), (int)(s23 >> 16)};
+    if (sl[0] < cnt) {
+        const int rc = __float_as_int(meta.x);
+        const int r0 = rc & 0xFFFF, c0 = rc >> 16;
+        if (r0 + TIL_UW > TIL_RS || c0 + TIL_UW > TIL_CS) {
+            ffb_flag(status, FFB_ERR_ARG);
+        } else {
+            float2 v[TIL_NU];
+#pragma unroll
+            for (int n = 0; n < TIL_NU; ++n)
+                v[n] = (sl[n] < cnt) ? __ldg(&Gp[__ldg(&nodes[nb0 + sl[n]])]) : make_float2(0.f, 0.f);
+            float4 wx[TIL_UW];
+#pragma unroll
+            for (int q = 0; q < TIL_UW; ++q) wx[q] = __ldg(&rec[q * TIL_GU + s]);
+            float *base = Tf + 2 * (r0 * TIL_CP + c0);
+#pragma unroll 1
+            for (int r = 0; r < TIL_UW; ++r) {
+                const float4 wy = __ldg(&rec[(TIL_UW + r) * TIL_GU + s]);
+                const float2 a0 = make_float2(wy.x * v[0].x, wy.x * v[0].y), a1 = make_float2(wy.y * v[1].x, wy.y * v[1].y);
+                const float2 a2 = make_float2(wy.z * v[2].x, wy.z * v[2].y), a3 = make_float2(wy.w * v[3].x, wy.w * v[3].y);
+                float *row = base + 2 * r * TIL_CP;
+#pragma unroll
+                for (int q = 0; q < TIL_UW; ++q) {
+                    const float re = fmaf(wx[q].x, a0.x, fmaf(wx[q].y, a1.x, fmaf(wx[q].z, a2.x, wx[q].w * a3.x)));
+                    const float im = fmaf(wx[q].x, a0.y, fmaf(wx[q].y, a1.y, fmaf(wx[q].z, a2.y, wx[q].w * a3.y)));
+                    atomicAdd(&row[2 * q], re);
+                    atomicAdd(&row[2 * q + 1], im);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float2 *Gi = Gext + (size_t)img * Mh * N;
+    for (int i = threadIdx.x; i < TIL_RS * TIL_CS; i += TIL_NT) {
+        const int r = i / TIL_CS, c = i - r * TIL_CS;
+        const int e = e0 + r;
+        const float2 val = T[r * TIL_CP + c];
+        if (e >= Mh || (val.x == 0.f && val.y == 0.f)) continue;
+        int col = (u0 + c - N / 2 - h) % N;
+        if (col < 0) col += N;
+        atomicAdd(&Gi[(size_t)e * N + col], val);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The tile table (host, float64).  Node t = j nh + l, l < nh = n_theta/2,
 // sits at p = N xi_j (cos theta_l, sin theta_l) in grid units; its window
 // starts at m = ceil(p - W/2) with weights phi(f - b), f = p - m, b = 0..7,
@@ -327,6 +398,17 @@ int ffb_launch_tile_polar(ffb_plan_t p, int nimg, float2 *F, cudaStream_t s) {
     ProfScope ps(p, FFB_KC_INTERP, s);
     k_interp_tile<<<g, TIL_NT, 0, s>>>(p->d_G, p->N, p->h, p->Mh, p->n_theta / 2, p->n_xi, p->d_tunits, p->d_tblk,
                                        p->d_tnodes, F, p->d_status);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+// the adjoint's spreading for nimg images: polar values Gpol -> Gext (zeroed)
+int ffb_launch_tile_spread(ffb_plan_t p, int nimg, const float2 *Gpol, float2 *Gext, cudaStream_t s) {
+    if (p->ntblk <= 0) return FFB_ERR_STATE;
+    dim3 g(p->ntblk, nimg);
+    ProfScope ps(p, FFB_KC_ADJ_SPREAD, s);
+    k_adj_spread_tile<<<g, TIL_NT, 0, s>>>(Gpol, p->N, p->h, p->Mh, p->n_theta / 2, p->n_xi, p->d_tunits, p->d_tblk,
+                                           p->d_tnodes, Gext, p->d_status);
     p->launches++;
     return ffb_check_cuda(cudaGetLastError());
 }
