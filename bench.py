@@ -160,19 +160,19 @@ def hbm_floor(plan):
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of a 152-image launch (the committed profile of the grid kernel at
-# L = 128), valid only
+# capture of a 152-image launch (the committed profile of the four-node-unit
+# grid kernel at L = 128), valid only
 # while the kernel's sources are byte-identical to the profiled ones (the
 # kernel's file from its top through the kernel, i.e. its macros, device
 # helpers and body, and the register-FFT header; from ffb_internal.cuh it uses
 # only the complex arithmetic and the status flag).  ncu empties L2 before the
-# capture, so the figure includes one read of the plan's 2.6 MB unit table,
+# capture, so the figure includes one read of the plan's 3 MB unit table,
 # which stays in L2 between launches in a live run.
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu:^k_grid_interp_half",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "e5875d077193c9ebc126ce8e8002b8b182eb036906f5b86b1b32c92eb895e4aa",
-                    "bytes_per_launch": 12652800 + 90112, "images_per_launch": 152},
+                    "sha256": "256b7490993661bdb66105e35481ef928e7f0034996e6a7c52429e7074644578",
+                    "bytes_per_launch": 12989184 + 55552, "images_per_launch": 152},
 }
 
 
