@@ -353,7 +353,10 @@ int ffb_launch_adjoint(ffb_plan_t p, const float *d_coef, int64_t n, float *d_im
         if (polar) {
             // inverse ring DFT to the polar buffer, then the half grids in
             // shared memory with the forward's unit or tile table
-            {
+            if (p->ring_direct) {
+                // register four-step inverse ring DFT (ffb_ring.cu)
+                if ((e = ffb_launch_ring_ifft(p, m, p->d_Fhat, p->d_Fpol, s))) return e;
+            } else {
                 ProfScope ps(p, FFB_KC_ADJ_RING, s);
                 dim3 g((p->n_xi + rb - 1) / rb, m);
                 if (rb == ADJ_RB)

@@ -372,6 +372,7 @@ struct RingOut {
     int lead;          // images per k in the planes
 };
 int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, const RingOut &out, cudaStream_t s);
+int ffb_launch_ring_ifft(ffb_plan_t plan, int m, const float *Yhat, float2 *Gpol, cudaStream_t s);
 int ffb_tc_prepare(ffb_plan_t plan, cudaStream_t s, RingOut *out);
 // chunks whose ring spectra one tensor-core quadrature launch takes (>= 1;
 // valid after ffb_tc_prepare)

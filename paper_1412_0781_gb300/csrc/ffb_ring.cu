@@ -209,6 +209,167 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inverse ring DFT of the adjoint (step a10, the transpose of Eq. 1DFFT with
+// the ring's conjugate completion): from the ring spectra Y_k, k <= k_max
+// (Yhat[k][img][c][j], float32, from the transposed quadrature), the polar
+// values G_l = s (g_l + conj g_{l + n/2}), l < n/2, of the zero-padded
+// inverse DFT g_l = sum_k Y_k e^{+2 pi i k l / n}, s = 2 pi / n.  Written out,
+//   G_l = s sum_k [Y_k e^{+i theta_l k} + (-1)^k conj(Y_k) e^{-i theta_l k}]
+//       = s conj( DFT_n(W)_l ),
+// W_0 = 2 Re Y_0, W_k = conj Y_k and W_{n-k} = (-1)^k Y_k for 1 <= k <= k_max,
+// zero elsewhere.  The forward DFT of W is the four-step of k_ring_fft with a
+// full length-M first pass (W has no symmetry); the outputs l < n/2 are the
+// t = 0 half.  A CTA stages its rings' Y into shared memory (coalesced over
+// rings), each warp forms its ring's W, transforms it, and the ring's
+// results leave as one contiguous run of n/2 values of the polar buffer.
+// grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
+// ---------------------------------------------------------------------------
+template <int NTH, int RFFT_RB = rfft_rb<NTH>()>
+__global__ void __launch_bounds__(32 * RFFT_RB, 1)
+k_ring_ifft(const float *__restrict__ Yhat, int n_xi, int kmax, int chunk, const float2 *__restrict__ twT,
+            const float2 *__restrict__ twA, float2 *__restrict__ Gpol) {
+    constexpr int M = NTH / 32;
+    constexpr int R = 32 / M;
+    constexpr int NH = NTH / 2;
+    constexpr int PR = NH + 1;       // pitch of a ring's region (odd in 8-byte slots)
+    static_assert(M >= 2 && M <= 32 && M * R == 32, "n_theta in {64, 128, 256, 512, 1024}");
+    extern __shared__ float2 smr[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *tb = smr + warp * (M * 32);                  // this warp's transpose buffer [M][32]
+    float2 *region = smr + RFFT_RB * M * 32;             // [RFFT_RB][PR]: Y_k, then G_l
+    const int img = blockIdx.y;
+    const int j0 = blockIdx.x * RFFT_RB;
+    // Y_k of the CTA's rings: thread t takes (k, ring) = (t / RB, t % RB), the
+    // re and im rows of Yhat coalesced over rings
+    for (int t = threadIdx.x; t < (kmax + 1) * RFFT_RB; t += 32 * RFFT_RB) {
+        const int k = t / RFFT_RB, jj = t - k * RFFT_RB;
+        float2 v = make_float2(0.f, 0.f);
+        if (j0 + jj < n_xi) {
+            const size_t b = (((size_t)k * chunk + img) * 2) * n_xi + j0 + jj;
+            v = make_float2(__ldg(&Yhat[b]), __ldg(&Yhat[b + n_xi]));
+        }
+        region[jj * PR + k] = v;
+    }
+    __syncthreads();
+    const int ring = j0 + warp;
+    if (ring >= n_xi) return;            // no block-wide barrier below
+    float2 *reg = region + warp * PR;
+    // W at w = 32 m + lane
+    float2 x[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int w = 32 * m + lane;
+        float2 v = make_float2(0.f, 0.f);
+        if (w == 0) {
+            v = make_float2(2.f * reg[0].x, 0.f);
+        } else if (w <= kmax) {
+            v = cconj(reg[w]);
+        } else if (w >= NTH - kmax) {
+            const int k = NTH - w;
+            v = reg[k];
+            if (k & 1) v = make_float2(-v.x, -v.y);
+        }
+        x[m] = v;
+    }
+    dft_reg<M>(x);                                       // pass A: over m
+#pragma unroll
+    for (int k1 = 1; k1 < M; ++k1) x[k1] = cmul(x[k1], __ldg(&twA[k1 * 32 + lane]));
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) tb[k1 * 32 + ((lane + k1 * R) & 31)] = x[k1];
+    __syncwarp();
+    const int g = lane / R, r = lane % R;
+    float2 y[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) y[i] = tb[g * 32 + ((r + R * i + g * R) & 31)];
+    dft_reg<M>(y);                                       // pass B, part 1: over i
+    const float scale = 6.283185307179586f / (float)NTH;
+    // every lane has read its W above and the transpose is past a warp
+    // barrier: the region now takes the results
+    if constexpr (R == 1) {
+#pragma unroll
+        for (int k2 = 0; k2 < M / 2; ++k2) {
+            const int l = g + M * k2;
+            reg[l] = make_float2(scale * y[k2].x, -scale * y[k2].y);
+        }
+    } else if constexpr (R == 2) {
+#pragma unroll
+        for (int k2 = 1; k2 < M; ++k2) {
+            const float2 w = make_float2(cos32(k2), -sin32(k2));
+            const float2 t = cmul(y[k2], w);
+            y[k2] = r ? t : y[k2];
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            y[k2].x += __shfl_xor_sync(0xffffffffu, y[k2].x, 1);
+            y[k2].y += __shfl_xor_sync(0xffffffffu, y[k2].y, 1);
+        }
+#pragma unroll
+        for (int h2 = 0; h2 < M / 2; ++h2) {
+            const int k2 = r * (M / 2) + h2;
+            const float2 val = r ? y[M / 2 + h2] : y[h2];
+            reg[g + M * k2] = make_float2(scale * val.x, -scale * val.y);
+        }
+    } else {
+#pragma unroll
+        for (int k2 = 1; k2 < M; ++k2) y[k2] = cmul(y[k2], __ldg(&twT[(r * k2 * (NTH / 32)) & (NTH - 1)]));
+#pragma unroll
+        for (int h = R / 2; h >= 1; h >>= 1) {
+            const bool up = (r & h) != 0;
+            const float2 w = (h > 1) ? __ldg(&twT[(r & (h - 1)) * (NTH / (2 * h))]) : make_float2(1.f, 0.f);
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, y[k2].x, h),
+                                              __shfl_xor_sync(0xffffffffu, y[k2].y, h));
+                const float2 d = csub(pv, y[k2]);
+                y[k2] = up ? ((h > 1) ? cmul(d, w) : d) : cadd(y[k2], pv);
+            }
+        }
+        int t = 0;
+        for (int b = 1; b < R; b <<= 1) t = (t << 1) | ((r & b) ? 1 : 0);
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const int l = g + M * (k2 + M * t);
+            if (l < NH) reg[l] = make_float2(scale * y[k2].x, -scale * y[k2].y);
+        }
+    }
+    __syncwarp();
+    float2 *dst = Gpol + ((size_t)img * n_xi + ring) * NH;
+    for (int l = lane; l < NH; l += 32) dst[l] = reg[l];
+}
+
+template <int NTH>
+static int launch_ring_ifft(ffb_plan_t p, int m, const float *Yhat, float2 *Gpol, cudaStream_t s) {
+    constexpr int RB = rfft_rb<NTH>();
+    static int attr = 0;
+    const size_t smem = sizeof(float2) * (size_t)RB * (NTH + NTH / 2 + 1);
+    if (smem > 48 * 1024 && attr < (int)smem) {
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_ring_ifft<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
+        if (e) return e;
+        attr = (int)smem;
+    }
+    dim3 g((p->n_xi + RB - 1) / RB, m);
+    ProfScope ps(p, FFB_KC_ADJ_RING, s);
+    k_ring_ifft<NTH><<<g, 32 * RB, smem, s>>>(Yhat, p->n_xi, p->k_max, p->chunk, (const float2 *)p->d_twT,
+                                               (const float2 *)p->d_twA, Gpol);
+    p->launches++;
+    return ffb_check_cuda(cudaGetLastError());
+}
+
+// the adjoint's inverse ring DFT for plans whose ring FFT runs in registers
+int ffb_launch_ring_ifft(ffb_plan_t p, int m, const float *Yhat, float2 *Gpol, cudaStream_t s) {
+    if (p->k_max >= p->n_theta / 2) return FFB_ERR_UNSUPPORTED;
+    switch (p->n_theta) {
+        case 64: return launch_ring_ifft<64>(p, m, Yhat, Gpol, s);
+        case 128: return launch_ring_ifft<128>(p, m, Yhat, Gpol, s);
+        case 256: return launch_ring_ifft<256>(p, m, Yhat, Gpol, s);
+        case 512: return launch_ring_ifft<512>(p, m, Yhat, Gpol, s);
+        case 1024: return launch_ring_ifft<1024>(p, m, Yhat, Gpol, s);
+        default: return FFB_ERR_UNSUPPORTED;
+    }
+}
+
 // ring FFT twiddles of the plan (built with the fused path's tables)
 int ffb_ring_prepare(ffb_plan_t p, cudaStream_t s) {
     int e = FFB_OK;
