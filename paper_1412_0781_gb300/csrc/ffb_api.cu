@@ -71,7 +71,8 @@ extern "C" int ffb_polar(ffb_plan_t p, const float *d_images, int64_t n, float *
     for (int64_t i0 = 0; i0 < n; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, n - i0);
         if (p->fused) {
-            CK(ffb_launch_fused_polar(p, d_images, i0, m, (float2 *)(d_F + (size_t)i0 * per), s, i0 > 0));
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, (float2 *)(d_F + (size_t)i0 * per), s, i0 > 0,
+                                      n - (i0 + m)));
         } else {
             CK(ffb_launch_grid(p, d_images, i0, m, s));
             CK(ffb_launch_polar(p, m, d_F + (size_t)i0 * per, s));
@@ -92,7 +93,7 @@ int ffb_expand_part(ffb_plan_t p, const float *d_images, int64_t g0, int64_t g1,
         int m = (int)std::min<int64_t>(p->chunk, g1 - i0);
         if (p->fused) {
             // chunks after the first follow this call's own kernels
-            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0));
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0, g1 - (i0 + m)));
             RingOut r = ring;   // this chunk's images in the group's planes
             const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
             r.p0 = (char *)ring.p0 + off;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
                    const float2 *__restrict__ tw, const float2 *__restrict__ twA, int n_xi, int n_theta, int nq0,
                    const float4 *__restrict__ units, const int2 *__restrict__ blocks, int nblk0, int nblk1,
-                   float2 *__restrict__ Fpol, int *status) {
+                   float2 *__restrict__ Fpol, int *status, int wave, int n_after) {
     constexpr int L = N / 2;
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
@@ -195,6 +195,26 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     const int img = blockIdx.y;
     const float *im = images + (size_t)img * L * L;
     pdl_trigger();
+    // L2 prefetches (hints, with no completion to wait for), one bulk copy of
+    // half `half` of an image's pixel rows each: this image's, so that the
+    // transform rounds after the first find them in L2, and the image that
+    // the CTA one wave later reads (img + wave of this launch, else of the
+    // images that follow it), so that its first round does too
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(L / 2 * L * 4);
+        const float *own = images + ((size_t)img * L + (size_t)half * (L / 2)) * L;
+        if ((reinterpret_cast<uintptr_t>(own) & 15) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(own)), "r"(bytes)
+                         : "memory");
+        const int tgt = img + wave;
+        if (wave > 0 && tgt < (int)gridDim.y + n_after) {
+            const float *nxt = images + ((size_t)tgt * L + (size_t)half * (L / 2)) * L;
+            if ((reinterpret_cast<uintptr_t>(nxt) & 15) == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(nxt)),
+                             "r"(bytes)
+                             : "memory");
+        }
+    }
     // the zero row below the half plane (no transform writes it)
     for (int i = threadIdx.x; i < SLD; i += FUS_NT) S[MH * SLD + i] = make_float2(0.f, 0.f);
     // cluster: the peer's S in the cluster window, this CTA's share of the
@@ -540,7 +560,7 @@ int ffb_launch_fused_spread(ffb_plan_t p, const float2 *Gpol, int m, float2 *Gex
 // stream is one of this library's and does not write the images)
 template <int N, int W>
 static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
-                        bool pdl) {
+                        bool pdl, int64_t n_after) {
     static int attr = 0, attr_cl = 0;
     const size_t smem = fused_smem<N, W>();
     const bool cl = p->fused == 2;
@@ -552,6 +572,12 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
         done = (int)smem;
     }
     const float *img = d_images + (size_t)i0 * p->L * p->L;
+    // images per wave at one CTA per SM and two per image (the N = 256
+    // kernel; smaller grids run more CTAs per SM and the prefetch, a hint,
+    // then lands on images already under way)
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int wave = sms / 2;
     ProfScope ps(p, FFB_KC_GRID_INTERP, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, m);
@@ -574,7 +600,7 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
                                               img, p->off, (const float *)p->d_corr, (const float2 *)p->d_twN,
                                               (const float2 *)p->d_twG, p->n_xi, p->n_theta, p->nq0, (const float4 *)p->d_nodes,
                                               (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
-                                              p->d_status));
+                                              p->d_status, wave, (int)std::min<int64_t>(n_after, 1 << 20)));
     p->launches++;
     return e;
 }
@@ -867,8 +893,8 @@ extern "C" int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta
 }
 
 int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
-                           bool pdl) {
-    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s, pdl);
-    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s, pdl);
+                           bool pdl, int64_t n_after) {
+    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after);
+    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after);
     return FFB_ERR_UNSUPPORTED;
 }

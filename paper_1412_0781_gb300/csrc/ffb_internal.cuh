@@ -363,8 +363,10 @@ int ffb_ring_prepare(ffb_plan_t plan, cudaStream_t s);   // ring FFT twiddle tab
 // adjoint spreading of m images' half-ring values (polar-buffer layout) into
 // the zeroed extended grid [m][Mh][N] with the fused path's unit table
 int ffb_launch_fused_spread(ffb_plan_t plan, const float2 *Gpol, int m, float2 *Gext, cudaStream_t s);
+// n_after: images that follow the chunk [i0, i0 + m) in d_images (the
+// kernel prefetches one wave ahead into L2, never past them)
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
-                           cudaStream_t s, bool pdl = false);
+                           cudaStream_t s, bool pdl = false, int64_t n_after = 0);
 struct RingOut {
     int fmt;           // FFB_FMT_*
     void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra), at the launch's first image
