@@ -507,30 +507,14 @@ def run_ours(args):
         hbuf.copy_(images)
         del images
         torch.cuda.empty_cache()
-        dbuf = torch.empty(hbuf.shape, dtype=torch.float32, device=dev)
         out_mean = torch.empty(plan.p[0], dtype=torch.float64, pin_memory=True)
         out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
 
-        copy_stream = torch.cuda.Stream(device=dev)
-        # host->device copies of at most ~200 MB each: on this system larger
-        # single copies from pinned memory ran an order of magnitude slower
-        nparts = max(8, -(-hbuf.numel() * 4 // (200 << 20)))
-        bounds = [(n * c // nparts, n * (c + 1) // nparts) for c in range(nparts)]
-        events = [torch.cuda.Event() for _ in range(nparts)]
-
         def e2e_step():
-            # host->device copy of part c+1 overlaps the expansion of part c
-            with torch.cuda.stream(copy_stream):
-                for c, (a, b) in enumerate(bounds):
-                    dbuf[a:b].copy_(hbuf[a:b], non_blocking=True)
-                    events[c].record(copy_stream)
-            for c, (a, b) in enumerate(bounds):
-                torch.cuda.current_stream().wait_event(events[c])
-                plan.expand(dbuf[a:b], out=r["coef"][a:b])
-                plan.covariance(r["coef"][a:b], reset=(c == 0))
-            m, C = plan.cov_get()
-            out_mean.copy_(m)
-            out_C.copy_(C)
+            # one C-ABI call: host images in, host mean and covariance out; the
+            # library copies the images in parts on its own stream, each part
+            # overlapping the expansion of the one before
+            plan.expand_cov_host(hbuf, reset=True, mean_out=out_mean, C_out=out_C)
 
         for _ in range(3):
             e2e_step()
@@ -548,7 +532,7 @@ def run_ours(args):
         e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
                "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8), "steps": k,
                "median_step_ms": statistics.median(steps_ms), "max_step_ms": max(steps_ms),
-               "h2d_parts": nparts}
+               "call": "ffb_expand_cov_host (pinned host images -> host mean and covariance)"}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:

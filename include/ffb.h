@@ -257,6 +257,26 @@ int ffb_cov_export(ffb_plan_t plan, double *h_state, void *stream);
 int ffb_cov_merge(int k_max, const int *h_p, int nstates, const double *h_states, double *h_out);
 int ffb_cov_import(ffb_plan_t plan, const double *h_state, void *stream);
 
+/* ffb_expand_cov_host -- Alg. 1 steps 3-4 and the accumulation of Alg. 2
+ * steps 1-4 for n images held in HOST memory, with the statistics returned
+ * to host memory: the end-to-end call of a user whose image stack sits in
+ * host RAM.  h_images [n][L][L] float32 (page-locked memory gives the full
+ * copy bandwidth; pageable memory works at the driver's staged rate).  The
+ * images move to the device in parts of whole chunks through a ring of
+ * three device buffers on a copy stream of the plan, each copy overlapping
+ * the expansion of the part before it; every part is expanded as ffb_expand
+ * and added to the accumulator as ffb_covariance (reset != 0 clears it
+ * first, so reset = 0 continues an earlier accumulation).  Then, when h_mean0
+ * or h_C is not NULL, the accumulator is finalised as ffb_cov_get and the
+ * k = 0 mean (p_0 float64) and the packed blocks (sum p_k^2 float64) are
+ * copied to them.  The device buffers (three parts of at most 256 MiB of
+ * images, and the coefficients of one part: P / (2 L^2) times as many bytes
+ * as its images) are allocated on first use and kept by the plan.  Synchronises `stream`; returns latched
+ * device errors, FFB_ERR_STATE when statistics are asked for and nothing was
+ * accumulated.  The host buffer must stay valid until the call returns. */
+int ffb_expand_cov_host(ffb_plan_t plan, const float *h_images, int64_t n, int reset,
+                        double *h_mean0, double *h_C, void *stream);
+
 /* ffb_eig -- Alg. 2 step 4: eigenpairs of every block C^(k) by a batched
  * float64 cyclic Jacobi solver on the GPU (one CTA per block).
  * d_evals[P]: per block descending; d_evecs packed p_k x p_k row-major,

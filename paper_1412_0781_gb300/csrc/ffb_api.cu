@@ -174,6 +174,76 @@ extern "C" int ffb_cov_get(ffb_plan_t p, double *d_mean0, double *d_C, void *str
     return read_status(p, s);
 }
 
+// Images in host memory, statistics back in host memory: the images go to
+// the device in parts of host_cap images through a ring of FFB_HOST_SLOTS
+// device buffers, copied on the plan's own stream while the previous parts
+// are expanded on the caller's; each copy waits only for its slot's previous
+// expansion, each expansion only for its own copy.
+extern "C" int ffb_expand_cov_host(ffb_plan_t p, const float *h_images, int64_t n, int reset, double *h_mean0,
+                                   double *h_C, void *stream) {
+    FFB_PLAN_HERE(p);
+    if (!p || n < 0 || (n > 0 && !h_images)) return FFB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n > 0) {
+        CK(ffb_ensure_scratch(p));
+        const size_t img_bytes = sizeof(float) * (size_t)p->L * p->L;
+        // a part of two quadrature groups, or fewer images where that would
+        // exceed 256 MiB per slot (whole chunks, at least one)
+        const int64_t grp = (int64_t)(p->precision != FFB_FP32 ? ffb_tc_group(p) : 1) * p->chunk;
+        int64_t cap = 2 * grp;
+        const int64_t lim = std::max<int64_t>(p->chunk, ((int64_t)(256u << 20) / (int64_t)img_bytes) / p->chunk * p->chunk);
+        cap = std::min(cap, lim);
+        if (p->host_cap < cap) {
+            if (p->h2d) CK(ffb_check_cuda(cudaStreamSynchronize(p->h2d)));
+            CK(ffb_check_cuda(cudaStreamSynchronize(s)));
+            if (p->d_hostimg) cudaFree(p->d_hostimg);
+            if (p->d_hostcoef) cudaFree(p->d_hostcoef);
+            p->d_hostimg = nullptr;
+            p->d_hostcoef = nullptr;
+            p->host_cap = 0;
+            CK(ffb_check_cuda(cudaMalloc((void **)&p->d_hostimg, img_bytes * (size_t)cap * FFB_HOST_SLOTS)));
+            CK(ffb_check_cuda(cudaMalloc((void **)&p->d_hostcoef, sizeof(float2) * (size_t)cap * p->P)));
+            p->host_cap = cap;
+        }
+        cap = p->host_cap;
+        if (!p->h2d) {
+            CK(ffb_check_cuda(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking)));
+            for (int i = 0; i < FFB_HOST_SLOTS; ++i) {
+                CK(ffb_check_cuda(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming)));
+                CK(ffb_check_cuda(cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming)));
+            }
+        }
+        // the slots' earlier contents may still be read by work the caller
+        // queued on s before this call
+        CK(ffb_check_cuda(cudaEventRecord(p->ev_free[0], s)));
+        CK(ffb_check_cuda(cudaStreamWaitEvent(p->h2d, p->ev_free[0], 0)));
+        int64_t part = 0;
+        for (int64_t i0 = 0; i0 < n; i0 += cap, ++part) {
+            const int64_t m = std::min(cap, n - i0);
+            const int slot = (int)(part % FFB_HOST_SLOTS);
+            float *d_img = p->d_hostimg + (size_t)slot * cap * p->L * p->L;
+            if (part >= FFB_HOST_SLOTS) CK(ffb_check_cuda(cudaStreamWaitEvent(p->h2d, p->ev_free[slot], 0)));
+            CK(ffb_check_cuda(cudaMemcpyAsync(d_img, h_images + (size_t)i0 * p->L * p->L, img_bytes * (size_t)m,
+                                              cudaMemcpyHostToDevice, p->h2d)));
+            CK(ffb_check_cuda(cudaEventRecord(p->ev_copied[slot], p->h2d)));
+            CK(ffb_check_cuda(cudaStreamWaitEvent(s, p->ev_copied[slot], 0)));
+            CK(ffb_expand_on(p, d_img, m, p->d_hostcoef, s));
+            CK(ffb_check_cuda(cudaEventRecord(p->ev_free[slot], s)));
+            CK(ffb_covariance(p, p->d_hostcoef, m, reset && i0 == 0, stream));
+        }
+    } else if (reset) {
+        CK(ffb_covariance(p, nullptr, 0, 1, stream));
+    }
+    if (!h_mean0 && !h_C) return read_status(p, s);
+    if (p->n_acc <= 0) return FFB_ERR_STATE;
+    CK(ffb_launch_cov_final(p, s));
+    if (h_mean0)
+        CK(ffb_check_cuda(cudaMemcpyAsync(h_mean0, p->d_mean, sizeof(double) * p->p[0], cudaMemcpyDeviceToHost, s)));
+    if (h_C)
+        CK(ffb_check_cuda(cudaMemcpyAsync(h_C, p->d_Cfin, sizeof(double) * p->cov_total, cudaMemcpyDeviceToHost, s)));
+    return read_status(p, s);
+}
+
 extern "C" int ffb_eig(ffb_plan_t p, double *d_evals, double *d_evecs, void *stream) {
     FFB_PLAN_HERE(p);
     if (!p) return FFB_ERR_ARG;

@@ -35,6 +35,7 @@ struct ProfEv {
 // FFB_ERR_TIMEOUT instead of spinning forever.
 #define FFB_WAIT_BUDGET (4000000000LL)
 
+#define FFB_HOST_SLOTS 3   // image parts in flight in ffb_expand_cov_host
 struct ffb_plan_s {
     // problem
     int L, off;          // image size, pixel index offset (i = a - off)
@@ -107,6 +108,14 @@ struct ffb_plan_s {
     float *d_M = nullptr;          // [cov_total] U diag(h) U^T per block
     int selected = 0;              // filter matrices valid
     int eig_ready = 0;             // d_evals / d_evecs hold eigenpairs
+    // host-buffer entry point (ffb_expand_cov_host): a ring of FFB_HOST_SLOTS
+    // device image buffers of host_cap images each, the coefficients of one
+    // part, the copy stream and per-slot events (copy done, slot free again)
+    float *d_hostimg = nullptr;
+    float *d_hostcoef = nullptr;
+    int64_t host_cap = 0;
+    cudaStream_t h2d = nullptr;
+    cudaEvent_t ev_copied[FFB_HOST_SLOTS] = {}, ev_free[FFB_HOST_SLOTS] = {};
     // status word written by kernels (first nonzero error wins)
     int *d_status = nullptr;
     // clock-cycle budget of the waits between the pipeline roles of the

@@ -195,9 +195,14 @@ static void free_plan(ffb_plan_t p) {
                     p->d_cov_work, p->d_cov_sb, p->d_H, p->d_G, p->d_Fhat, p->d_acc, p->d_sum0,
                     p->d_shift, p->d_Cfin, p->d_mean, p->d_evals, p->d_evecs, p->d_status,
                     p->d_coef_den, p->d_gain, p->d_M, p->d_eig_work, p->d_Fpol, p->d_nodes, p->d_node_blk, p->d_twA, p->d_twG,
-                    p->d_tunits, p->d_tblk, p->d_tnodes};
+                    p->d_tunits, p->d_tblk, p->d_tnodes, p->d_hostimg, p->d_hostcoef};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    for (int i = 0; i < FFB_HOST_SLOTS; ++i) {
+        if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
+        if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
+    }
+    if (p->h2d) cudaStreamDestroy(p->h2d);
     for (ProfEv &e : p->prof) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

@@ -38,6 +38,7 @@ SIGNATURES = {
     "ffb_expand_adjoint": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "ffb_covariance": (_i, [_vp, _vp, _i64, _i, _vp]),
     "ffb_cov_get": (_i, [_vp, _vp, _vp, _vp]),
+    "ffb_expand_cov_host": (_i, [_vp, _vp, _i64, _i, _vp, _vp, _vp]),
     "ffb_cov_export": (_i, [_vp, _pd, _vp]),
     "ffb_cov_merge": (_i, [_i, _pi, _i, _pd, _pd]),
     "ffb_cov_import": (_i, [_vp, _pd, _vp]),
@@ -158,6 +159,16 @@ def _check(status, where):
 def _ptr(t, dtype, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
     if t.dtype != dtype:
         raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
     if not t.is_contiguous():
@@ -289,6 +300,22 @@ class Plan:
         C = torch.empty(self.cov_total, device=device, dtype=torch.float64)
         _check(load().ffb_cov_get(self._h, _ptr(mean, torch.float64, "mean"), _ptr(C, torch.float64, "C"),
                                   _stream(stream)), "ffb_cov_get")
+        return mean, C
+
+    def expand_cov_host(self, images, reset=True, mean_out=None, C_out=None, stream=None):
+        """Synchronising: host images float32 (n, L, L) (pinned for full copy
+        bandwidth) -> expansion and covariance accumulation on the device ->
+        (mean0 float64 (p_0,), packed C float64 (sum p_k^2,)) in host memory
+        (ffb_expand_cov_host).  mean_out / C_out: optional host float64
+        tensors to fill."""
+        n = images.shape[0]
+        mean = torch.empty(self.p[0], dtype=torch.float64) if mean_out is None else mean_out
+        C = torch.empty(self.cov_total, dtype=torch.float64) if C_out is None else C_out
+        if mean.numel() < self.p[0] or C.numel() < self.cov_total:
+            raise ValueError("mean_out / C_out too small")
+        _check(load().ffb_expand_cov_host(self._h, _hptr(images, torch.float32, "images"), n, int(bool(reset)),
+                                          _hptr(mean, torch.float64, "mean_out"), _hptr(C, torch.float64, "C_out"),
+                                          _stream(stream)), "ffb_expand_cov_host")
         return mean, C
 
     def state_len(self):
