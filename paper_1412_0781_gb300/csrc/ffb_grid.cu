@@ -8,7 +8,8 @@
 // (half 1): a (N/2 + 1 + 2h)^2 block that fits in one SM's shared memory
 // for N <= 256 (137 x 137 complex = 150 KB at N = 256, w = 8).
 //
-// Phase 1  rows: for pixel rows a1 (two per complex FFT), the length-N DFT
+// Phase 1  rows: for pixel rows a1 (two per complex FFT, one FFT per half
+//          warp at N = 256, per warp at N = 128), the length-N DFT
 //          over i2 of I(i) corr(i1) corr(i2) placed at i2 mod N; the outputs
 //          m2 in [-h, N/2 + h] are stored in column a1 of S[m2 + h][.].
 // Phase 2  columns: for each m2 row of S, the length-N DFT over i1 (entries
@@ -162,6 +163,60 @@ __device__ __forceinline__ void warp_fft_halfzero(const float2 *z, float2 *buf, 
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Length-256 forward DFT of the same half-zero sequence (nonzeros at
+// (a - 64) mod 256, a < 128) by 16 lanes, one half of a warp, as a 16 x 16
+// four-step: index l = 16 m + j (lane j of the half), k = k1 + 16 k2,
+//   X_k = sum_j W^{j k1} [sum_m s_{16m+j} W_16^{m k1}] W_16^{j k2},  W = e^{-2 pi i/256}.
+// xin[t] holds s at m = t (t < 4) and m = 8 + t (t >= 4), the only nonzero
+// m; the length-16 DFT over m therefore starts from four half-zero length-4
+// DFTs.  After the twiddle W^{j k1} (plan table [k1][j]) one transpose
+// through the half's 128-entry buffer, in two rounds of eight k1 each
+// (position rotated by k1: conflict-free), gives lane j the values of k1 = j
+// over all sixteen j; a length-16 DFT over them leaves X_{j + 16 k2} in
+// y[k2].  No cross-lane shuffles: two transforms per warp, each with about
+// 40 % fewer instructions than the whole-warp form above.  Phase 1 at
+// N = 256 uses it (its 32 row pairs per CTA then take one round of the 24
+// warps instead of two); in phase 2 the outputs' way back into the rows
+// costs more than it saves, and phase 2 keeps the whole-warp form.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void half_fft256_halfzero(const float2 (&xin)[8], float2 (&y)[16], float2 *hbuf,
+                                                     const float2 *__restrict__ twH, int j) {
+    // pass A: m = 4 n1 + n2 with n1 in {0, 3}: DFT4 over n1 of (a, 0, 0, d)
+    float2 u[4][4];   // u[n2][q] = that DFT4, times W_16^{n2 q}
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        const float2 a = xin[n2], d = xin[4 + n2];
+        const float2 v[4] = {cadd(a, d), make_float2(a.x - d.y, a.y + d.x), csub(a, d),
+                             make_float2(a.x + d.y, a.y - d.x)};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[n2][q] = (n2 * q == 0) ? v[q] : cmul(v[q], w16(n2 * q));
+    }
+    float2 x[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float2 v[4] = {u[0][q], u[1][q], u[2][q], u[3][q]};
+        dft4<false>(v);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) x[q + 4 * p] = v[p];
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], __ldg(&twH[k1 * 16 + j]));
+    // transpose, k1 < 8 then k1 >= 8: entry (k1 mod 8, j) at 16 (k1 mod 8) + ((j + k1) mod 16)
+#pragma unroll
+    for (int rnd = 0; rnd < 2; ++rnd) {
+#pragma unroll
+        for (int k1 = 8 * rnd; k1 < 8 * rnd + 8; ++k1) hbuf[(k1 - 8 * rnd) * 16 + ((j + k1) & 15)] = x[k1];
+        __syncwarp();
+        if ((j >> 3) == rnd) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y[i] = hbuf[(j - 8 * rnd) * 16 + ((i + j) & 15)];
+        }
+        __syncwarp();
+    }
+    dft_reg<16>(y);
+}
+
 // distributed shared memory of a thread-block cluster: a float2 store into the
 // peer CTA's shared memory (cluster-space address from mapa), and the
 // cluster-wide barrier with release / acquire ordering of shared memory
@@ -233,33 +288,102 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     // ---- phase 1: row transforms (two pixel rows per complex FFT) --------
     // (cluster: this CTA's pixel rows are a1 in [part L/2, (part + 1) L/2))
     bool bad = false;
-    for (int rp = part * (L / 2 / nparts) + warp; rp < (part + 1) * (L / 2 / nparts); rp += FUS_WARPS) {
-        const int a1 = 2 * rp;
-        float x[L / 32], y[L / 32];
+    // N = 256: one row pair per half warp (half_fft256_halfzero); half hw of
+    // the warp takes pair slot 2 warp + hw, both halves run every step
+    const int hw = lane >> 4, j16 = lane & 15;
+    float2 *hbuf = buf + hw * (N / 2);
+    const float2 *twH = twA + N;      // W^{j k1}, [16][16], after the warp FFT's table
+    if constexpr (N == 256) {
+        static_assert(N != 256 || (L == 128 && H == 4 && MH == 137), "half-warp FFT layout");
+        const int nrp = L / 2 / nparts;
+        for (int q0 = 2 * warp; q0 < nrp; q0 += 2 * FUS_WARPS) {
+            const int q = q0 + hw;
+            const bool act = q < nrp;
+            const int a1 = 2 * (part * nrp + (act ? q : 0));
+            const float c1 = corr[a1], c2 = corr[a1 + 1];
+            float2 xin[8];
 #pragma unroll
-        for (int q = 0; q < L / 32; ++q) {
-            x[q] = __ldg(&im[(size_t)a1 * L + lane + 32 * q]);
-            y[q] = __ldg(&im[(size_t)(a1 + 1) * L + lane + 32 * q]);
-        }
-        const float c1 = corr[a1], c2 = corr[a1 + 1];
-        float2 z[L / 32];
+            for (int t = 0; t < 8; ++t) {
+                const int a2 = (t < 4) ? (L / 2 + 16 * t + j16) : (16 * (t - 4) + j16);
+                float xv = 0.f, yv = 0.f;
+                if (act) {
+                    xv = __ldg(&im[(size_t)a1 * L + a2]);
+                    yv = __ldg(&im[(size_t)(a1 + 1) * L + a2]);
+                }
+                bad |= !(isfinite(xv) && isfinite(yv));
+                const float ca = corr[a2];
+                xin[t] = make_float2(xv * c1 * ca, yv * c2 * ca);
+            }
+            float2 Z[16];
+            half_fft256_halfzero(xin, Z, hbuf, twH, j16);
+            // the two real rows' spectra from Z_m and conj Z_{N-m}, through the
+            // half's buffer in two rounds: k in [0, 64) u [192, 256) (pairs of
+            // m in [0, 64) u [252, 256): rows e in [0, 68)), then k in
+            // [64, 192) (m in [65, 132]: e in [69, 136]); slot k2 of lane j16
+            // is k = j16 + 16 k2.  Row e = 68 (m = 64, partner 192) straddles
+            // the rounds: lane 0 holds both (k2 = 4, 12) and writes it.
+            if (act && j16 == 0) {
+                const float2 Zm = Z[4], Zc = cconj(Z[12]);
+                const float2 D = csub(Zm, Zc);
+                S[68 * SLD + a1] = make_float2(0.5f * (Zm.x + Zc.x), 0.5f * (Zm.y + Zc.y));
+                S[68 * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
+            }
 #pragma unroll
-        for (int q = 0; q < L / 32; ++q) {
-            const int a2 = lane + 32 * q;
-            bad |= !(isfinite(x[q]) && isfinite(y[q]));
-            const float ca = corr[a2];
-            z[q] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
+            for (int rnd = 0; rnd < 2; ++rnd) {
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const bool in0 = (k2 < 4 || k2 >= 12);
+                    if (in0 == (rnd == 0)) {
+                        const int k = j16 + 16 * k2;
+                        hbuf[rnd == 0 ? (k < 64 ? k : k - 128) : k - 64] = Z[k2];
+                    }
+                }
+                __syncwarp();
+                const int e0 = (rnd == 0) ? 0 : 69, e1 = (rnd == 0) ? 68 : MH;
+                for (int e = e0 + j16; e < e1; e += 16) {
+                    const int m = (e - H) & (N - 1), mc = (N - m) & (N - 1);
+                    const int pm = (rnd == 0) ? (m < 64 ? m : m - 128) : m - 64;
+                    const int pc = (rnd == 0) ? (mc < 64 ? mc : mc - 128) : mc - 64;
+                    const float2 Zm = hbuf[pm];
+                    const float2 Zc = cconj(hbuf[pc]);
+                    const float2 D = csub(Zm, Zc);
+                    if (act) {
+                        S[e * SLD + a1] = make_float2(0.5f * (Zm.x + Zc.x), 0.5f * (Zm.y + Zc.y));
+                        S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
+                    }
+                }
+                __syncwarp();
+            }
         }
-        warp_fft_halfzero<N>(z, buf, tw, twA, lane);
-        for (int e = lane; e < MH; e += 32) {
-            const int m = (e - H) & (N - 1);
-            const float2 Z = buf[fswz<N>(m)];
-            const float2 Zc = cconj(buf[fswz<N>((N - m) & (N - 1))]);
-            const float2 D = csub(Z, Zc);
-            S[e * SLD + a1] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
-            S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
+    } else {
+        for (int rp = part * (L / 2 / nparts) + warp; rp < (part + 1) * (L / 2 / nparts); rp += FUS_WARPS) {
+            const int a1 = 2 * rp;
+            float x[L / 32], y[L / 32];
+#pragma unroll
+            for (int q = 0; q < L / 32; ++q) {
+                x[q] = __ldg(&im[(size_t)a1 * L + lane + 32 * q]);
+                y[q] = __ldg(&im[(size_t)(a1 + 1) * L + lane + 32 * q]);
+            }
+            const float c1 = corr[a1], c2 = corr[a1 + 1];
+            float2 z[L / 32];
+#pragma unroll
+            for (int q = 0; q < L / 32; ++q) {
+                const int a2 = lane + 32 * q;
+                bad |= !(isfinite(x[q]) && isfinite(y[q]));
+                const float ca = corr[a2];
+                z[q] = make_float2(x[q] * c1 * ca, y[q] * c2 * ca);
+            }
+            warp_fft_halfzero<N>(z, buf, tw, twA, lane);
+            for (int e = lane; e < MH; e += 32) {
+                const int m = (e - H) & (N - 1);
+                const float2 Z = buf[fswz<N>(m)];
+                const float2 Zc = cconj(buf[fswz<N>((N - m) & (N - 1))]);
+                const float2 D = csub(Z, Zc);
+                S[e * SLD + a1] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+                S[e * SLD + a1 + 1] = make_float2(0.5f * D.y, -0.5f * D.x);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     if (bad) ffb_flag(status, FFB_ERR_NONFINITE);
     __syncthreads();
@@ -837,15 +961,23 @@ int ffb_fused_prepare(ffb_plan_t p, cudaStream_t s) {
     std::vector<int2> blk;
     int nb[2] = {0, 0};
     if ((e = build_units(N, p->w, p->beta, p->n_xi, p->n_theta, xi.data(), rec, blk, nb))) return e;
-    // FFT twiddles W_N^{j k1} as [k1][j] (k1 < N / 32, j < 32), from float64
+    // FFT twiddles W_N^{j k1} as [k1][j] (k1 < N / 32, j < 32: the whole-warp
+    // FFT), then at N = 256 as [k1][j] (k1, j < 16: the half-warp FFT), from
+    // float64
     {
         const int MG = N / 32;
-        std::vector<float2> twg((size_t)MG * 32);
+        std::vector<float2> twg((size_t)MG * 32 + (N == 256 ? 256 : 0));
         for (int k1 = 0; k1 < MG; ++k1)
             for (int j = 0; j < 32; ++j) {
                 const double a = -2.0 * M_PI * (double)((j * k1) % N) / (double)N;
                 twg[(size_t)k1 * 32 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
             }
+        if (N == 256)
+            for (int k1 = 0; k1 < 16; ++k1)
+                for (int j = 0; j < 16; ++j) {
+                    const double a = -2.0 * M_PI * (double)((j * k1) % N) / (double)N;
+                    twg[(size_t)N + k1 * 16 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+                }
         if (p->d_twG) cudaFree(p->d_twG);
         p->d_twG = nullptr;
         e = ffb_check_cuda(cudaMalloc((void **)&p->d_twG, sizeof(float2) * twg.size()));
