@@ -171,8 +171,8 @@ def hbm_floor(plan):
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu:^k_grid_interp_half",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "256b7490993661bdb66105e35481ef928e7f0034996e6a7c52429e7074644578",
-                    "bytes_per_launch": 12989184 + 55552, "images_per_launch": 152},
+                    "sha256": "35f496769f5c561136bcd7a33ce1e037d7159e0a9cceb69c5eac28400644be0d",
+                    "bytes_per_launch": 17964288 + 46336, "images_per_launch": 152},
 }
 
 
