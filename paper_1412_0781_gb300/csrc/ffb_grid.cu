@@ -307,8 +307,11 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
                 const int a2 = (t < 4) ? (L / 2 + 16 * t + j16) : (16 * (t - 4) + j16);
                 float xv = 0.f, yv = 0.f;
                 if (act) {
-                    xv = __ldg(&im[(size_t)a1 * L + a2]);
-                    yv = __ldg(&im[(size_t)(a1 + 1) * L + a2]);
+                    // pixels are read once: evict first (the unit table and
+                    // the polar buffer then keep their L2 lines)
+                    const unsigned long long pf = l2_evict_first();
+                    xv = ldg_hint(&im[(size_t)a1 * L + a2], pf);
+                    yv = ldg_hint(&im[(size_t)(a1 + 1) * L + a2], pf);
                 }
                 bad |= !(isfinite(xv) && isfinite(yv));
                 const float ca = corr[a2];

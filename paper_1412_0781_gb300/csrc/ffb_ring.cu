@@ -74,7 +74,8 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
         float2 v[M / 2], E[M / 2];
 #pragma unroll
         for (int m = 0; m < M / 2; ++m) {
-            const float2 xm = src[32 * m + lane];
+            // read once: evict first, so that the planes stay in L2 longer
+            const float2 xm = ldg_hint(&src[32 * m + lane], l2_evict_first());
             u[m] = xm.x;
             v[m] = make_float2(xm.y * wsin<M>(m), xm.y * wcos<M>(m));
         }
@@ -198,8 +199,10 @@ k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const 
                 const float2 hf = __bfloat1622float2(h);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
                 if (two) {
-                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out0 + idx) = h;
-                    if (FMT == FFB_FMT_BF16X2) *(__nv_bfloat162 *)((__nv_bfloat16 *)out1 + idx) = l;
+                    // the quadrature reads the planes later in the step: evict last
+                    const unsigned long long pl = l2_evict_last();
+                    st_hint((__nv_bfloat16 *)out0 + idx, *(const unsigned *)&h, pl);
+                    if (FMT == FFB_FMT_BF16X2) st_hint((__nv_bfloat16 *)out1 + idx, *(const unsigned *)&l, pl);
                 } else {
                     ((__nv_bfloat16 *)out0)[idx] = __low2bfloat16(h);
                     if (FMT == FFB_FMT_BF16X2) ((__nv_bfloat16 *)out1)[idx] = __low2bfloat16(l);

@@ -36,8 +36,12 @@
 
 // operand planes of one quadrature group: 4 BF16x3 chunks at L = 128 (114 MB;
 // measured 1.7 % faster per step than 2 chunks in 64 MiB, though the planes
-// and the polar buffer then exceed L2)
+// and the polar buffer then exceed L2; with the L2 eviction hints of the
+// pixel, polar-buffer and plane accesses, 4 chunks 1,194 k images/s, 2 chunks
+// 1,175 k, 1 chunk 1,169 k)
+#ifndef FFB_PLANE_BUDGET_MB
 #define FFB_PLANE_BUDGET_MB 128
+#endif
 
 #define TC_BUDGET FFB_WAIT_BUDGET   // drains of issued copies and MMAs
 
@@ -200,8 +204,11 @@ k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ man
                     uint8_t *sb = sm + (size_t)stg * st_bytes;
                     // the stage holds BNmax rows of B; this stack's box fills BN of them
                     tc::mbar_arrive_expect_tx(&full[stg], NPA * a_bytes + NPB * (uint32_t)st->BN * 128u);
-                    tc::tma_load_3d(sb, &st->mA0, &full[stg], ch * KCH, 128 * m, k);
-                    if (NPA > 1) tc::tma_load_3d(sb + a_bytes, &st->mA1, &full[stg], ch * KCH, 128 * m, k);
+                    // A planes are read once (evict first); the radial table
+                    // B is read by every item of its k (normal)
+                    const unsigned long long pf = l2_evict_first();
+                    tc::tma_load_3d_hint(sb, &st->mA0, &full[stg], ch * KCH, 128 * m, k, pf);
+                    if (NPA > 1) tc::tma_load_3d_hint(sb + a_bytes, &st->mA1, &full[stg], ch * KCH, 128 * m, k, pf);
                     tc::tma_load_3d(sb + NPA * a_bytes, &st->mB0, &full[stg], ch * KCH, 0, k);
                     if (NPB > 1) tc::tma_load_3d(sb + NPA * a_bytes + b_bytes, &st->mB1, &full[stg], ch * KCH, 0, k);
                 }
