@@ -516,9 +516,23 @@ def run_ours(args):
             # overlapping the expansion of the one before
             plan.expand_cov_host(hbuf, reset=True, mean_out=out_mean, C_out=out_C)
 
+        def h2d_rate():
+            # one plain copy of the whole pinned buffer: the host link's rate
+            # at the time (it is shared with other tenants of the machine)
+            dtmp = torch.empty(hbuf.shape, dtype=torch.float32, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dtmp.copy_(hbuf, non_blocking=True)
+            torch.cuda.synchronize()
+            rate = hbuf.numel() * 4 / (time.perf_counter() - t0) / 1e9
+            del dtmp
+            torch.cuda.empty_cache()
+            return rate
+
         for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
+        h2d_before = h2d_rate()
         # host clock around every step (each ends with the covariance on the
         # host); the value is total images / total time over k steps
         k = max(5, args.steps // 2)
@@ -532,7 +546,8 @@ def run_ours(args):
         e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
                "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8), "steps": k,
                "median_step_ms": statistics.median(steps_ms), "max_step_ms": max(steps_ms),
-               "call": "ffb_expand_cov_host (pinned host images -> host mean and covariance)"}
+               "call": "ffb_expand_cov_host (pinned host images -> host mean and covariance)",
+               "h2d_gbs_plain_copy": [round(h2d_before, 1), round(h2d_rate(), 1)]}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
