@@ -7,10 +7,19 @@
 
 #include "ffb_fft.cuh"
 
-// rings per ring-FFT CTA (one warp each): 32, or 8 at n_theta = 1024 where a
-// warp's transpose buffer holds 32 x 32 values
+// rings per ring-FFT CTA (one warp each): 32; 16 at n_theta = 512, where two
+// such CTAs share an SM and their barrier waits overlap (32 rings: one CTA
+// per SM, 18.3 ms per 100k images at L = 128; 16: 16.9 ms; 8: 18.5 ms); 8 at
+// n_theta = 1024, where a warp's transpose buffer holds 32 x 32 values
+#ifndef FFB_RFFT_RB512
+#define FFB_RFFT_RB512 16
+#endif
 template <int NTH>
-constexpr int rfft_rb() { return NTH > 512 ? 8 : 32; }
+constexpr int rfft_rb() { return NTH > 512 ? 8 : (NTH == 512 ? FFB_RFFT_RB512 : 32); }
+// CTAs per SM the register budget aims at (n_theta <= 512: 32 warps per SM
+// at 64 registers, whatever the rings per CTA)
+template <int NTH, int RB>
+constexpr int rfft_minb() { return NTH <= 512 ? 32 / RB : 1; }
 
 // cos / sin (2 pi m / M) for M = 2 .. 32
 template <int M>
@@ -44,7 +53,7 @@ __device__ __forceinline__ float wsin(int m) { return (M <= 16) ? sin16((16 / (M
 // grid (ceil(n_xi / RFFT_RB), nimg), 32 RFFT_RB threads.
 // ---------------------------------------------------------------------------
 template <int NTH, int FMT, int RFFT_RB = rfft_rb<NTH>()>
-__global__ void __launch_bounds__(32 * RFFT_RB, 1)
+__global__ void __launch_bounds__(32 * RFFT_RB, rfft_minb<NTH, RFFT_RB>())
 k_ring_fft(const float2 *__restrict__ Fpol, int n_xi, int kmax, int lead, const float2 *__restrict__ twT,
            const float2 *__restrict__ twA,
            void *__restrict__ out0, void *__restrict__ out1, int ld) {
