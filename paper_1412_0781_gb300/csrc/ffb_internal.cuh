@@ -185,14 +185,15 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // L2 eviction-priority policies for data read once (evict first) and for
 // data a later kernel of the step reads again (evict last), and accesses
 // that carry them
+// (no side effects: not volatile, so that the compiler hoists them out of loops)
 __device__ __forceinline__ unsigned long long l2_evict_first() {
     unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 __device__ __forceinline__ unsigned long long l2_evict_last() {
     unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 __device__ __forceinline__ float ldg_hint(const float *a, unsigned long long pol) {
