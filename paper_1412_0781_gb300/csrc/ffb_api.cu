@@ -92,13 +92,17 @@ int ffb_expand_part(ffb_plan_t p, const float *d_images, int64_t g0, int64_t g1,
     for (int64_t i0 = g0; i0 < g1; i0 += p->chunk) {
         int m = (int)std::min<int64_t>(p->chunk, g1 - i0);
         if (p->fused) {
-            // chunks after the first follow this call's own kernels
-            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0, g1 - (i0 + m)));
+            // chunks after the first follow this call's own kernels; where the
+            // plan takes the tensor-core ring DFT the grid kernel leaves bf16
+            // planes for it
+            const bool tcdft = ffb_tc_dft_ok(p);
+            CK(ffb_launch_fused_polar(p, d_images, i0, m, p->d_Fpol, s, i0 > 0, g1 - (i0 + m), tcdft));
             RingOut r = ring;   // this chunk's images in the group's planes
             const size_t off = (size_t)(i0 - g0) * 2 * ring.ld * es;
             r.p0 = (char *)ring.p0 + off;
             if (ring.p1) r.p1 = (char *)ring.p1 + off;
-            CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
+            if (tcdft) CK(ffb_launch_tc_dft(p, m, r, s));
+            else CK(ffb_launch_ring_fft(p, m, p->d_Fpol, r, s));
         } else if (p->ring_direct) {
             // tiled interpolation into the polar buffer, then the register
             // ring FFT straight into this chunk's quadrature operands

@@ -46,6 +46,8 @@
 // unit, about 3 MB at N = 256, read from L2 by every CTA).  The kernel
 // stages a block's results in shared memory and stores them in natural
 // order.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(FUS_NT, 1)
 k_grid_interp_half(const float *__restrict__ images, int off, const float *__restrict__ corr,
                    const float2 *__restrict__ tw, const float2 *__restrict__ twA, int n_xi, int n_theta, int nq0,
                    const float4 *__restrict__ units, const int2 *__restrict__ blocks, int nblk0, int nblk1,
-                   float2 *__restrict__ Fpol, int *status, int wave, int n_after) {
+                   float2 *__restrict__ Fpol, int *status, int wave, int n_after,
+                   __nv_bfloat16 *__restrict__ planes, long long pstride) {
     constexpr int L = N / 2;
     constexpr int H = (W + 1) / 2;
     constexpr int MH = fus_mh(N, W);              // rows of S (m2 + h)
@@ -515,7 +518,19 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
             const int t = t0 + i;
             const int j = (int)__umulhi((unsigned)t, nl_magic);
             const int l = lbeg + (t - j * nl);
-            Fout[(size_t)j * nh + l] = stage[i];
+            if (planes) {
+                // u and v as bf16 hi / lo planes [hi, lo][u, v][image][ring][l]
+                // (the tensor-core ring DFT's operands)
+                const float2 v = stage[i];
+                const size_t o = ((size_t)img * n_xi + j) * nh + l;
+                const __nv_bfloat16 uh = __float2bfloat16_rn(v.x), vh = __float2bfloat16_rn(v.y);
+                planes[o] = uh;
+                planes[(size_t)pstride + o] = vh;
+                planes[2 * (size_t)pstride + o] = __float2bfloat16_rn(v.x - __bfloat162float(uh));
+                planes[3 * (size_t)pstride + o] = __float2bfloat16_rn(v.y - __bfloat162float(vh));
+            } else {
+                Fout[(size_t)j * nh + l] = stage[i];
+            }
         }
     }
 }
@@ -687,7 +702,7 @@ int ffb_launch_fused_spread(ffb_plan_t p, const float2 *Gpol, int m, float2 *Gex
 // stream is one of this library's and does not write the images)
 template <int N, int W>
 static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
-                        bool pdl, int64_t n_after) {
+                        bool pdl, int64_t n_after, bool planes) {
     static int attr = 0, attr_cl = 0;
     const size_t smem = fused_smem<N, W>();
     const bool cl = p->fused == 2;
@@ -727,7 +742,9 @@ static int launch_fused(ffb_plan_t p, const float *d_images, int64_t i0, int m, 
                                               img, p->off, (const float *)p->d_corr, (const float2 *)p->d_twN,
                                               (const float2 *)p->d_twG, p->n_xi, p->n_theta, p->nq0, (const float4 *)p->d_nodes,
                                               (const int2 *)p->d_node_blk, p->node_nblk[0], p->node_nblk[1], Fpol,
-                                              p->d_status, wave, (int)std::min<int64_t>(n_after, 1 << 20)));
+                                              p->d_status, wave, (int)std::min<int64_t>(n_after, 1 << 20),
+                                              planes ? (__nv_bfloat16 *)Fpol : (__nv_bfloat16 *)nullptr,
+                                              (long long)p->chunk * p->n_xi * (p->n_theta / 2)));
     p->launches++;
     return e;
 }
@@ -1028,8 +1045,9 @@ extern "C" int ffb_interp_units(int N, int w, double beta, int n_xi, int n_theta
 }
 
 int ffb_launch_fused_polar(ffb_plan_t p, const float *d_images, int64_t i0, int m, float2 *Fpol, cudaStream_t s,
-                           bool pdl, int64_t n_after) {
-    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after);
-    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after);
+                           bool pdl, int64_t n_after, bool planes) {
+    if (planes && Fpol != p->d_Fpol) return FFB_ERR_ARG;   // the plane stride is the plan's chunk
+    if (p->N == 256) return launch_fused<256, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after, planes);
+    if (p->N == 128) return launch_fused<128, 8>(p, d_images, i0, m, Fpol, s, pdl, n_after, planes);
     return FFB_ERR_UNSUPPORTED;
 }

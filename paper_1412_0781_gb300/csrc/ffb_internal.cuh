@@ -405,8 +405,10 @@ int ffb_ring_prepare(ffb_plan_t plan, cudaStream_t s);   // ring FFT twiddle tab
 int ffb_launch_fused_spread(ffb_plan_t plan, const float2 *Gpol, int m, float2 *Gext, cudaStream_t s);
 // n_after: images that follow the chunk [i0, i0 + m) in d_images (the
 // kernel prefetches one wave ahead into L2, never past them)
+// planes: write the polar samples as the bf16 hi / lo planes of the
+// tensor-core ring DFT (into the plan's polar buffer) instead of float32
 int ffb_launch_fused_polar(ffb_plan_t plan, const float *d_images, int64_t i0, int m, float2 *Fpol,
-                           cudaStream_t s, bool pdl = false, int64_t n_after = 0);
+                           cudaStream_t s, bool pdl = false, int64_t n_after = 0, bool planes = false);
 struct RingOut {
     int fmt;           // FFB_FMT_*
     void *p0, *p1;     // planes (FFB_FMT_F32: p0 = float32 spectra), at the launch's first image
@@ -416,6 +418,10 @@ struct RingOut {
 int ffb_launch_ring_fft(ffb_plan_t plan, int m, const float2 *Fpol, const RingOut &out, cudaStream_t s);
 int ffb_launch_ring_ifft(ffb_plan_t plan, int m, const float *Yhat, float2 *Gpol, cudaStream_t s);
 int ffb_tc_prepare(ffb_plan_t plan, cudaStream_t s, RingOut *out);
+// ring DFT on the tensor cores (ffb_tc.cu): whether the plan takes it, and
+// one chunk's launch from the bf16 polar planes into the operand planes
+bool ffb_tc_dft_ok(ffb_plan_t plan);
+int ffb_launch_tc_dft(ffb_plan_t plan, int m, const RingOut &out, cudaStream_t s);
 // chunks whose ring spectra one tensor-core quadrature launch takes (>= 1;
 // valid after ffb_tc_prepare)
 int ffb_tc_group(ffb_plan_t plan);

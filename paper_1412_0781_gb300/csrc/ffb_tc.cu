@@ -112,7 +112,11 @@ struct TcStack {
     int P, nimg, nM, NCH;  // coefficients per image, images, M tiles, 128-byte K chunks
     int item0;
     int BN;                // rows of the B map's box (<= the launch's BNmax)
-    int pad_[2];
+    // ring DFT launches (EPI 1): the quadrature's operand planes (hi in coef,
+    // lo here) at the chunk's first image, their image lead and row pitch,
+    // k_max, and the rings per image (the accumulator rows of one M tile)
+    void *out1;
+    int lead, ld, kmax, nring;
 };
 
 // the stack of `item`: the launch's one stack, or, in a group, the last stack
@@ -137,7 +141,7 @@ __device__ __forceinline__ const TcStack *tc_stack_of(const TcStack &one, const 
 // tcgen05.ld into a padded [64 images][BN q][re, im] stage, releases the
 // accumulator (acce) and writes the coefficients as contiguous runs per
 // image.  BNmax and acc_cols cover the widest stack of the launch.
-template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP, int EPI = 0>
 __global__ void __launch_bounds__(32 * TCB_WARPS)
 k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ many, int S, int BNmax, int acc_cols,
             int nst, int nitems, int *status, long long wb) {
@@ -150,7 +154,7 @@ k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ man
     const uint32_t st_bytes = NPA * a_bytes + NPB * b_bytes;   // one stage: every plane of one K chunk
     const int ldst = 2 * BNmax + 2;             // floats per image row of the epilogue stage
     float *stage = (float *)(sm + (size_t)nst * st_bytes);
-    const size_t stage_bytes = ((size_t)64 * ldst * 4 + 15) & ~(size_t)15;
+    const size_t stage_bytes = EPI ? 0 : ((size_t)64 * ldst * 4 + 15) & ~(size_t)15;
     uint64_t *bars = (uint64_t *)(sm + (size_t)nst * st_bytes + stage_bytes);
     uint64_t *full = bars, *empty = bars + nst, *accf = bars + 2 * nst, *acce = bars + 2 * nst + 2;
     uint32_t *slot = (uint32_t *)(bars + 2 * nst + 4);
@@ -287,6 +291,54 @@ k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ man
                 tc::mbar_wait(&accf[it & 1], (uint32_t)((it >> 1) & 1), TC_BUDGET);
             }
         }
+    } else if constexpr (EPI == 1) {                      // ---- ring DFT epilogue
+        // accumulator row = ring j of image m (one image per M tile), column
+        // col = 2 e + c of parity item k: the ring spectrum F_{2e+k}, part c,
+        // written as the quadrature's bf16 hi / lo operand planes
+        // [kk][image][c][j] (32 consecutive rings per warp store)
+        const int q4 = warp & 3;
+        const int cg = (warp - 2) >> 2;
+        const int j = 32 * q4 + lane;
+        int si = 0;
+        for (int it = 0; it < myitems; ++it) {
+            const int item = blockIdx.x + it * gridDim.x;
+            const TcStack *st = tc_stack_of<GROUP>(one, many, S, item, si);
+            const int local = item - st->item0, nM = st->nM;
+            const int k = local / nM, m = local - k * nM;
+            const int BN = st->BN;
+            const int a = it & 1;
+            const bool live = *(volatile int *)okflag != 0;
+            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), live ? wb : 0);
+            if (!ok && live) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+            tc::fence_after_sync();
+            if (ok) {
+                __nv_bfloat16 *o0 = (__nv_bfloat16 *)st->coef, *o1 = (__nv_bfloat16 *)st->out1;
+                const size_t ld = (size_t)st->ld, lead = (size_t)st->lead;
+                for (int c16 = 16 * cg; c16 < BN; c16 += 16 * (TCB_EPI / 4)) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * acc_cols + c16), v);
+                    if (j < st->nring) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int col = c16 + i;
+                            const int kk = 2 * (col >> 1) + k;
+                            if (kk <= st->kmax) {
+                                const size_t idx = (((size_t)kk * lead + m) * 2 + (col & 1)) * ld + j;
+                                const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
+                                o0[idx] = h;
+                                o1[idx] = __float2bfloat16_rn(v[i] - __bfloat162float(h));
+                            }
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[a]);
+        }
     } else {                                              // ---- epilogue warps
         const int q4 = warp & 3;                          // TMEM lanes 32 q4 .. 32 q4 + 31
         const int cg = (warp - 2) >> 2;                   // which column groups of 16
@@ -385,6 +437,11 @@ struct TcState {
     void *bhi = nullptr, *blo = nullptr;   // padded radial tables [k][BN][ld]
     void *ahi = nullptr, *alo = nullptr;   // ring spectra planes [k][2 grp chunk][ld]
     TcStack one;                           // maps and plan fields of this plan's launches
+    // ring DFT on the tensor cores (ffb_tc_dft_*): its tables and stack
+    void *dft_hi = nullptr, *dft_lo = nullptr;
+    int *dft_pk = nullptr;
+    TcStack dft;
+    int dft_ready = 0;
 };
 
 static TcState *tc_state(ffb_plan_t p) {
@@ -395,7 +452,7 @@ static TcState *tc_state(ffb_plan_t p) {
 void ffb_tc_release(ffb_plan_t p) {
     if (!p->tc) return;
     TcState *t = (TcState *)p->tc;
-    void *ptrs[] = {t->bhi, t->blo, t->ahi, t->alo};
+    void *ptrs[] = {t->bhi, t->blo, t->ahi, t->alo, t->dft_hi, t->dft_lo, t->dft_pk};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete t;
@@ -412,9 +469,9 @@ static size_t tc_stage_bytes(int prec, int BN) {
     return (size_t)np * 128 * 128 + (size_t)np * BN * 128;
 }
 
-static size_t tc_smem_bytes(int prec, int BN, int nst) {
+static size_t tc_smem_bytes(int prec, int BN, int nst, int epi = 0) {
     const size_t ring = (size_t)nst * tc_stage_bytes(prec, BN);
-    const size_t stage = ((size_t)64 * (2 * BN + 2) * 4 + 15) & ~(size_t)15;
+    const size_t stage = epi ? 0 : ((size_t)64 * (2 * BN + 2) * 4 + 15) & ~(size_t)15;
     return 1024 + ring + stage + 8 * (2 * (size_t)nst + 4) + 16;
 }
 
@@ -527,17 +584,17 @@ static void tc_launch_shape(int prec, int BN, int *per_sm, int *nst) {
     }
 }
 
-template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP, int EPI = 0>
 static int launch_tc_kernel(int prec, const TcStack &one, const TcStack *many, int S, int nitems, int BNmax,
                             int acc_cols, int per_sm, int nst, int *status, long long wb, cudaStream_t s) {
     if (nst <= 0 || nitems <= 0) return nitems <= 0 ? FFB_OK : FFB_ERR_UNSUPPORTED;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = tc_smem_bytes(prec, BNmax, nst);
+    const size_t smem = tc_smem_bytes(prec, BNmax, nst, EPI);
     static int attr = 0;
     if (attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>,
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP, EPI>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         attr = (int)smem;
@@ -553,8 +610,8 @@ static int launch_tc_kernel(int prec, const TcStack &one, const TcStack *many, i
     cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>, one, many, S, BNmax,
-                                             acc_cols, nst, nitems, status, wb));
+    return ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP, EPI>, one, many, S,
+                                             BNmax, acc_cols, nst, nitems, status, wb));
 }
 
 template <bool GROUP>
@@ -582,6 +639,107 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
     ProfScope ps(p, FFB_KC_BESSEL, s);
     const int e = launch_tc_prec<false>(p->precision, one, nullptr, 1, nitems, t->BN, t->tmem_cols, per_sm, nst,
                                         p->d_status, p->wait_budget, s);
+    p->launches++;
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Ring DFT on the tensor cores (Eq. 1DFFT at n_theta = 512, BF16x3, the
+// shared-memory grid path with 128 rings per image).  With the conjugate
+// completion f_{l + n/2} = conj f_l of a ring, f = u + i v,
+//   F_k = s sum_{l < n/2} e^{-i k theta_l} (f_l + (-1)^k conj f_l),  s = 2 pi / n,
+// i.e. F_k = 2 s sum_l u_l e^{-i k theta_l} for even k and
+// F_k = 2 s sum_l v_l (sin k theta_l + i cos k theta_l) for odd k: two real
+// contractions over l, of the rings' real parts with the even-k table and of
+// their imaginary parts with the odd-k table, 2 (k_max / 2 + 1) <= 192
+// columns (re, im per k) each.  The grid kernel leaves u and v as bf16 hi / lo
+// planes [hi, lo][u, v][image][ring][l] in the polar buffer; the items of a
+// launch are (parity, image), one 128-ring image per M tile, K = 256 in four
+// 128-byte chunks; the epilogue writes F as the quadrature's operand planes.
+// This trades the FFT's 1.5 MFLOP per image for 2 x 3 x 128 x 192 x 256 x 2
+// = 75.5 MFLOP on the tensor cores (measured faster than the register FFT,
+// which is issue-bound).
+// ---------------------------------------------------------------------------
+#define TC_DFT_BN 192
+
+bool ffb_tc_dft_ok(ffb_plan_t p) {
+    return p->fused && p->precision == FFB_BF16X3 && p->n_theta == 512 && p->n_xi == 128 &&
+           2 * (p->k_max / 2 + 1) <= TC_DFT_BN;
+}
+
+int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
+    TcState *t = tc_state(p);
+    if (t->dft_ready) return FFB_OK;
+    if (!ffb_tc_dft_ok(p) || !p->d_Fpol) return FFB_ERR_UNSUPPORTED;
+    const int n = p->n_theta, nh = n / 2, BN = TC_DFT_BN;
+    const double sc = 2.0 * (2.0 * M_PI / (double)n);
+    std::vector<__nv_bfloat16> hi((size_t)2 * BN * nh), lo((size_t)2 * BN * nh);
+    for (int par = 0; par < 2; ++par)
+        for (int col = 0; col < BN; ++col) {
+            const int k = 2 * (col >> 1) + par, c = col & 1;
+            for (int l = 0; l < nh; ++l) {
+                double v = 0.0;
+                if (k <= p->k_max) {
+                    const double a = 2.0 * M_PI * (double)(((long long)k * l) % n) / (double)n;
+                    if (par == 0) v = c ? -sc * std::sin(a) : sc * std::cos(a);
+                    else v = c ? sc * std::cos(a) : sc * std::sin(a);
+                }
+                const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+                const size_t i = ((size_t)par * BN + col) * nh + l;
+                hi[i] = h;
+                lo[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+            }
+        }
+    int e;
+    const size_t tb = sizeof(__nv_bfloat16) * hi.size();
+    if ((e = ffb_check_cuda(cudaMalloc(&t->dft_hi, tb)))) return e;
+    if ((e = ffb_check_cuda(cudaMalloc(&t->dft_lo, tb)))) return e;
+    if ((e = ffb_check_cuda(cudaMalloc((void **)&t->dft_pk, 2 * sizeof(int))))) return e;
+    const int pk2[2] = {BN, BN};
+    if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_hi, hi.data(), tb, cudaMemcpyHostToDevice, s)))) return e;
+    if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_lo, lo.data(), tb, cudaMemcpyHostToDevice, s)))) return e;
+    if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_pk, pk2, sizeof pk2, cudaMemcpyHostToDevice, s)))) return e;
+    if ((e = ffb_check_cuda(cudaStreamSynchronize(s)))) return e;
+    // A: the polar buffer as four bf16 planes of chunk x n_xi rows of nh
+    const uint64_t rows = (uint64_t)p->chunk * p->n_xi;
+    __nv_bfloat16 *pl = (__nv_bfloat16 *)p->d_Fpol;
+    TcStack &d = t->dft;
+    std::memset(&d, 0, sizeof d);
+    if ((e = make_map(&d.mA0, pl, true, nh, rows, 2, 128))) return e;
+    if ((e = make_map(&d.mA1, pl + 2 * rows * nh, true, nh, rows, 2, 128))) return e;
+    if ((e = make_map(&d.mB0, t->dft_hi, true, nh, BN, 2, BN))) return e;
+    if ((e = make_map(&d.mB1, t->dft_lo, true, nh, BN, 2, BN))) return e;
+    d.pk = t->dft_pk;
+    d.NCH = nh * 2 / 128;
+    d.BN = BN;
+    d.kmax = p->k_max;
+    d.nring = p->n_xi;
+    t->dft_ready = 1;
+    return FFB_OK;
+}
+
+// one launch per chunk of m images: F of every ring into the operand planes
+// of the group (r: the chunk's first image in them)
+int ffb_launch_tc_dft(ffb_plan_t p, int m, const RingOut &r, cudaStream_t s) {
+    int e = ffb_tc_dft_prepare(p, s);
+    if (e) return e;
+    TcState *t = tc_state(p);
+    TcStack one = t->dft;
+    one.coef = (float *)r.p0;
+    one.out1 = r.p1;
+    one.lead = r.lead;
+    one.ld = r.ld;
+    one.nimg = m;
+    one.nM = m;
+    one.item0 = 0;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    int nst = 4;
+    while (nst > 0 && tc_smem_bytes(FFB_BF16X3, TC_DFT_BN, nst, 1) > (size_t)optin) --nst;
+    if (nst <= 0) return FFB_ERR_UNSUPPORTED;
+    ProfScope ps(p, FFB_KC_RING_FFT, s);
+    e = launch_tc_kernel<1, 2, 2, 3, false, 1>(FFB_BF16X3, one, nullptr, 1, 2 * m, TC_DFT_BN, 256, 1, nst,
+                                               p->d_status, p->wait_budget, s);
     p->launches++;
     return e;
 }
