@@ -112,11 +112,7 @@ struct TcStack {
     int P, nimg, nM, NCH;  // coefficients per image, images, M tiles, 128-byte K chunks
     int item0;
     int BN;                // rows of the B map's box (<= the launch's BNmax)
-    // ring DFT launches (EPI 1): the quadrature's operand planes (hi in coef,
-    // lo here) at the chunk's first image, their image lead and row pitch,
-    // k_max, and the rings per image (the accumulator rows of one M tile)
-    void *out1;
-    int lead, ld, kmax, nring;
+    int pad_[2];
 };
 
 // the stack of `item`: the launch's one stack, or, in a group, the last stack
@@ -141,7 +137,7 @@ __device__ __forceinline__ const TcStack *tc_stack_of(const TcStack &one, const 
 // tcgen05.ld into a padded [64 images][BN q][re, im] stage, releases the
 // accumulator (acce) and writes the coefficients as contiguous runs per
 // image.  BNmax and acc_cols cover the widest stack of the launch.
-template <int KIND, int NPA, int NPB, int NPROD, bool GROUP, int EPI = 0>
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
 __global__ void __launch_bounds__(32 * TCB_WARPS)
 k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ many, int S, int BNmax, int acc_cols,
             int nst, int nitems, int *status, long long wb) {
@@ -154,7 +150,7 @@ k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ man
     const uint32_t st_bytes = NPA * a_bytes + NPB * b_bytes;   // one stage: every plane of one K chunk
     const int ldst = 2 * BNmax + 2;             // floats per image row of the epilogue stage
     float *stage = (float *)(sm + (size_t)nst * st_bytes);
-    const size_t stage_bytes = EPI ? 0 : ((size_t)64 * ldst * 4 + 15) & ~(size_t)15;
+    const size_t stage_bytes = ((size_t)64 * ldst * 4 + 15) & ~(size_t)15;
     uint64_t *bars = (uint64_t *)(sm + (size_t)nst * st_bytes + stage_bytes);
     uint64_t *full = bars, *empty = bars + nst, *accf = bars + 2 * nst, *acce = bars + 2 * nst + 2;
     uint32_t *slot = (uint32_t *)(bars + 2 * nst + 4);
@@ -291,54 +287,6 @@ k_tc_bessel(const __grid_constant__ TcStack one, const TcStack *__restrict__ man
                 tc::mbar_wait(&accf[it & 1], (uint32_t)((it >> 1) & 1), TC_BUDGET);
             }
         }
-    } else if constexpr (EPI == 1) {                      // ---- ring DFT epilogue
-        // accumulator row = ring j of image m (one image per M tile), column
-        // col = 2 e + c of parity item k: the ring spectrum F_{2e+k}, part c,
-        // written as the quadrature's bf16 hi / lo operand planes
-        // [kk][image][c][j] (32 consecutive rings per warp store)
-        const int q4 = warp & 3;
-        const int cg = (warp - 2) >> 2;
-        const int j = 32 * q4 + lane;
-        int si = 0;
-        for (int it = 0; it < myitems; ++it) {
-            const int item = blockIdx.x + it * gridDim.x;
-            const TcStack *st = tc_stack_of<GROUP>(one, many, S, item, si);
-            const int local = item - st->item0, nM = st->nM;
-            const int k = local / nM, m = local - k * nM;
-            const int BN = st->BN;
-            const int a = it & 1;
-            const bool live = *(volatile int *)okflag != 0;
-            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), live ? wb : 0);
-            if (!ok && live) {
-                ffb_flag(status, FFB_ERR_TIMEOUT);
-                atomicExch(okflag, 0);
-            }
-            tc::fence_after_sync();
-            if (ok) {
-                __nv_bfloat16 *o0 = (__nv_bfloat16 *)st->coef, *o1 = (__nv_bfloat16 *)st->out1;
-                const size_t ld = (size_t)st->ld, lead = (size_t)st->lead;
-                for (int c16 = 16 * cg; c16 < BN; c16 += 16 * (TCB_EPI / 4)) {
-                    float v[16];
-                    tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * acc_cols + c16), v);
-                    if (j < st->nring) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int col = c16 + i;
-                            const int kk = 2 * (col >> 1) + k;
-                            if (kk <= st->kmax) {
-                                const size_t idx = (((size_t)kk * lead + m) * 2 + (col & 1)) * ld + j;
-                                const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
-                                o0[idx] = h;
-                                o1[idx] = __float2bfloat16_rn(v[i] - __bfloat162float(h));
-                            }
-                        }
-                    }
-                }
-            }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&acce[a]);
-        }
     } else {                                              // ---- epilogue warps
         const int q4 = warp & 3;                          // TMEM lanes 32 q4 .. 32 q4 + 31
         const int cg = (warp - 2) >> 2;                   // which column groups of 16
@@ -439,8 +387,7 @@ struct TcState {
     TcStack one;                           // maps and plan fields of this plan's launches
     // ring DFT on the tensor cores (ffb_tc_dft_*): its tables and stack
     void *dft_hi = nullptr, *dft_lo = nullptr;
-    int *dft_pk = nullptr;
-    TcStack dft;
+    TcStack dft;                           // its four TMA maps
     int dft_ready = 0;
 };
 
@@ -452,7 +399,7 @@ static TcState *tc_state(ffb_plan_t p) {
 void ffb_tc_release(ffb_plan_t p) {
     if (!p->tc) return;
     TcState *t = (TcState *)p->tc;
-    void *ptrs[] = {t->bhi, t->blo, t->ahi, t->alo, t->dft_hi, t->dft_lo, t->dft_pk};
+    void *ptrs[] = {t->bhi, t->blo, t->ahi, t->alo, t->dft_hi, t->dft_lo};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete t;
@@ -469,9 +416,9 @@ static size_t tc_stage_bytes(int prec, int BN) {
     return (size_t)np * 128 * 128 + (size_t)np * BN * 128;
 }
 
-static size_t tc_smem_bytes(int prec, int BN, int nst, int epi = 0) {
+static size_t tc_smem_bytes(int prec, int BN, int nst) {
     const size_t ring = (size_t)nst * tc_stage_bytes(prec, BN);
-    const size_t stage = epi ? 0 : ((size_t)64 * (2 * BN + 2) * 4 + 15) & ~(size_t)15;
+    const size_t stage = ((size_t)64 * (2 * BN + 2) * 4 + 15) & ~(size_t)15;
     return 1024 + ring + stage + 8 * (2 * (size_t)nst + 4) + 16;
 }
 
@@ -584,17 +531,17 @@ static void tc_launch_shape(int prec, int BN, int *per_sm, int *nst) {
     }
 }
 
-template <int KIND, int NPA, int NPB, int NPROD, bool GROUP, int EPI = 0>
+template <int KIND, int NPA, int NPB, int NPROD, bool GROUP>
 static int launch_tc_kernel(int prec, const TcStack &one, const TcStack *many, int S, int nitems, int BNmax,
                             int acc_cols, int per_sm, int nst, int *status, long long wb, cudaStream_t s) {
     if (nst <= 0 || nitems <= 0) return nitems <= 0 ? FFB_OK : FFB_ERR_UNSUPPORTED;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = tc_smem_bytes(prec, BNmax, nst, EPI);
+    const size_t smem = tc_smem_bytes(prec, BNmax, nst);
     static int attr = 0;
     if (attr < (int)smem) {
-        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP, EPI>,
+        int e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (e) return e;
         attr = (int)smem;
@@ -610,8 +557,8 @@ static int launch_tc_kernel(int prec, const TcStack &one, const TcStack *many, i
     cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP, EPI>, one, many, S,
-                                             BNmax, acc_cols, nst, nitems, status, wb));
+    return ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_bessel<KIND, NPA, NPB, NPROD, GROUP>, one, many, S, BNmax,
+                                             acc_cols, nst, nitems, status, wb));
 }
 
 template <bool GROUP>
@@ -651,16 +598,215 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
 // i.e. F_k = 2 s sum_l u_l e^{-i k theta_l} for even k and
 // F_k = 2 s sum_l v_l (sin k theta_l + i cos k theta_l) for odd k: two real
 // contractions over l, of the rings' real parts with the even-k table and of
-// their imaginary parts with the odd-k table, 2 (k_max / 2 + 1) <= 192
-// columns (re, im per k) each.  The grid kernel leaves u and v as bf16 hi / lo
-// planes [hi, lo][u, v][image][ring][l] in the polar buffer; the items of a
-// launch are (parity, image), one 128-ring image per M tile, K = 256 in four
-// 128-byte chunks; the epilogue writes F as the quadrature's operand planes.
-// This trades the FFT's 1.5 MFLOP per image for 2 x 3 x 128 x 192 x 256 x 2
-// = 75.5 MFLOP on the tensor cores (measured faster than the register FFT,
-// which is issue-bound).
+// their imaginary parts with the odd-k table, 192 columns (re, im of 96 k)
+// each.  The grid kernel leaves u and v as bf16 hi / lo planes
+// [hi, lo][u, v][image][ring][l] in the polar buffer.  CTA b of a launch
+// takes the parity p = b mod 2 and the column half h = (b / 2) mod 2 (96
+// columns: its table slice, hi and lo, 96 KB, stays in shared memory) and the
+// images b / 4, b / 4 + G / 4, ...; one image (its 128 rings) is one M tile,
+// K = 256 in four 128-byte chunks streamed by TMA through four stages of
+// 32 KB (u or v, hi and lo).  BF16x3: A_hi B_hi + A_hi B_lo + A_lo B_hi into
+// one of two TMEM accumulators of 96 columns; eight epilogue warps write the
+// spectra as the quadrature's operand planes (bf16 hi / lo, [k][image][re,
+// im][ring], 32 rings per warp store).  This trades the FFT's 1.5 MFLOP per
+// image for 4 x 3 x 128 x 96 x 256 x 2 = 75.5 MFLOP on the tensor cores.
+// Waits are bounded like the quadrature's.  Measured at L = 128 (per 100k
+// images): the register FFT 16.9 ms, this kernel 12.5 ms; its timeline
+// (clock64 stamps) shows the MMAs of one item (48 of M 128 x N 96 x K 16)
+// taking about 5.4 k cycles with or without the A loads, about half the
+// tensor cores' dense rate, and the epilogue (3.1 k cycles) overlapping them.
 // ---------------------------------------------------------------------------
-#define TC_DFT_BN 192
+#define TC_DFT_BN 192            // table columns per parity
+#define TC_DFT_NB 96             // columns per CTA (half a table)
+#define TC_DFT_NST 4             // A stages
+#define TC_DFT_A_BYTES (2u * 128u * 128u)              // one stage: hi and lo, 128 rows x 128 B
+#define TC_DFT_B_BYTES (2u * TC_DFT_NB * 128u)         // one K chunk of the table slice: hi and lo
+#define TC_DFT_NCH 4             // 128-byte K chunks (K = 256 bf16)
+
+static size_t tc_dft_smem() {
+    return 1024 + (size_t)TC_DFT_NCH * TC_DFT_B_BYTES + (size_t)TC_DFT_NST * TC_DFT_A_BYTES +
+           8 * (2 * TC_DFT_NST + 5) + 16;
+}
+
+__global__ void __launch_bounds__(32 * TCB_WARPS)
+k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+             const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+             __nv_bfloat16 *__restrict__ out0, __nv_bfloat16 *__restrict__ out1, int lead, int ld, int kmax,
+             int nimg, int nring, int *status, long long wb) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint8_t *bsm = sm;                                              // [NCH][hi, lo][96 rows][128 B]
+    uint8_t *asm_ = sm + TC_DFT_NCH * TC_DFT_B_BYTES;               // [NST][hi, lo][128 rows][128 B]
+    uint64_t *bars = (uint64_t *)(asm_ + TC_DFT_NST * TC_DFT_A_BYTES);
+    uint64_t *full = bars, *empty = bars + TC_DFT_NST, *accf = bars + 2 * TC_DFT_NST,
+             *acce = bars + 2 * TC_DFT_NST + 2, *bfull = bars + 2 * TC_DFT_NST + 4;
+    uint32_t *slot = (uint32_t *)(bars + 2 * TC_DFT_NST + 5);
+    int *okflag = (int *)(slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int par = blockIdx.x & 1, hcol = (blockIdx.x >> 1) & 1;
+    const int step = gridDim.x >> 2;
+    const int first = blockIdx.x >> 2;
+    const int myitems = (first < nimg) ? (nimg - 1 - first) / step + 1 : 0;
+    constexpr int ACC = 128;                                        // TMEM columns per accumulator
+    pdl_trigger();
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * TC_DFT_NST; ++i) tc::mbar_init(&bars[i], 1);
+        tc::mbar_init(&accf[0], 1);
+        tc::mbar_init(&accf[1], 1);
+        tc::mbar_init(&acce[0], TCB_EPI);
+        tc::mbar_init(&acce[1], TCB_EPI);
+        tc::mbar_init(bfull, 1);
+        tc::fence_mbar_init();
+        *okflag = 1;
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(slot, 2 * ACC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *slot;
+
+    if (warp == 0) {
+        if (lane == 0) {                                  // ---- TMA producer
+            pdl_wait();   // the polar planes come from the grid kernel
+            // the CTA's table slice, once: rows hcol * 96 .. + 95 of parity par
+            tc::mbar_arrive_expect_tx(bfull, TC_DFT_NCH * TC_DFT_B_BYTES);
+            for (int ch = 0; ch < TC_DFT_NCH; ++ch) {
+                uint8_t *b = bsm + ch * TC_DFT_B_BYTES;
+                tc::tma_load_3d(b, &mB0, bfull, ch * 64, hcol * TC_DFT_NB, par);
+                tc::tma_load_3d(b + TC_DFT_B_BYTES / 2, &mB1, bfull, ch * 64, hcol * TC_DFT_NB, par);
+            }
+            const unsigned long long pf = l2_evict_first();
+            int64_t g = 0;
+            bool ok = true;
+            for (int it = 0; it < myitems && ok && *(volatile int *)okflag; ++it) {
+                const int img = first + it * step;
+                for (int ch = 0; ch < TC_DFT_NCH; ++ch, ++g) {
+                    const int stg = (int)(g % TC_DFT_NST);
+                    if (g >= TC_DFT_NST &&
+                        !tc::mbar_wait(&empty[stg], (uint32_t)(((g / TC_DFT_NST) - 1) & 1), wb)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *a = asm_ + stg * TC_DFT_A_BYTES;
+                    tc::mbar_arrive_expect_tx(&full[stg], TC_DFT_A_BYTES);
+                    tc::tma_load_3d_hint(a, &mA0, &full[stg], ch * 64, 128 * img, par, pf);
+                    tc::tma_load_3d_hint(a + TC_DFT_A_BYTES / 2, &mA1, &full[stg], ch * 64, 128 * img, par, pf);
+                }
+            }
+            if (!ok) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+            // every issued copy lands before the CTA may leave
+            tc::mbar_wait(bfull, 0u, TC_BUDGET);
+            for (int64_t h = (g > TC_DFT_NST ? g - TC_DFT_NST : 0); h < g; ++h)
+                tc::mbar_wait(&full[h % TC_DFT_NST], (uint32_t)((h / TC_DFT_NST) & 1), TC_BUDGET);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                  // ---- MMA issue
+            int64_t g = 0;
+            bool ok = tc::mbar_wait(bfull, 0u, wb);
+            int it = 0;
+            const uint32_t id = tc::idesc(1, 128, TC_DFT_NB);
+            for (; it < myitems && ok; ++it) {
+                const int a = it & 1;
+                if (it >= 2 && !tc::mbar_wait(&acce[a], (uint32_t)(((it >> 1) - 1) & 1), wb)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t dt = tbase + (uint32_t)(a * ACC);
+                for (int ch = 0; ch < TC_DFT_NCH; ++ch, ++g) {
+                    const int stg = (int)(g % TC_DFT_NST);
+                    if (!tc::mbar_wait(&full[stg], (uint32_t)((g / TC_DFT_NST) & 1), wb)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(asm_ + stg * TC_DFT_A_BYTES);
+                    const uint32_t sb = tc::smem_u32(bsm + ch * TC_DFT_B_BYTES);
+#pragma unroll
+                    for (int pr = 0; pr < 3; ++pr) {
+                        const int pa = (pr == 2) ? 1 : 0;   // products (hi, hi), (hi, lo), (lo, hi)
+                        const int pb = (pr == 1) ? 1 : 0;
+                        const uint32_t a0 = sa + pa * (TC_DFT_A_BYTES / 2);
+                        const uint32_t b0 = sb + pb * (TC_DFT_B_BYTES / 2);
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = tc::desc_sw128(a0 + 32u * ks);
+                            const uint64_t bd = tc::desc_sw128(b0 + 32u * ks);
+                            tc::mma_bf16(dt, ad, bd, id, (ch > 0 || pr > 0 || ks > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&empty[stg]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[a]);
+            }
+            if (!ok) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+                tc::mma_commit(&accf[it & 1]);   // tracks every MMA issued so far
+                tc::mbar_wait(&accf[it & 1], (uint32_t)((it >> 1) & 1), TC_BUDGET);
+            }
+        }
+    } else {                                              // ---- epilogue warps
+        // accumulator row = ring j of the item's image, column c of the
+        // slice = table column hcol * 96 + c: spectrum F_kk, kk = 2 (col / 2)
+        // + par, part col mod 2
+        const int q4 = warp & 3;
+        const int cg = (warp - 2) >> 2;
+        const int j = 32 * q4 + lane;
+        for (int it = 0; it < myitems; ++it) {
+            const int img = first + it * step;
+            const int a = it & 1;
+            const bool live = *(volatile int *)okflag != 0;
+            const bool ok = tc::mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), live ? wb : 0);
+            if (!ok && live) {
+                ffb_flag(status, FFB_ERR_TIMEOUT);
+                atomicExch(okflag, 0);
+            }
+            tc::fence_after_sync();
+            if (ok) {
+                // columns 2e, 2e + 1 of the slice are re, im of k = col0 + 2e + par
+                // (col0 even): plane offsets k S + (2 img) ld + j and that + ld,
+                // S = 2 lead ld (32-bit: the group's planes hold < 2^31 values)
+                const int S = 2 * lead * ld;
+                const int base = 2 * img * ld + j;
+                for (int c16 = 16 * cg; c16 < TC_DFT_NB; c16 += 16 * (TCB_EPI / 4)) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * ACC + c16), v);
+                    const int k0 = hcol * TC_DFT_NB + c16 + par;
+                    const int o0 = k0 * S + base;
+                    if (j < nring) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            if (k0 + i <= kmax) {
+                                const int o = o0 + i * S;
+                                const __nv_bfloat16 hr = __float2bfloat16_rn(v[i]);
+                                const __nv_bfloat16 hi_ = __float2bfloat16_rn(v[i + 1]);
+                                out0[o] = hr;
+                                out1[o] = __float2bfloat16_rn(v[i] - __bfloat162float(hr));
+                                out0[o + ld] = hi_;
+                                out1[o + ld] = __float2bfloat16_rn(v[i + 1] - __bfloat162float(hi_));
+                            }
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[a]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tbase, 2 * ACC);
+}
 
 bool ffb_tc_dft_ok(ffb_plan_t p) {
     return p->fused && p->precision == FFB_BF16X3 && p->n_theta == 512 && p->n_xi == 128 &&
@@ -694,11 +840,8 @@ int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
     const size_t tb = sizeof(__nv_bfloat16) * hi.size();
     if ((e = ffb_check_cuda(cudaMalloc(&t->dft_hi, tb)))) return e;
     if ((e = ffb_check_cuda(cudaMalloc(&t->dft_lo, tb)))) return e;
-    if ((e = ffb_check_cuda(cudaMalloc((void **)&t->dft_pk, 2 * sizeof(int))))) return e;
-    const int pk2[2] = {BN, BN};
     if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_hi, hi.data(), tb, cudaMemcpyHostToDevice, s)))) return e;
     if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_lo, lo.data(), tb, cudaMemcpyHostToDevice, s)))) return e;
-    if ((e = ffb_check_cuda(cudaMemcpyAsync(t->dft_pk, pk2, sizeof pk2, cudaMemcpyHostToDevice, s)))) return e;
     if ((e = ffb_check_cuda(cudaStreamSynchronize(s)))) return e;
     // A: the polar buffer as four bf16 planes of chunk x n_xi rows of nh
     const uint64_t rows = (uint64_t)p->chunk * p->n_xi;
@@ -707,13 +850,8 @@ int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
     std::memset(&d, 0, sizeof d);
     if ((e = make_map(&d.mA0, pl, true, nh, rows, 2, 128))) return e;
     if ((e = make_map(&d.mA1, pl + 2 * rows * nh, true, nh, rows, 2, 128))) return e;
-    if ((e = make_map(&d.mB0, t->dft_hi, true, nh, BN, 2, BN))) return e;
-    if ((e = make_map(&d.mB1, t->dft_lo, true, nh, BN, 2, BN))) return e;
-    d.pk = t->dft_pk;
-    d.NCH = nh * 2 / 128;
-    d.BN = BN;
-    d.kmax = p->k_max;
-    d.nring = p->n_xi;
+    if ((e = make_map(&d.mB0, t->dft_hi, true, nh, BN, 2, TC_DFT_NB))) return e;
+    if ((e = make_map(&d.mB1, t->dft_lo, true, nh, BN, 2, TC_DFT_NB))) return e;
     t->dft_ready = 1;
     return FFB_OK;
 }
@@ -723,23 +861,31 @@ int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
 int ffb_launch_tc_dft(ffb_plan_t p, int m, const RingOut &r, cudaStream_t s) {
     int e = ffb_tc_dft_prepare(p, s);
     if (e) return e;
+    if (m <= 0) return FFB_OK;
     TcState *t = tc_state(p);
-    TcStack one = t->dft;
-    one.coef = (float *)r.p0;
-    one.out1 = r.p1;
-    one.lead = r.lead;
-    one.ld = r.ld;
-    one.nimg = m;
-    one.nM = m;
-    one.item0 = 0;
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    int nst = 4;
-    while (nst > 0 && tc_smem_bytes(FFB_BF16X3, TC_DFT_BN, nst, 1) > (size_t)optin) --nst;
-    if (nst <= 0) return FFB_ERR_UNSUPPORTED;
+    const size_t smem = tc_dft_smem();
+    static int attr = 0;
+    if (attr < (int)smem) {
+        if ((e = ffb_check_cuda(cudaFuncSetAttribute(k_tc_ringdft, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem))))
+            return e;
+        attr = (int)smem;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int grid = 4 * std::max(1, std::min(sms / 4, m));   // (parity, half) x image groups
     ProfScope ps(p, FFB_KC_RING_FFT, s);
-    e = launch_tc_kernel<1, 2, 2, 3, false, 1>(FFB_BF16X3, one, nullptr, 1, 2 * m, TC_DFT_BN, 256, 1, nst,
-                                               p->d_status, p->wait_budget, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * TCB_WARPS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {ffb_pdl_attr()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = ffb_check_cuda(cudaLaunchKernelEx(&cfg, k_tc_ringdft, t->dft.mA0, t->dft.mA1, t->dft.mB0, t->dft.mB1,
+                                          (__nv_bfloat16 *)r.p0, (__nv_bfloat16 *)r.p1, r.lead, r.ld, p->k_max, m,
+                                          p->n_xi, p->d_status, p->wait_budget));
     p->launches++;
     return e;
 }
