@@ -145,6 +145,15 @@ def executed_flops(plan):
             "ring_fft": n_xi * 5 * nth * math.log2(nth)}
 
 
+def tc_ring_dft(plan, precision):
+    """Whether the plan's ring DFT runs as the dense tensor-core contraction
+    (BF16x3, shared-memory grid path, n_theta = 512, 128 rings), and its
+    executed flops per image: two parities x three products x 128 rings x
+    192 table columns x 256 samples x 2."""
+    on = precision == "bf16x3" and plan.polar_variant > 0 and plan.n_theta == 512 and plan.n_xi == 128
+    return on, (2 * 3 * plan.n_xi * 192 * (plan.n_theta // 2) * 2 if on else 0)
+
+
 PROF_STRIDE = 32   # kernel timing: every 32nd launch of each kernel class
 POST_N = 20000     # images for the a8-a10 timings after the step
 
@@ -171,8 +180,8 @@ def hbm_floor(plan):
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu:^k_grid_interp_half",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "35f496769f5c561136bcd7a33ce1e037d7159e0a9cceb69c5eac28400644be0d",
-                    "bytes_per_launch": 17964288 + 46336, "images_per_launch": 152},
+                    "sha256": "7261d4a0e7c2e883d58606534a99e9fbf3ea8c50966a70fc17a513a301083209",
+                    "bytes_per_launch": 17974784 + 54528, "images_per_launch": 152},
 }
 
 
@@ -434,10 +443,12 @@ def run_ours(args):
 
     # the whole step against its floor: the FP32-ALU work of a1-a4 at the
     # FFMA peak (the tensor-core and HBM floors are far higher)
-    alu_flops = flops["grid_interp"] + flops["ring_fft"]
+    tc_ring, _ = tc_ring_dft(plan, head)
+    alu_flops = flops["grid_interp"] + (0.0 if tc_ring else flops["ring_fft"])
     floor = peak * 1e12 / alu_flops
     roofline["step"] = {"bound": "alu", "floor_images_per_s": floor, "frac": value / floor,
-                        "note": "a1-a4 FP32 work %.2f MFLOP/image at the FFMA peak; HBM floor %.1f M images/s" % (
+                        "note": "%s FP32 work %.2f MFLOP/image at the FFMA peak; HBM floor %.1f M images/s" % (
+                            "a1-a3 (the ring DFT runs on the tensor cores)" if tc_ring else "a1-a4",
                             alu_flops / 1e6, hbm_floor(plan) / 1e6)}
 
     # a8-a10 after the timed step (reported beside the metric, not part of
@@ -571,7 +582,15 @@ def run_ours(args):
             continue
         rate = flops[c] * n * args.steps / (ms_c / 1e3) / 1e12
         contraction = c in ("bessel", "covariance")
-        if contraction and tc_peak:
+        tc_ring, ring_exec = tc_ring_dft(plan, head)
+        if c == "ring_fft" and tc_ring and tc_peak:
+            exe_rate = ring_exec * n * args.steps / (ms_c / 1e3) / 1e12
+            stages[c] = {"bound": "tensor", "achieved": rate, "executed": exe_rate, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": exe_rate / tc_peak, "peak_note": tc_note,
+                         "ms_per_step": ms_c / args.steps,
+                         "note": "dense ring DFT on the tensor cores, %.1f MFLOP/image executed (BF16x3); "
+                                 "achieved counts the FFT's %.2f MFLOP/image" % (ring_exec / 1e6, flops[c] / 1e6)}
+        elif contraction and tc_peak:
             products = 3 if head in ("bf16x3", "tf32x3") else 1
             stages[c] = {"bound": "tensor", "achieved": rate, "executed": rate * products, "peak": tc_peak,
                          "unit": "TFLOP/s", "frac": rate * products / tc_peak, "peak_note": tc_note,
