@@ -257,6 +257,18 @@ int ffb_cov_export(ffb_plan_t plan, double *h_state, void *stream);
 int ffb_cov_merge(int k_max, const int *h_p, int nstates, const double *h_states, double *h_out);
 int ffb_cov_import(ffb_plan_t plan, const double *h_state, void *stream);
 
+/* ffb_ringdft_table -- host only: the tables of the ring DFT that runs on the
+ * tensor cores (Eq. 1DFFT at n_theta = 512 with BF16x3), as float copies of
+ * their bf16 hi and lo parts: [parity p][192 columns][n_theta/2], column
+ * 2e + c (c = 0 real, 1 imaginary part) of k = 2e + p, zero for k > k_max.
+ * With the ring's conjugate completion and samples f_l = u_l + i v_l
+ * (l < n_theta/2), F_k = sum_l T[p=0][2e+c][l] u_l (even k) or
+ * sum_l T[p=1][2e+c][l] v_l (odd k), T = hi + lo, which includes the
+ * 2 pi / n_theta weight and the factor 2 of the completion.  h_hi, h_lo:
+ * 2 x 192 x n_theta/2 floats each (either may be NULL).  Returns
+ * FFB_ERR_UNSUPPORTED for odd n_theta or k_max >= 192. */
+int ffb_ringdft_table(int n_theta, int k_max, float *h_hi, float *h_lo);
+
 /* ffb_expand_cov_host -- Alg. 1 steps 3-4 and the accumulation of Alg. 2
  * steps 1-4 for n images held in HOST memory, with the statistics returned
  * to host memory: the end-to-end call of a user whose image stack sits in

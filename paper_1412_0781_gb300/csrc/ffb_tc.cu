@@ -813,30 +813,50 @@ bool ffb_tc_dft_ok(ffb_plan_t p) {
            2 * (p->k_max / 2 + 1) <= TC_DFT_BN;
 }
 
-int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
-    TcState *t = tc_state(p);
-    if (t->dft_ready) return FFB_OK;
-    if (!ffb_tc_dft_ok(p) || !p->d_Fpol) return FFB_ERR_UNSUPPORTED;
-    const int n = p->n_theta, nh = n / 2, BN = TC_DFT_BN;
+// the ring DFT's tables [parity][192 columns][n/2] as bf16 hi / lo: column
+// 2e + c of parity p is part c (re, im) of k = 2e + p; zero for k > k_max
+static int tc_dft_table(int n, int kmax, std::vector<__nv_bfloat16> &hi, std::vector<__nv_bfloat16> &lo) {
+    if (n < 4 || (n & 1) || kmax < 0 || 2 * (kmax / 2 + 1) > TC_DFT_BN) return FFB_ERR_UNSUPPORTED;
+    const int nh = n / 2, BN = TC_DFT_BN;
     const double sc = 2.0 * (2.0 * M_PI / (double)n);
-    std::vector<__nv_bfloat16> hi((size_t)2 * BN * nh), lo((size_t)2 * BN * nh);
+    hi.assign((size_t)2 * BN * nh, __float2bfloat16_rn(0.f));
+    lo.assign((size_t)2 * BN * nh, __float2bfloat16_rn(0.f));
     for (int par = 0; par < 2; ++par)
         for (int col = 0; col < BN; ++col) {
             const int k = 2 * (col >> 1) + par, c = col & 1;
+            if (k > kmax) continue;
             for (int l = 0; l < nh; ++l) {
-                double v = 0.0;
-                if (k <= p->k_max) {
-                    const double a = 2.0 * M_PI * (double)(((long long)k * l) % n) / (double)n;
-                    if (par == 0) v = c ? -sc * std::sin(a) : sc * std::cos(a);
-                    else v = c ? sc * std::cos(a) : sc * std::sin(a);
-                }
+                const double a = 2.0 * M_PI * (double)(((long long)k * l) % n) / (double)n;
+                const double v = (par == 0) ? (c ? -sc * std::sin(a) : sc * std::cos(a))
+                                            : (c ? sc * std::cos(a) : sc * std::sin(a));
                 const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
                 const size_t i = ((size_t)par * BN + col) * nh + l;
                 hi[i] = h;
                 lo[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
             }
         }
-    int e;
+    return FFB_OK;
+}
+
+extern "C" int ffb_ringdft_table(int n_theta, int k_max, float *h_hi, float *h_lo) {
+    std::vector<__nv_bfloat16> hi, lo;
+    const int e = tc_dft_table(n_theta, k_max, hi, lo);
+    if (e) return e;
+    for (size_t i = 0; i < hi.size(); ++i) {
+        if (h_hi) h_hi[i] = __bfloat162float(hi[i]);
+        if (h_lo) h_lo[i] = __bfloat162float(lo[i]);
+    }
+    return FFB_OK;
+}
+
+int ffb_tc_dft_prepare(ffb_plan_t p, cudaStream_t s) {
+    TcState *t = tc_state(p);
+    if (t->dft_ready) return FFB_OK;
+    if (!ffb_tc_dft_ok(p) || !p->d_Fpol) return FFB_ERR_UNSUPPORTED;
+    const int n = p->n_theta, nh = n / 2, BN = TC_DFT_BN;
+    std::vector<__nv_bfloat16> hi, lo;
+    int e = tc_dft_table(n, p->k_max, hi, lo);
+    if (e) return e;
     const size_t tb = sizeof(__nv_bfloat16) * hi.size();
     if ((e = ffb_check_cuda(cudaMalloc(&t->dft_hi, tb)))) return e;
     if ((e = ffb_check_cuda(cudaMalloc(&t->dft_lo, tb)))) return e;

@@ -39,6 +39,7 @@ SIGNATURES = {
     "ffb_covariance": (_i, [_vp, _vp, _i64, _i, _vp]),
     "ffb_cov_get": (_i, [_vp, _vp, _vp, _vp]),
     "ffb_expand_cov_host": (_i, [_vp, _vp, _i64, _i, _vp, _vp, _vp]),
+    "ffb_ringdft_table": (_i, [_i, _i, _vp, _vp]),
     "ffb_cov_export": (_i, [_vp, _pd, _vp]),
     "ffb_cov_merge": (_i, [_i, _pi, _i, _pd, _pd]),
     "ffb_cov_import": (_i, [_vp, _pd, _vp]),
@@ -108,6 +109,17 @@ def interp_units(N, w, beta, n_theta, xi):
     gu = int(cnt[4])
     return (rec.reshape(int(cnt[1]), int(cnt[7]), gu, 4), blk.reshape(-1, 2), (int(cnt[2]), int(cnt[3])),
             int(cnt[5]), int(cnt[6]), int(cnt[8]))
+
+
+def ringdft_table(n_theta, k_max):
+    """Host-only: the tensor-core ring DFT's tables (see ffb_ringdft_table):
+    (hi, lo) float32 arrays of shape (2, 192, n_theta/2)."""
+    import numpy as np
+    hi = np.zeros((2, 192, n_theta // 2), dtype=np.float32)
+    lo = np.zeros_like(hi)
+    _check(load().ffb_ringdft_table(int(n_theta), int(k_max), hi.ctypes.data_as(ctypes.c_void_p),
+                                    lo.ctypes.data_as(ctypes.c_void_p)), "ffb_ringdft_table")
+    return hi, lo
 
 
 def tile_units(N, w, beta, n_theta, xi):
