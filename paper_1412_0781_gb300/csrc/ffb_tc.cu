@@ -601,30 +601,41 @@ static int launch_tc(ffb_plan_t p, TcState *t, int nimg, float *d_coef_chunk, cu
 // their imaginary parts with the odd-k table, 192 columns (re, im of 96 k)
 // each.  The grid kernel leaves u and v as bf16 hi / lo planes
 // [hi, lo][u, v][image][ring][l] in the polar buffer.  CTA b of a launch
-// takes the parity p = b mod 2 and the column half h = (b / 2) mod 2 (96
-// columns: its table slice, hi and lo, 96 KB, stays in shared memory) and the
-// images b / 4, b / 4 + G / 4, ...; one image (its 128 rings) is one M tile,
-// K = 256 in four 128-byte chunks streamed by TMA through four stages of
-// 32 KB (u or v, hi and lo).  BF16x3: A_hi B_hi + A_hi B_lo + A_lo B_hi into
-// one of two TMEM accumulators of 96 columns; eight epilogue warps write the
-// spectra as the quadrature's operand planes (bf16 hi / lo, [k][image][re,
-// im][ring], 32 rings per warp store).  This trades the FFT's 1.5 MFLOP per
-// image for 4 x 3 x 128 x 96 x 256 x 2 = 75.5 MFLOP on the tensor cores.
+// takes the parity p = b mod 2 (with 96-column slices also the half
+// (b / 2) mod 2, its slice resident in shared memory) and the images
+// b / NGRP, b / NGRP + G / NGRP, ...; one image (its 128 rings) is one M
+// tile, K = 256 in four 128-byte chunks streamed by TMA (with the table's
+// chunk beside it when it streams).  BF16x3: A_hi B_hi + A_hi B_lo + A_lo B_hi
+// into one of two TMEM accumulators; eight epilogue warps write the spectra
+// as the quadrature's operand planes (bf16 hi / lo, [k][image][re, im][ring],
+// 32 rings per warp store).  This trades the FFT's 1.5 MFLOP per image for
+// 2 x 3 x 128 x 192 x 256 x 2 = 75.5 MFLOP on the tensor cores.
 // Waits are bounded like the quadrature's.  Measured at L = 128 (per 100k
-// images): the register FFT 16.9 ms, this kernel 12.5 ms; its timeline
-// (clock64 stamps) shows the MMAs of one item (48 of M 128 x N 96 x K 16)
-// taking about 5.4 k cycles with or without the A loads, about half the
-// tensor cores' dense rate, and the epilogue (3.1 k cycles) overlapping them.
+// images): the register FFT 16.9 ms, this kernel 12.5 ms with resident
+// 96-column slices and 12.0 ms with the streamed 192-column table; the
+// timeline of the 96-column form (clock64 stamps) shows one image's 48 MMAs
+// (M 128 x N 96 x K 16) taking about 5.4 k cycles with or without the ring
+// loads, about half the tensor cores' dense rate, the epilogue (3.1 k
+// cycles) overlapping them.
 // ---------------------------------------------------------------------------
 #define TC_DFT_BN 192            // table columns per parity
-#define TC_DFT_NB 96             // columns per CTA (half a table)
-#define TC_DFT_NST 4             // A stages
-#define TC_DFT_A_BYTES (2u * 128u * 128u)              // one stage: hi and lo, 128 rows x 128 B
+// columns per CTA: all 192, the table streamed beside the rings through two
+// 80 KB stages (48 MMAs of N = 192 per image and parity), or 96, half a
+// table kept in shared memory and the rings through four 32 KB stages
+// (measured per 100k images at L = 128: 12.0 ms and 12.5 ms)
+#ifndef TC_DFT_NB
+#define TC_DFT_NB 192
+#endif
+#define TC_DFT_RES (TC_DFT_NB < TC_DFT_BN)                // the CTA's table slice stays in shared memory
+#define TC_DFT_NGRP (2 * TC_DFT_BN / TC_DFT_NB)           // CTAs per image: parities x column slices
+#define TC_DFT_NST (TC_DFT_RES ? 4 : 2)                   // pipeline stages
+#define TC_DFT_A_BYTES (2u * 128u * 128u)              // one K chunk of an image's rings: hi and lo, 128 rows x 128 B
 #define TC_DFT_B_BYTES (2u * TC_DFT_NB * 128u)         // one K chunk of the table slice: hi and lo
+#define TC_DFT_STAGE (TC_DFT_A_BYTES + (TC_DFT_RES ? 0u : TC_DFT_B_BYTES))
 #define TC_DFT_NCH 4             // 128-byte K chunks (K = 256 bf16)
 
 static size_t tc_dft_smem() {
-    return 1024 + (size_t)TC_DFT_NCH * TC_DFT_B_BYTES + (size_t)TC_DFT_NST * TC_DFT_A_BYTES +
+    return 1024 + (TC_DFT_RES ? (size_t)TC_DFT_NCH * TC_DFT_B_BYTES : 0) + (size_t)TC_DFT_NST * TC_DFT_STAGE +
            8 * (2 * TC_DFT_NST + 5) + 16;
 }
 
@@ -636,18 +647,18 @@ k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CU
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *bsm = sm;                                              // [NCH][hi, lo][96 rows][128 B]
-    uint8_t *asm_ = sm + TC_DFT_NCH * TC_DFT_B_BYTES;               // [NST][hi, lo][128 rows][128 B]
-    uint64_t *bars = (uint64_t *)(asm_ + TC_DFT_NST * TC_DFT_A_BYTES);
+    uint8_t *asm_ = sm + (TC_DFT_RES ? TC_DFT_NCH * TC_DFT_B_BYTES : 0);   // [NST] stages
+    uint64_t *bars = (uint64_t *)(asm_ + TC_DFT_NST * TC_DFT_STAGE);
     uint64_t *full = bars, *empty = bars + TC_DFT_NST, *accf = bars + 2 * TC_DFT_NST,
              *acce = bars + 2 * TC_DFT_NST + 2, *bfull = bars + 2 * TC_DFT_NST + 4;
     uint32_t *slot = (uint32_t *)(bars + 2 * TC_DFT_NST + 5);
     int *okflag = (int *)(slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int par = blockIdx.x & 1, hcol = (blockIdx.x >> 1) & 1;
-    const int step = gridDim.x >> 2;
-    const int first = blockIdx.x >> 2;
+    const int par = blockIdx.x & 1, hcol = TC_DFT_RES ? (blockIdx.x >> 1) & 1 : 0;
+    const int step = gridDim.x / TC_DFT_NGRP;
+    const int first = blockIdx.x / TC_DFT_NGRP;
     const int myitems = (first < nimg) ? (nimg - 1 - first) / step + 1 : 0;
-    constexpr int ACC = 128;                                        // TMEM columns per accumulator
+    constexpr int ACC = TC_DFT_NB <= 128 ? 128 : 256;               // TMEM columns per accumulator
     pdl_trigger();
 
     if (threadIdx.x == 0) {
@@ -673,11 +684,13 @@ k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CU
         if (lane == 0) {                                  // ---- TMA producer
             pdl_wait();   // the polar planes come from the grid kernel
             // the CTA's table slice, once: rows hcol * 96 .. + 95 of parity par
-            tc::mbar_arrive_expect_tx(bfull, TC_DFT_NCH * TC_DFT_B_BYTES);
-            for (int ch = 0; ch < TC_DFT_NCH; ++ch) {
-                uint8_t *b = bsm + ch * TC_DFT_B_BYTES;
-                tc::tma_load_3d(b, &mB0, bfull, ch * 64, hcol * TC_DFT_NB, par);
-                tc::tma_load_3d(b + TC_DFT_B_BYTES / 2, &mB1, bfull, ch * 64, hcol * TC_DFT_NB, par);
+            if (TC_DFT_RES) {
+                tc::mbar_arrive_expect_tx(bfull, TC_DFT_NCH * TC_DFT_B_BYTES);
+                for (int ch = 0; ch < TC_DFT_NCH; ++ch) {
+                    uint8_t *b = bsm + ch * TC_DFT_B_BYTES;
+                    tc::tma_load_3d(b, &mB0, bfull, ch * 64, hcol * TC_DFT_NB, par);
+                    tc::tma_load_3d(b + TC_DFT_B_BYTES / 2, &mB1, bfull, ch * 64, hcol * TC_DFT_NB, par);
+                }
             }
             const unsigned long long pf = l2_evict_first();
             int64_t g = 0;
@@ -691,10 +704,15 @@ k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
-                    uint8_t *a = asm_ + stg * TC_DFT_A_BYTES;
-                    tc::mbar_arrive_expect_tx(&full[stg], TC_DFT_A_BYTES);
+                    uint8_t *a = asm_ + stg * TC_DFT_STAGE;
+                    tc::mbar_arrive_expect_tx(&full[stg], TC_DFT_STAGE);
                     tc::tma_load_3d_hint(a, &mA0, &full[stg], ch * 64, 128 * img, par, pf);
                     tc::tma_load_3d_hint(a + TC_DFT_A_BYTES / 2, &mA1, &full[stg], ch * 64, 128 * img, par, pf);
+                    if (!TC_DFT_RES) {   // the table's K chunk beside the rings' (streamed)
+                        uint8_t *b = a + TC_DFT_A_BYTES;
+                        tc::tma_load_3d(b, &mB0, &full[stg], ch * 64, 0, par);
+                        tc::tma_load_3d(b + TC_DFT_B_BYTES / 2, &mB1, &full[stg], ch * 64, 0, par);
+                    }
                 }
             }
             if (!ok) {
@@ -702,14 +720,14 @@ k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CU
                 atomicExch(okflag, 0);
             }
             // every issued copy lands before the CTA may leave
-            tc::mbar_wait(bfull, 0u, TC_BUDGET);
+            if (TC_DFT_RES) tc::mbar_wait(bfull, 0u, TC_BUDGET);
             for (int64_t h = (g > TC_DFT_NST ? g - TC_DFT_NST : 0); h < g; ++h)
                 tc::mbar_wait(&full[h % TC_DFT_NST], (uint32_t)((h / TC_DFT_NST) & 1), TC_BUDGET);
         }
     } else if (warp == 1) {
         if (lane == 0) {                                  // ---- MMA issue
             int64_t g = 0;
-            bool ok = tc::mbar_wait(bfull, 0u, wb);
+            bool ok = TC_DFT_RES ? tc::mbar_wait(bfull, 0u, wb) : true;
             int it = 0;
             const uint32_t id = tc::idesc(1, 128, TC_DFT_NB);
             for (; it < myitems && ok; ++it) {
@@ -727,8 +745,8 @@ k_tc_ringdft(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CU
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t sa = tc::smem_u32(asm_ + stg * TC_DFT_A_BYTES);
-                    const uint32_t sb = tc::smem_u32(bsm + ch * TC_DFT_B_BYTES);
+                    const uint32_t sa = tc::smem_u32(asm_ + stg * TC_DFT_STAGE);
+                    const uint32_t sb = TC_DFT_RES ? tc::smem_u32(bsm + ch * TC_DFT_B_BYTES) : sa + TC_DFT_A_BYTES;
 #pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
                         const int pa = (pr == 2) ? 1 : 0;   // products (hi, hi), (hi, lo), (lo, hi)
@@ -893,7 +911,7 @@ int ffb_launch_tc_dft(ffb_plan_t p, int m, const RingOut &r, cudaStream_t s) {
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    const int grid = 4 * std::max(1, std::min(sms / 4, m));   // (parity, half) x image groups
+    const int grid = TC_DFT_NGRP * std::max(1, std::min(sms / TC_DFT_NGRP, m));   // (parity, slice) x image groups
     ProfScope ps(p, FFB_KC_RING_FFT, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
