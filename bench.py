@@ -451,6 +451,59 @@ def run_ours(args):
                             "a1-a3 (the ring DFT runs on the tensor cores)" if tc_ring else "a1-a4",
                             alu_flops / 1e6, hbm_floor(plan) / 1e6)}
 
+    # end to end through the public API with host buffers, right after the
+    # timed step (the same plan, before the after-step timings)
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        hbuf = torch.empty(images.shape, dtype=torch.float32, pin_memory=True)
+        hbuf.copy_(images)
+        out_mean = torch.empty(plan.p[0], dtype=torch.float64, pin_memory=True)
+        out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            # one C-ABI call: host images in, host mean and covariance out; the
+            # library copies the images in parts on its own stream, each part
+            # overlapping the expansion of the one before
+            plan.expand_cov_host(hbuf, reset=True, mean_out=out_mean, C_out=out_C)
+
+        def h2d_rate():
+            # one plain copy of the whole pinned buffer: the host link's rate
+            # at the time (it is shared with other tenants of the machine)
+            dtmp = torch.empty(hbuf.shape, dtype=torch.float32, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dtmp.copy_(hbuf, non_blocking=True)
+            torch.cuda.synchronize()
+            rate = hbuf.numel() * 4 / (time.perf_counter() - t0) / 1e9
+            del dtmp
+            torch.cuda.empty_cache()
+            return rate
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        h2d_before = h2d_rate()
+        # host clock around every step (each ends with the covariance on the
+        # host); the value is total images / total time over k steps
+        k = max(5, args.steps // 2)
+        steps_ms = []
+        e2e_clk = ClockSampler(local)
+        e2e_clk.start()
+        time.sleep(0.3)
+        for _ in range(k):
+            ts = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            steps_ms.append((time.perf_counter() - ts) * 1e3)
+        e2e_clocks = e2e_clk.stop()
+        dt = sum(steps_ms) / 1e3 / k
+        e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
+               "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8), "steps": k,
+               "median_step_ms": statistics.median(steps_ms), "max_step_ms": max(steps_ms),
+               "call": "ffb_expand_cov_host (pinned host images -> host mean and covariance)",
+               "h2d_gbs_plain_copy": [round(h2d_before, 1), round(h2d_rate(), 1)], "clocks": e2e_clocks}
+        del hbuf
+
     # a8-a10 after the timed step (reported beside the metric, not part of
     # it): the eigendecomposition of the step's covariance, MP-Wiener
     # denoising (a9 selection and filter, a10 synthesis through the adjoint,
@@ -510,55 +563,6 @@ def run_ours(args):
                 "next2_invariants_coef_read_frac_hbm": coef_bytes / (f2_inv_ms / 1e3) / (hbm * 1e9),
                 "next3_estimate_support_images_per_s": m / (f3_est_ms / 1e3)}
         del den, adj
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e and rank == 0:
-        hbuf = torch.empty(images.shape, dtype=torch.float32, pin_memory=True)
-        hbuf.copy_(images)
-        del images
-        torch.cuda.empty_cache()
-        out_mean = torch.empty(plan.p[0], dtype=torch.float64, pin_memory=True)
-        out_C = torch.empty(plan.cov_total, dtype=torch.float64, pin_memory=True)
-
-        def e2e_step():
-            # one C-ABI call: host images in, host mean and covariance out; the
-            # library copies the images in parts on its own stream, each part
-            # overlapping the expansion of the one before
-            plan.expand_cov_host(hbuf, reset=True, mean_out=out_mean, C_out=out_C)
-
-        def h2d_rate():
-            # one plain copy of the whole pinned buffer: the host link's rate
-            # at the time (it is shared with other tenants of the machine)
-            dtmp = torch.empty(hbuf.shape, dtype=torch.float32, device=dev)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dtmp.copy_(hbuf, non_blocking=True)
-            torch.cuda.synchronize()
-            rate = hbuf.numel() * 4 / (time.perf_counter() - t0) / 1e9
-            del dtmp
-            torch.cuda.empty_cache()
-            return rate
-
-        for _ in range(3):
-            e2e_step()
-        torch.cuda.synchronize()
-        h2d_before = h2d_rate()
-        # host clock around every step (each ends with the covariance on the
-        # host); the value is total images / total time over k steps
-        k = max(5, args.steps // 2)
-        steps_ms = []
-        for _ in range(k):
-            ts = time.perf_counter()
-            e2e_step()
-            torch.cuda.synchronize()
-            steps_ms.append((time.perf_counter() - ts) * 1e3)
-        dt = sum(steps_ms) / 1e3 / k
-        e2e = {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": int(hbuf.numel() * 4),
-               "d2h_bytes_per_step": int((plan.p[0] + plan.cov_total) * 8), "steps": k,
-               "median_step_ms": statistics.median(steps_ms), "max_step_ms": max(steps_ms),
-               "call": "ffb_expand_cov_host (pinned host images -> host mean and covariance)",
-               "h2d_gbs_plain_copy": [round(h2d_before, 1), round(h2d_rate(), 1)]}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
