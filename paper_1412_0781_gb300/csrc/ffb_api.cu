@@ -129,7 +129,7 @@ int ffb_expand_on(ffb_plan_t p, const float *d_images, int64_t n, float *d_coef,
         CK(ffb_tc_prepare(p, s, nullptr));
         grp = ffb_tc_group(p);
     }
-    // groups of grp chunks: polar transform and ring FFT per chunk, one
+    // groups of grp chunks: polar transform and ring DFT per chunk, one
     // quadrature launch per group
     for (int64_t g0 = 0; g0 < n; g0 += (int64_t)grp * p->chunk) {
         const int64_t g1 = std::min<int64_t>(n, g0 + (int64_t)grp * p->chunk);

@@ -17,9 +17,11 @@
 //          place (the row is read completely before it is written).
 // Phase 3  interpolation of the half's nodes from S (w x w taps of the ES
 //          kernel with weights from the plan), the result written to the
-//          polar buffer F[img][j][l], l < n_theta/2.
-// The ring FFT (ffb_ring.cu) then completes every half ring with
-// F(theta + pi) = conj F(theta) and takes the length-n_theta FFT of Eq. 1DFFT.
+//          polar buffer F[img][j][l], l < n_theta/2 (float32 pairs, or the
+//          bf16 hi / lo planes of u and v for the tensor-core ring DFT).
+// The ring DFT of Eq. 1DFFT then completes every half ring with
+// F(theta + pi) = conj F(theta): the register FFT of ffb_ring.cu, or, for the
+// BF16x3 plans at n_theta = 512, the tensor-core contraction of ffb_tc.cu.
 //
 // Phases 1 and 2 are the same for both halves.  Where clusters of two CTAs
 // fill the GPU, the two CTAs of an image form one and split them: each
@@ -427,7 +429,7 @@ k_grid_interp_half(const float *__restrict__ images, int off, const float *__res
     if constexpr (CL) cluster_sync_all();
     else __syncthreads();
 
-    // the polar buffer may still be read by the previous kernel (the ring FFT
+    // the polar buffer may still be read by the previous kernel (the ring DFT
     // of the previous chunk) when this launch started early
     pdl_wait();
 
