@@ -180,7 +180,7 @@ def hbm_floor(plan):
 NCU_TRAFFIC = {
     "grid_interp": {"sources": ["paper_1412_0781_gb300/csrc/ffb_grid.cu:^k_grid_interp_half",
                                 "paper_1412_0781_gb300/csrc/ffb_fft.cuh"],
-                    "sha256": "7261d4a0e7c2e883d58606534a99e9fbf3ea8c50966a70fc17a513a301083209",
+                    "sha256": "7c1b52d63320b99dafa946b70647e582c41079b925af4f2d76dd0b0ccd0abc12",
                     "bytes_per_launch": 17974784 + 54528, "images_per_launch": 152},
 }
 
