@@ -174,13 +174,19 @@ def test_fused_cluster_variant_equals_plain(dev, L, monkeypatch):
     plain.close()
 
 
-@pytest.mark.parametrize("which,samples", [("fp32", (0, 9999, 19999)), ("precision", (0, 50000, 99999))])
+@pytest.mark.parametrize("which,samples", [
+    ("fp32", (0, 151, 152, 607, 608, 9999, 12345, 19847, 19999)),
+    ("precision", (0, 151, 152, 607, 608, 1215, 1216, 50000, 77777, 99847, 99999))])
 def test_expand_full_size_l128_sampled(dev, which, samples):
-    """Full-size L = 128 stacks (n = 20000 and n = 100000, the benchmark's
-    launch configuration), sampled images against the oracle."""
+    """Full-size L = 128 stacks in the benchmark's launch configuration:
+    n = 20000 in FP32 and n = 100000 in BF16x3 (the headline precision, whose
+    ring DFT runs on the tensor cores), sampled images against the oracle,
+    at the first and last image and across chunk (152 images) and
+    quadrature-group (608 images) boundaries."""
     spec = data.FP32_L128 if which == "fp32" else data.PRECISION_L128
     imgs, _, _ = data.blob_stack(spec, device=dev)
-    gp, op = gplan(128), fb.make_plan(128, 0.5, 64.0)
+    gp = gplan(128) if which == "fp32" else gplan(128, precision="bf16x3")
+    op = fb.make_plan(128, 0.5, 64.0)
     coef = gp.expand(imgs)
     torch.cuda.synchronize()
     a = as_complex(coef[list(samples)])
