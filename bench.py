@@ -623,7 +623,12 @@ def run_ours(args):
                                                sms, max_mhz)}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        # the comparison the metric names, up front: the same step in FP32
+        fp32 = None
+        if "fp32" in results and head != "fp32":
+            v32 = world * n / (results["fp32"]["ms"] / args.steps / 1e3)
+            fp32 = {"value": v32, "speedup": value / v32}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "vs_fp32": fp32, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3 (f32 acc)", "bf16x3": "bf16x3 (f32 acc)",
                                                 "tf32": "tf32", "bf16": "bf16"}[head],
