@@ -53,7 +53,7 @@ typedef enum {
     FFB_ERR_NOT_CONVERGED = -5,  /* Jacobi sweep limit reached                  */
     FFB_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up          */
     FFB_ERR_STATE = -7,          /* call out of order (e.g. eig before cov)     */
-    FFB_ERR_UNSUPPORTED = -8     /* size/precision not supported by this build */
+    FFB_ERR_UNSUPPORTED = -8     /* size/precision not supported by the library */
 } ffb_status;
 
 /* Arithmetic of the two dense contractions (radial quadrature, covariance). */
